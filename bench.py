@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Benchmark of exact block-triple triangle counting on one B300 per rank.
+
+One step is the whole hot path on one synthetic graph whose raw edge list is
+already resident in HBM: ingest (undirected, deduplicated, self-loops
+dropped), degree order and orientation, p x p partition, block-triple queue,
+the counting kernel with global and per-vertex counts, and the reduction.
+The metric is unique undirected edges per second of step time (PGAbB
+Section 5.4 counts triangles after degree ordering; here ordering and
+partitioning are inside the timed step).
+
+``value``: device-resident throughput, CUDA events on the launching stream.
+``e2e``:   the same through the one-call C ABI entry with pinned host
+           buffers (host-to-device copy of the raw edges and device-to-host
+           copy of the total and per-vertex counts inside the timed call).
+``roofline``: the counting kernel's algorithmic bytes (4|E+| + 4 sum_v
+           indeg(v) outdeg(v) + 8(n+1)) over its device time, against the
+           measured HBM copy bandwidth.
+``cpu_baseline``: the oracle (single-threaded C) on a bounded sample.
+
+With ``--impl reference`` the oracle itself is the measured arm (rank 0
+only).  Under torchrun each rank runs an independent replica (the path
+needs no exchange between replicas): ``value`` is the summed edges of all
+ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import graphgen  # noqa: E402
+
+WORKLOADS = {
+    "rmat24": dict(kind="rmat", scale=24, ef=16, p=32, seed=1,
+                   desc="R-MAT scale 24, edge factor 16 (a,b,c,d = .57,.19,.19,.05), seeded relabel; p=32"),
+    "rmat20": dict(kind="rmat", scale=20, ef=16, p=16, seed=1,
+                   desc="R-MAT scale 20, edge factor 16 (a,b,c,d = .57,.19,.19,.05), seeded relabel; p=16"),
+    "grid4096": dict(kind="grid", side=4096, pct=1.0, p=32, seed=1,
+                     desc="4096x4096 4-neighbour grid + 1% uniform random extra edges; p=32"),
+    "er4096": dict(kind="er", n=4096, m=65536, p=4, seed=1,
+                   desc="Erdos-Renyi G(n=4096, m=65536) distinct pairs; p=4"),
+}
+
+# CPU-baseline sample: the oracle's whole pipeline on the same generator
+# family at a size it finishes in about 20 s single-threaded.
+CPU_SAMPLE = dict(kind="rmat", scale=20, ef=16, p=16, seed=1)
+REF_SAMPLE = dict(kind="rmat", scale=17, ef=16, p=8, seed=1)
+
+
+def generate(w, out=None):
+    if w["kind"] == "rmat":
+        return graphgen.rmat(w["scale"], w["ef"], w["seed"], out=out)
+    if w["kind"] == "grid":
+        return graphgen.grid_plus_percent(w["side"], w["pct"], w["seed"])
+    if w["kind"] == "er":
+        return graphgen.er_distinct(w["n"], w["m"], w["seed"])
+    raise ValueError(w)
+
+
+def raw_edge_count(w):
+    if w["kind"] == "rmat":
+        return w["ef"] << w["scale"]
+    return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "of measured"
+    except Exception:
+        return 6400.0, "of fallback"
+
+
+def kernel_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes from the committed ncu summary for this kernel
+    and workload, or None when absent or taken on an older kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    src = os.path.join(ROOT, "paper_2209_04541_b300", "csrc", "tc.cu")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9]+)", text)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h:
+        return None
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return int(m.group(1)) if h.group(1) == cur else None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.err = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
+        if self.gpu_id:
+            cmd.insert(1, f"--id={self.gpu_id}")
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception as e:  # nvidia-smi missing
+            self.err = str(e)
+        time.sleep(0.15)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "error": self.err or "no sampler"}
+        time.sleep(0.1)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sms, maxes, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sms.append(float(parts[0]))
+                maxes.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sms) if sms else None,
+                "sm_max_mhz": max(maxes) if maxes else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sms), "reasons": sorted(reasons)}
+
+
+def aggregate(ms_local: float, units_local: float, dist=None):
+    """(max step ms over ranks, summed units over ranks)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms_local, units_local
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+    u = torch.tensor([units_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def oracle_pipeline(w):
+    """Oracle on one sample: clean -> order/orient -> count (global and
+    per-vertex).  Returns (seconds, unique edges, triangles)."""
+    import oracle
+    src, dst, n = generate(w)
+    t0 = time.perf_counter()
+    g = oracle.clean(src, dst, n)
+    o = oracle.orient(g)
+    c = oracle.cuts(o, w["p"])
+    oracle.block_edges(o, w["p"], c)
+    T, _, _ = oracle.tc_forward(o)
+    return time.perf_counter() - t0, g.m, T
+
+
+def cpu_baseline():
+    secs, m, _ = oracle_pipeline(CPU_SAMPLE)
+    return {"value": m / secs, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": "oracle (single-threaded C) clean+degree order+orient+partition+count with per-vertex "
+                      "counts on R-MAT scale 20 ef16 (same generator, 1/16 of the scale-24 vertices): "
+                      f"{m} unique edges in {secs:.2f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    w = REF_SAMPLE
+    times = []
+    m = T = 0
+    for i in range(args.warmup + args.steps):
+        secs, m, T = oracle_pipeline(w)
+        if i >= args.warmup:
+            times.append(secs)
+    ms = 1e3 * statistics.mean(times)
+    value = m / (ms / 1e3)
+    sample = (f"oracle (single-threaded C) clean+order+orient+partition+count per step on R-MAT scale "
+              f"{w['scale']} ef{w['ef']} p={w['p']} ({m} unique edges, {T} triangles), a bounded sample of "
+              f"the {args.workload} workload family")
+    line = {"impl": "reference", "metric": "TC edges/s", "value": value, "unit": "edges/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["desc"], "sample": f"rmat_s{w['scale']}"},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat24")
+    ap.add_argument("--mode", choices=["persistent", "plain"], default="persistent")
+    ap.add_argument("--order", choices=["weight", "locality"], default="weight")
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--per-vertex", type=int, default=1)
+    ap.add_argument("--p", type=int, default=0, help="override the workload's p")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2209_04541_b300 import pgabb as P
+
+    w = dict(WORKLOADS[args.workload])
+    if args.p:
+        w["p"] = args.p
+    mraw = raw_edge_count(w)
+    if mraw is not None:
+        hs = torch.empty(mraw, dtype=torch.uint32, pin_memory=True)
+        hd = torch.empty(mraw, dtype=torch.uint32, pin_memory=True)
+        _, _, n = generate(w, out=(hs.numpy(), hd.numpy()))
+    else:
+        s_np, d_np, n = generate(w)
+        hs = torch.from_numpy(s_np).pin_memory()
+        hd = torch.from_numpy(d_np).pin_memory()
+    mraw = hs.numel()
+    stream = torch.cuda.current_stream()
+    ds, dd = hs.cuda(non_blocking=True), hd.cuda(non_blocking=True)
+    tv = torch.zeros(n, dtype=torch.uint64, device="cuda")
+    P.load()
+    mode = P.PGB_MODE_PERSISTENT if args.mode == "persistent" else P.PGB_MODE_PLAIN
+    opts = P.pgb_tc_opts_default(mode=mode, per_vertex=args.per_vertex, chunk_edges=args.chunk,
+                                 order=P.PGB_ORDER_WEIGHT if args.order == "weight" else P.PGB_ORDER_LOCALITY)
+    info = {}
+
+    def step():
+        g = P.pgb_graph_from_edges(ds, dd, n, stream)
+        b = P.pgb_partition(g, w["p"], P.PGB_CUT_NNZ, stream)
+        g.free()
+        r = P.pgb_tc_run(b, opts, stream)
+        T, _ = P.pgb_tc_result_get(r, per_vertex=tv if args.per_vertex else None)
+        kms = P.pgb_tc_result_kernel_ms(r)
+        if not info:
+            info.update(P.pgb_blocks_info(b))
+        r.free()
+        b.free()
+        return T, kms
+
+    for _ in range(args.warmup):
+        T, _ = step()
+    torch.cuda.synchronize()
+    if dist.is_initialized():
+        dist.barrier()
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    l0 = P.pgb_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kms_all = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        T2, kms = step()
+        kms_all.append(kms)
+        assert T2 == T, "counts differ between steps"
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = P.pgb_kernel_launches() - l0
+    clocks = sampler.stop()
+    if dist.is_initialized():
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms_local = e0.elapsed_time(e1) / args.steps
+    m_u = info["m"]
+    ms, units = aggregate(ms_local, float(m_u), dist)
+    value = units / (ms / 1e3)
+
+    kernel_ms = statistics.mean(kms_all)
+    peak, peak_note = measured_peaks()
+    kname = "k_tc_persistent" if mode == P.PGB_MODE_PERSISTENT else "k_tc_tuple"
+    achieved = info["alg_bytes"] / (kernel_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_note, "alg_bytes": info["alg_bytes"],
+                "kernel_ms": kernel_ms, "traffic": kernel_traffic(kname, args.workload)}
+
+    e2e = None
+    if not args.no_e2e:
+        hout = torch.zeros(n, dtype=torch.uint64, pin_memory=True)
+        times = []
+        for i in range(2 + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Te, _ = P.pgb_tc_count_edges(hs, hd, n, w["p"], P.PGB_CUT_NNZ, opts, stream,
+                                         per_vertex=hout if args.per_vertex else None)
+            t1 = time.perf_counter()
+            assert Te == T
+            if i >= 2:
+                times.append(t1 - t0)
+        e_ms, e_units = aggregate(1e3 * statistics.mean(times), float(m_u), dist)
+        e2e = {"value": e_units / (e_ms / 1e3), "unit": "edges/s", "ms_per_step": e_ms,
+               "h2d_bytes_per_step": 8 * mraw, "d2h_bytes_per_step": 8 + (8 * n if args.per_vertex else 0)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {"metric": "TC edges/s", "value": value, "unit": "edges/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": w["desc"], "name": args.workload, "p": w["p"], "mode": args.mode,
+                           "order": args.order, "per_vertex": bool(args.per_vertex), "n": n,
+                           "raw_edges": mraw, "unique_edges": m_u, "triangles": T,
+                           "wedges": info["wedges"], "triples": info["triples"],
+                           "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (raw edge list %.2f GB, oriented graph %.2f GB)"
+                                 % (8 * mraw / 1e9, 8 * m_u / 1e9)},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "gpu_launches_per_step": launches / args.steps,
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist.is_initialized():
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,239 @@
+/*
+ * pgabb.h - C ABI of the B300 block-triple triangle-counting library.
+ *
+ * The library implements the data-parallel hot path of PGAbB's block-based
+ * model (Yasar et al., arXiv 2209.04541) for triangle counting:
+ *
+ *   load an undirected graph            (Section 5.1 preprocessing)
+ *   degree-order and orient it          (Section 5.4: degree ordering;
+ *                                        "only half of the edges")
+ *   partition it into p x p blocks      (Section 4.3: symmetric
+ *                                        rectilinear 2D partition,
+ *                                        row-major block IDs)
+ *   build the block-triple queue        (Section 3.6 block-list
+ *                                        composition; Section 4.4 weights,
+ *                                        decreasing order)
+ *   run the device kernel per triple    (Section 3.6, Listing "tc-dev":
+ *                                        per edge of the first block,
+ *                                        intersect partial lists)
+ *   reduce                              (Section 3.3 reduce_dev)
+ *
+ * Conventions for every call:
+ *   - Return value: PGB_OK (0) or a negative PGB_E_* code.  On error the
+ *     thread-local message from pgb_last_error() says what failed and no
+ *     output handle is written.  No C++ exception crosses this ABI.
+ *   - `mem` says where caller pointers live: PGB_MEM_HOST (pageable or
+ *     pinned host memory) or PGB_MEM_DEVICE (device memory of the current
+ *     CUDA device).  Host inputs are copied to the device inside the call.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     ordered on it; calls that must return sizes or values to the host
+ *     synchronise it.
+ *   - Input arrays are borrowed for the duration of the call only.  Handles
+ *     (pgb_graph, pgb_blocks, pgb_tc_result) are owned by the library and
+ *     released with their *_free call; device memory behind them comes from
+ *     the allocator set by pgb_set_allocator (default: cudaMallocAsync on
+ *     the handle's stream).
+ *   - Vertex IDs are uint32 and must be < n; counts are uint64 and exact.
+ */
+#ifndef PGABB_H
+#define PGABB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- status codes */
+#define PGB_OK           0
+#define PGB_E_INVAL     -1  /* bad argument: NULL pointer, ID >= n, p == 0, ... */
+#define PGB_E_NOMEM     -2  /* host or device allocation failed */
+#define PGB_E_OVERFLOW  -3  /* a size exceeds the supported range (e.g. >= 2^32 oriented edges) */
+#define PGB_E_CUDA      -4  /* a CUDA runtime call or kernel failed */
+#define PGB_E_BUDGET    -5  /* the request can never fit the device budget */
+#define PGB_E_TIMEOUT   -6  /* a bounded device wait gave up */
+#define PGB_E_CANCELLED -7  /* the job was cancelled */
+#define PGB_E_STATE     -8  /* handle used in the wrong state */
+
+/* ----------------------------------------------------------- memory kinds */
+#define PGB_MEM_HOST   0
+#define PGB_MEM_DEVICE 1
+
+/* ------------------------------------------------------------- cut rules */
+/* Section 4.3 asks for contiguous symmetric cuts but fixes no rule.
+ * PGB_CUT_NNZ: c[t] = least rank r with rowptr[r] * p >= t * |E+| (the
+ *              oriented out-degree prefix split into p equal shares).
+ * PGB_CUT_UNIFORM: c[t] = floor(t * n / p). */
+#define PGB_CUT_NNZ     0
+#define PGB_CUT_UNIFORM 1
+
+/* ------------------------------------------------------------- run modes */
+/* PGB_MODE_PLAIN: one kernel launch per block triple (i, j, k), each
+ *   counting the triangles u < v < w with u in V_i, v in V_j, w in V_k:
+ *   the block-list (A_ij, A_ik, A_jk) of Section 3.6 exactly.
+ * PGB_MODE_PERSISTENT: one persistent kernel drains a device queue of block
+ *   tuples (A_ij, A_i[k0..k1], A_j[k0..k1]) whose third block is a run of
+ *   consecutive column blocks (a coarser conformal cut); heavy tuples are
+ *   split into edge chunks. */
+#define PGB_MODE_PLAIN      0
+#define PGB_MODE_PERSISTENT 1
+
+/* ------------------------------------------------- intersection variants */
+/* Section 3.6: "list or hashmap-based" intersection.  Every variant returns
+ * the same integers; the choice only changes speed.
+ * PGB_VAR_AUTO:    chosen per tuple by the autotuner from block density and
+ *                  degree skew.
+ * PGB_VAR_BSEARCH: each element of the shorter list is binary-searched in
+ *                  the longer one; work is flattened across a warp.
+ * PGB_VAR_MERGE:   warp-cooperative merge of 32-element chunks.
+ * PGB_VAR_HASH:    the first endpoint's partial list is put in a
+ *                  shared-memory hash table and probed. */
+#define PGB_VAR_AUTO    0
+#define PGB_VAR_BSEARCH 1
+#define PGB_VAR_MERGE   2
+#define PGB_VAR_HASH    3
+
+/* Queue order of block tuples (Section 4.4 sorts by decreasing weight). */
+#define PGB_ORDER_WEIGHT   0  /* decreasing weight (Section 4.4) */
+#define PGB_ORDER_LOCALITY 1  /* by column block j, then decreasing weight */
+
+typedef struct pgb_graph pgb_graph;
+typedef struct pgb_blocks pgb_blocks;
+typedef struct pgb_tc_result pgb_tc_result;
+
+/* ------------------------------------------------------------- allocator */
+/* Device allocator hooks.  alloc returns device memory usable on `stream`
+ * (NULL on failure); free releases memory obtained from alloc.  Set before
+ * any handle exists; passing NULLs restores the default (cudaMallocAsync /
+ * cudaFreeAsync).  Returns PGB_E_STATE while handles are alive. */
+typedef void* (*pgb_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*pgb_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+int pgb_set_allocator(pgb_alloc_fn alloc, pgb_free_fn free_fn, void* ctx);
+
+/* ----------------------------------------------------------------- load */
+/* Section 5.1 (graphs made undirected, duplicate edges removed); self-loops
+ * are dropped.  src/dst: m raw pairs (any direction, repeats allowed),
+ * IDs < n.  Produces the cleaned simple undirected graph (kept on the
+ * device as sorted canonical pairs a < b plus vertex degrees).
+ * Errors: PGB_E_INVAL (NULL with m > 0, ID >= n, out == NULL),
+ * PGB_E_NOMEM, PGB_E_OVERFLOW (n > 2^32 - 1 cannot happen; m >= 2^32
+ * unique edges), PGB_E_CUDA. */
+int pgb_graph_from_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n,
+                         int mem, void* stream, pgb_graph** out);
+
+/* Same, from a CSR adjacency: offs int64[n+1] (non-decreasing, offs[0] = 0),
+ * cols uint32[offs[n]]; row v lists neighbours of v (either direction, any
+ * order, repeats allowed). */
+int pgb_graph_from_csr(uint32_t n, const int64_t* offs, const uint32_t* cols, int mem, void* stream,
+                       pgb_graph** out);
+
+/* n and the number of undirected edges after cleaning. */
+int pgb_graph_info(const pgb_graph* g, uint32_t* n, uint64_t* m_undirected);
+
+/* Copy the cleaned graph out: a[e] < b[e], sorted by (a, b), m_undirected
+ * entries each (either may be NULL); deg gets n degrees (may be NULL). */
+int pgb_graph_export(const pgb_graph* g, uint32_t* a, uint32_t* b, uint32_t* deg, int mem,
+                     void* stream);
+
+void pgb_graph_free(pgb_graph* g);
+
+/* ------------------------------------------------------------ partition */
+/* Section 5.4 degree ordering + orientation, then the Section 4.3 p x p
+ * symmetric partition and the Section 3.6 / 4.4 block-triple queue.
+ *   rank:  vertices sorted by (degree ascending, original ID ascending);
+ *   E+:    u -> v for every edge with rank(u) < rank(v), rows sorted;
+ *   cuts:  c[0] = 0 <= c[1] <= ... <= c[p] = n by `cut_rule`;
+ *   A_ij:  oriented edges with rank(u) in [c_i, c_i+1), rank(v) in
+ *          [c_j, c_j+1); only i <= j can be non-empty;
+ *   queue: triples i <= j <= k with A_ij, A_ik, A_jk non-empty, weight
+ *          |A_ij| + |A_ik| + |A_jk|, decreasing weight, ties by (i, j, k).
+ * Errors: PGB_E_INVAL (p == 0, p > 1024, p > n when n > 0, bad rule),
+ * PGB_E_NOMEM, PGB_E_OVERFLOW, PGB_E_CUDA.  The graph may be freed after. */
+int pgb_partition(const pgb_graph* g, uint32_t p, int cut_rule, void* stream, pgb_blocks** out);
+
+typedef struct {
+    uint32_t n;            /* vertices */
+    uint32_t p;            /* parts per dimension */
+    uint64_t m;            /* oriented edges |E+| = undirected edges */
+    uint64_t nonempty_blocks;
+    uint64_t triples;      /* queue length */
+    uint64_t wedges;       /* sum over v of indeg(v) * outdeg(v) in E+ */
+    uint64_t alg_bytes;    /* 4|E+| + 4 * wedges + 8 (n + 1) */
+    uint32_t max_outdeg;
+    uint32_t reserved;
+} pgb_blocks_stats;
+
+int pgb_blocks_info(const pgb_blocks* b, pgb_blocks_stats* out);
+
+/* Export one array of the partition (host or device destination):
+ *   PGB_EXPORT_PERM       uint32[n]   vertex of each rank
+ *   PGB_EXPORT_ROWPTR     int64[n+1]  oriented CSR offsets (rank space)
+ *   PGB_EXPORT_COL        uint32[m]   oriented CSR columns (rank space)
+ *   PGB_EXPORT_CUTS       uint32[p+1]
+ *   PGB_EXPORT_BLOCK_EDGES uint64[p*p] |A_ij| row-major
+ *   PGB_EXPORT_TRIPLES    uint32[3*T] queue (i, j, k) in order
+ *   PGB_EXPORT_WEIGHTS    uint64[T]   queue weights */
+#define PGB_EXPORT_PERM        0
+#define PGB_EXPORT_ROWPTR      1
+#define PGB_EXPORT_COL         2
+#define PGB_EXPORT_CUTS        3
+#define PGB_EXPORT_BLOCK_EDGES 4
+#define PGB_EXPORT_TRIPLES     5
+#define PGB_EXPORT_WEIGHTS     6
+int pgb_blocks_export(const pgb_blocks* b, int what, void* dst, int mem, void* stream);
+
+void pgb_blocks_free(pgb_blocks* b);
+
+/* ------------------------------------------------------------------ run */
+typedef struct {
+    int32_t mode;          /* PGB_MODE_* (default PGB_MODE_PERSISTENT) */
+    int32_t variant;       /* PGB_VAR_* (default PGB_VAR_AUTO) */
+    int32_t per_vertex;    /* also count t[x] per vertex (default 1) */
+    int32_t per_triple;    /* PLAIN mode: keep one count per queued triple */
+    int32_t use_graph;     /* capture the launches in a CUDA graph (default 0) */
+    int32_t order;         /* PGB_ORDER_* (default PGB_ORDER_WEIGHT) */
+    uint64_t device_budget;/* bytes for resident blocks; 0 = no limit */
+    uint32_t chunk_edges;  /* PERSISTENT: edges per dequeued chunk (0 = auto) */
+    uint32_t reserved[7];
+} pgb_tc_opts;
+
+void pgb_tc_opts_default(pgb_tc_opts* o);
+
+/* Section 3.6 device kernel over every queued block tuple, then the
+ * Section 3.3 reduction.  Enqueued on `stream`; the result handle is
+ * ready when pgb_tc_result_get returns.  Errors: PGB_E_INVAL (bad opts),
+ * PGB_E_BUDGET, PGB_E_NOMEM, PGB_E_CUDA. */
+int pgb_tc_run(const pgb_blocks* b, const pgb_tc_opts* opts, void* stream, pgb_tc_result** out);
+
+/* Wait for the run and fetch results.  total: global triangle count (may be
+ * NULL).  per_vertex: n uint64 counts t[x] indexed by ORIGINAL vertex ID
+ * (may be NULL; PGB_E_STATE if the run had per_vertex = 0). */
+int pgb_tc_result_get(pgb_tc_result* r, uint64_t* total, uint64_t* per_vertex, int mem);
+
+/* PLAIN mode with per_triple = 1: counts[t] for queue entry t (T entries). */
+int pgb_tc_result_triples(pgb_tc_result* r, uint64_t* counts, int mem);
+
+/* Device time of the counting kernels of this run in milliseconds (CUDA
+ * events around the launches on the run's stream); valid after get. */
+int pgb_tc_result_kernel_ms(pgb_tc_result* r, float* ms);
+
+void pgb_tc_result_free(pgb_tc_result* r);
+
+/* One call: load + partition + run + fetch.  per_vertex may be NULL. */
+int pgb_tc_count_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, uint32_t p,
+                       int cut_rule, const pgb_tc_opts* opts, int mem, void* stream, uint64_t* total,
+                       uint64_t* per_vertex);
+
+/* ----------------------------------------------------------------- misc */
+const char* pgb_last_error(void);   /* thread-local; never NULL */
+const char* pgb_version(void);
+
+/* Number of the library's own CUDA kernels launched by this process so far
+ * (calls into library primitives such as CUB radix sorts are not counted). */
+uint64_t pgb_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PGABB_H */

@@ -1,7 +1,7 @@
 """ORACLE: test infrastructure only.
 
 Plain single-threaded CPU restatement of exact triangle counting over block
-triples (PGAbB, arXiv 2209.04541, Section 3.5), used to check the CUDA path.
+triples (PGAbB, arXiv 2209.04541, Section 3.6), used to check the CUDA path.
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import it.  It shares no code with the CUDA library and never
 imports it; the only shared module is the seeded input generator
@@ -166,7 +166,7 @@ class Oriented:
 
 
 def orient(g: Graph) -> Oriented:
-    """Section 5.5: degree ordering (ties by ID) and upper orientation."""
+    """Section 5.4: degree ordering (ties by ID) and upper orientation."""
     lib, n = g.lib, g.n
     perm = np.empty(max(n, 1), dtype=np.uint32)
     rank = np.empty(max(n, 1), dtype=np.uint32)

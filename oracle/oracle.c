@@ -11,22 +11,22 @@
  *
  *   or_clean              Section 5.1: graphs are made undirected and
  *                         duplicate edges are removed; self-loops dropped.
- *   or_tc_node_iterator   Section 3.5: a triangle is a mutually connected
+ *   or_tc_node_iterator   Section 3.6: a triangle is a mutually connected
  *                         triple; count common neighbours of each edge's
  *                         endpoints by list intersection.  Original IDs.
  *   or_tc_vertex          the per-vertex count t[x] = number of triangles
  *                         containing x, for one x at a time.
- *   or_degree_rank        Section 5.5: degree-based vertex ordering
+ *   or_degree_rank        Section 5.4: degree-based vertex ordering
  *                         (ascending degree, ties by original ID).
- *   or_orient             Section 5.5: triangle counting needs half the
+ *   or_orient             Section 5.4: triangle counting needs half the
  *                         edges (keep u->v when rank(u) < rank(v)).
  *   or_cuts               Section 4.3: symmetric rectilinear p x p cuts
  *                         (nnz-balanced or uniform contiguous rank ranges).
  *   or_block_edges        Section 3.1 / 4.3: edges of block A_ij.
- *   or_triples            Section 3.5 block-list composition; Section 4.4
+ *   or_triples            Section 3.6 block-list composition; Section 4.4
  *                         default weight (edges in the block-list), sorted
  *                         in decreasing weight.
- *   or_tc_forward         Section 3.5 kernel summed over all block triples:
+ *   or_tc_forward         Section 3.6 kernel summed over all block triples:
  *                         for each oriented edge (u,v), count common
  *                         out-neighbours; per-vertex and per-triple counts.
  *   or_tc_vertex_sample   or_tc_vertex over a list of vertices.

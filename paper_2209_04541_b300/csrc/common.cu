@@ -1,0 +1,88 @@
+// Error reporting, the device allocator hook and small shared helpers.
+#include <atomic>
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace pgb {
+
+static thread_local std::string t_last_error = "";
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+
+void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+static std::mutex g_alloc_mu;
+static pgb_alloc_fn g_alloc = nullptr;
+static pgb_free_fn g_free = nullptr;
+static void* g_ctx = nullptr;
+static std::atomic<long> g_live{0};
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launches(uint64_t k) { g_launches += k; }
+
+void live_handles_add(int d) { g_live += d; }
+
+void* dev_alloc(size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return nullptr;
+    void* p = nullptr;
+    if (g_alloc) {
+        p = g_alloc(bytes, s, g_ctx);
+        if (!p) fail(PGB_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+        return p;
+    }
+    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        fail(PGB_E_NOMEM, "cudaMallocAsync of " + std::to_string(bytes) + " bytes failed: " +
+                              cudaGetErrorString(e));
+    }
+    return p;
+}
+
+void dev_free(void* p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    if (g_free) {
+        g_free(p, bytes, s, g_ctx);
+        return;
+    }
+    cudaFreeAsync(p, s);
+}
+
+int num_bits(uint64_t x) {
+    int b = 0;
+    while (b < 64 && (x >> b) != 0) ++b;
+    return b < 1 ? 1 : b;
+}
+
+void copy_out(void* dst, const void* src_dev, size_t bytes, int mem, cudaStream_t s) {
+    if (bytes == 0) return;
+    if (!dst) fail(PGB_E_INVAL, "NULL destination");
+    PGB_CUDA(cudaMemcpyAsync(dst, src_dev, bytes,
+                             mem == PGB_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (mem != PGB_MEM_DEVICE) PGB_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace pgb
+
+extern "C" {
+
+const char* pgb_last_error(void) { return pgb::t_last_error.c_str(); }
+
+const char* pgb_version(void) { return "pgabb-b300 0.1.0 (sm_103a)"; }
+
+uint64_t pgb_kernel_launches(void) { return pgb::g_launches.load(); }
+
+int pgb_set_allocator(pgb_alloc_fn alloc, pgb_free_fn free_fn, void* ctx) {
+    return pgb::guard([&] {
+        std::lock_guard<std::mutex> lk(pgb::g_alloc_mu);
+        if (pgb::g_live.load() != 0) pgb::fail(PGB_E_STATE, "allocator changed while handles are alive");
+        if ((alloc == nullptr) != (free_fn == nullptr))
+            pgb::fail(PGB_E_INVAL, "alloc and free must both be set or both be NULL");
+        pgb::g_alloc = alloc;
+        pgb::g_free = free_fn;
+        pgb::g_ctx = ctx;
+    });
+}
+
+}  // extern "C"

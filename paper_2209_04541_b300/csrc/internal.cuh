@@ -1,0 +1,168 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "pgabb.h"
+
+namespace pgb {
+
+// ------------------------------------------------------------------ errors
+
+// Thrown inside the library only; every extern "C" entry converts it to a
+// status code through guard().
+struct Error {
+    int code;
+    std::string msg;
+};
+
+void set_error(const std::string& msg);
+[[noreturn]] void fail(int code, const std::string& msg);
+
+#define PGB_CUDA(call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            ::pgb::fail(e_ == cudaErrorMemoryAllocation ? PGB_E_NOMEM : PGB_E_CUDA,        \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+// Check the launch(es) just issued and count them as the library's own
+// kernel launches (library primitives such as CUB sorts are not counted).
+#define PGB_CHECK_LAUNCHES(what, k)                                                        \
+    do {                                                                                   \
+        ::pgb::note_launches(k);                                                           \
+        cudaError_t e_ = cudaGetLastError();                                               \
+        if (e_ != cudaSuccess)                                                             \
+            ::pgb::fail(PGB_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+#define PGB_CHECK_LAUNCH(what) PGB_CHECK_LAUNCHES(what, 1)
+
+void note_launches(uint64_t k);
+
+template <class F>
+int guard(F&& f) {
+    try {
+        f();
+        return PGB_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return PGB_E_NOMEM;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return PGB_E_CUDA;
+    }
+}
+
+// --------------------------------------------------------------- allocator
+
+void* dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void* p, size_t bytes, cudaStream_t s);
+void live_handles_add(int d);
+
+// Owning device buffer that returns its memory to the library allocator on
+// the stream it was allocated on.
+template <class T>
+struct DevBuf {
+    T* ptr = nullptr;
+    size_t count = 0;
+    cudaStream_t stream = nullptr;
+
+    DevBuf() = default;
+    DevBuf(size_t n, cudaStream_t s) { alloc(n, s); }
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept { swap(o); }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) {
+            release();
+            swap(o);
+        }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+
+    void swap(DevBuf& o) noexcept {
+        std::swap(ptr, o.ptr);
+        std::swap(count, o.count);
+        std::swap(stream, o.stream);
+    }
+    void alloc(size_t n, cudaStream_t s) {
+        release();
+        stream = s;
+        count = n;
+        ptr = n ? static_cast<T*>(dev_alloc(n * sizeof(T), s)) : nullptr;
+    }
+    void release() {
+        if (ptr) dev_free(ptr, count * sizeof(T), stream);
+        ptr = nullptr;
+        count = 0;
+    }
+    size_t bytes() const { return count * sizeof(T); }
+};
+
+// Scratch bytes for library primitives (CUB temp storage).
+struct Scratch {
+    DevBuf<unsigned char> buf;
+    void* get(size_t bytes, cudaStream_t s) {
+        if (buf.count < bytes) buf.alloc(bytes + (bytes >> 3) + 256, s);
+        return buf.ptr;
+    }
+};
+
+int num_bits(uint64_t x);  // bits needed to represent values in [0, x]
+
+// ------------------------------------------------------------------ handles
+
+}  // namespace pgb
+
+struct pgb_graph {
+    uint32_t n = 0;
+    uint64_t m = 0;                       // unique undirected edges
+    uint32_t id_bits = 1;                 // bits per packed endpoint
+    pgb::DevBuf<uint64_t> keys;           // (a << id_bits) | b, a < b, sorted
+    pgb::DevBuf<uint32_t> deg;            // degree per vertex
+    cudaStream_t stream = nullptr;
+};
+
+struct pgb_triple {
+    uint32_t i, j, k;
+    uint64_t w;
+};
+
+struct pgb_blocks {
+    uint32_t n = 0, p = 0;
+    uint64_t m = 0;
+    cudaStream_t stream = nullptr;
+    pgb::DevBuf<uint32_t> perm;    // rank -> original ID
+    pgb::DevBuf<uint32_t> rowptr;  // n + 1 oriented offsets (m < 2^32)
+    pgb::DevBuf<uint32_t> col;     // m oriented columns, rank space, rows sorted
+    pgb::DevBuf<uint32_t> rowidx;  // m row of each oriented edge
+    pgb::DevBuf<uint32_t> bedge;   // m CSR edge positions grouped by block (i, j) row-major
+    pgb::DevBuf<uint32_t> cuts_d;  // p + 1
+    std::vector<uint32_t> cuts;    // p + 1
+    std::vector<uint64_t> block_edges;  // p * p
+    std::vector<uint64_t> block_off;    // p * p + 1 offsets into bedge
+    std::vector<pgb_triple> triples;    // queue order
+    uint64_t wedges = 0;
+    uint32_t max_outdeg = 0;
+};
+
+namespace pgb {
+
+// Kernel-side stages (each enqueued on `s`; those that need sizes sync).
+void ingest_keys(pgb_graph* g, const uint32_t* src, const uint32_t* dst, uint64_t m, cudaStream_t s);
+void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, pgb_blocks* b);
+void copy_out(void* dst, const void* src_dev, size_t bytes, int mem, cudaStream_t s);
+
+}  // namespace pgb

@@ -1,0 +1,420 @@
+// Degree ordering, upper orientation, p x p partition and block-triple
+// queue (Sections 3.6, 4.3, 4.4 and 5.4 of PGAbB).
+//
+// Layout produced (all on the device, rank space):
+//   perm[r]     original ID of rank r (ranks sort vertices by (degree, ID))
+//   rowptr/col  oriented CSR: row u lists v > u ascending (uint32 offsets;
+//               the library rejects graphs with 2^32 or more edges)
+//   rowidx[e]   row of oriented edge e
+//   bedge       edge positions grouped by block (i, j) in row-major block
+//               order (Section 4.3 "row-major order"), CSR order inside a
+//               block; block (i, j) occupies [block_off[ij], block_off[ij+1])
+// Because every part is a contiguous rank range, the partial list of u in
+// block A_ik is the contiguous slice of row u with columns in [c_k, c_k+1).
+#include <cub/device/device_radix_sort.cuh>
+
+#include <algorithm>
+#include <memory>
+#include <numeric>
+
+#include "internal.cuh"
+
+namespace pgb {
+
+static int grid_for(uint64_t items, int threads = 256) {
+    uint64_t g = (items + threads - 1) / threads;
+    if (g > 148ull * 32) g = 148ull * 32;
+    return g < 1 ? 1 : (int)g;
+}
+
+__global__ void k_iota(uint32_t* __restrict__ x, uint64_t n) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x[i] = (uint32_t)i;
+}
+
+__global__ void k_invert(const uint32_t* __restrict__ perm, uint32_t n, uint32_t* __restrict__ rank) {
+    uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) rank[perm[r]] = r;
+}
+
+// Oriented key of each undirected edge: (low rank << B) | high rank.
+__global__ void k_orient_keys(const uint64_t* __restrict__ keys, uint64_t m, uint32_t B,
+                              const uint32_t* __restrict__ rank, uint64_t* __restrict__ okeys) {
+    const uint64_t mask = (1ull << B) - 1;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        uint64_t k = keys[e];
+        uint32_t ra = rank[(uint32_t)(k >> B)], rb = rank[(uint32_t)(k & mask)];
+        uint32_t lo = ra < rb ? ra : rb, hi = ra < rb ? rb : ra;
+        okeys[e] = ((uint64_t)lo << B) | hi;
+    }
+}
+
+// Unpack sorted oriented keys into COO rows / CSR columns and write every
+// rowptr entry exactly once: rowptr[r] = first edge whose row is >= r.
+__global__ void k_unpack_csr(const uint64_t* __restrict__ okeys, uint64_t m, uint32_t n, uint32_t B,
+                             uint32_t* __restrict__ rowidx, uint32_t* __restrict__ col,
+                             uint32_t* __restrict__ rowptr) {
+    const uint64_t mask = (1ull << B) - 1;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        uint64_t k = okeys[e];
+        uint32_t u = (uint32_t)(k >> B);
+        rowidx[e] = u;
+        col[e] = (uint32_t)(k & mask);
+        uint32_t prev = (e == 0) ? 0 : (uint32_t)(okeys[e - 1] >> B) + 1;
+        for (uint32_t r = prev; r <= u; ++r) rowptr[r] = (uint32_t)e;
+        if (e == m - 1)
+            for (uint32_t r = u + 1; r <= n; ++r) rowptr[r] = (uint32_t)m;
+    }
+}
+
+__global__ void k_fill_u32(uint32_t* __restrict__ x, uint64_t n, uint32_t v) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x[i] = v;
+}
+
+// Cut points.  NNZ rule: c[t] = least r in [0, n] with rowptr[r] * p >= t * M,
+// found by binary search over the non-decreasing rowptr.  UNIFORM rule:
+// c[t] = floor(t * n / p).
+__global__ void k_cuts(const uint32_t* __restrict__ rowptr, uint32_t n, uint32_t p, int rule,
+                       uint32_t* __restrict__ cuts) {
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > p) return;
+    if (t == 0) { cuts[0] = 0; return; }
+    if (t == p) { cuts[p] = n; return; }
+    if (rule == PGB_CUT_UNIFORM) {
+        cuts[t] = (uint32_t)(((uint64_t)t * n) / p);
+        return;
+    }
+    const uint64_t M = rowptr[n];
+    const uint64_t need = (uint64_t)t * M;
+    uint32_t lo = 0, hi = n + 1;  // first r in [0, n] with rowptr[r] * p >= need
+    while (lo < hi) {
+        uint32_t mid = lo + (hi - lo) / 2;
+        if ((uint64_t)rowptr[mid] * p >= need) hi = mid; else lo = mid + 1;
+    }
+    cuts[t] = lo;
+}
+
+__device__ __forceinline__ uint32_t part_of(const uint32_t* cuts, uint32_t p, uint32_t r) {
+    // largest t in [0, p) with cuts[t] <= r
+    uint32_t lo = 0, hi = p;
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (cuts[mid] <= r) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Block id (i * p + j) of every oriented edge, and the p x p block edge
+// histogram (shared-memory counters when p*p fits, global otherwise).
+__global__ void k_block_ids(const uint32_t* __restrict__ rowidx, const uint32_t* __restrict__ col, uint64_t m,
+                            const uint32_t* __restrict__ cuts_g, uint32_t p, uint32_t* __restrict__ bid,
+                            unsigned long long* __restrict__ hist) {
+    extern __shared__ uint32_t sm[];
+    uint32_t* cuts = sm;
+    uint32_t* h = sm + p + 1;
+    const bool use_smem = (uint64_t)p * p <= 4096;
+    for (uint32_t i = threadIdx.x; i <= p; i += blockDim.x) cuts[i] = cuts_g[i];
+    if (use_smem)
+        for (uint32_t i = threadIdx.x; i < p * p; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        uint32_t b = part_of(cuts, p, rowidx[e]) * p + part_of(cuts, p, col[e]);
+        if (bid) bid[e] = b;
+        if (use_smem) atomicAdd(&h[b], 1u);
+        else atomicAdd(&hist[b], 1ull);
+    }
+    if (use_smem) {
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < p * p; i += blockDim.x)
+            if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+    }
+}
+
+// In-degree histogram of the oriented graph.
+__global__ void k_indeg(const uint32_t* __restrict__ col, uint64_t m, uint32_t* __restrict__ indeg) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
+        atomicAdd(&indeg[col[e]], 1u);
+}
+
+// sum_v indeg(v) * outdeg(v) and max outdeg.
+__global__ void k_wedges(const uint32_t* __restrict__ indeg, const uint32_t* __restrict__ rowptr, uint32_t n,
+                         unsigned long long* __restrict__ out_sum, unsigned int* __restrict__ out_max) {
+    __shared__ unsigned long long ssum[32];
+    __shared__ unsigned int smax[32];
+    unsigned long long acc = 0;
+    unsigned int mx = 0;
+    uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint32_t od = rowptr[v + 1] - rowptr[v];
+        acc += (unsigned long long)indeg[v] * od;
+        mx = od > mx ? od : mx;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_down_sync(0xffffffffu, acc, o);
+        unsigned int y = __shfl_down_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { ssum[w] = acc; smax[w] = mx; }
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        acc = l < nw ? ssum[l] : 0;
+        mx = l < nw ? smax[l] : 0;
+        for (int o = 16; o > 0; o >>= 1) {
+            acc += __shfl_down_sync(0xffffffffu, acc, o);
+            unsigned int y = __shfl_down_sync(0xffffffffu, mx, o);
+            mx = y > mx ? y : mx;
+        }
+        if (l == 0) {
+            atomicAdd(out_sum, acc);
+            atomicMax(out_max, mx);
+        }
+    }
+}
+
+template <class K, class V>
+static void sort_pairs(K* keys, K* keys_alt, V* vals, V* vals_alt, uint64_t count, int end_bit, cudaStream_t s,
+                       Scratch& scratch, K** keys_out, V** vals_out) {
+    cub::DoubleBuffer<K> dk(keys, keys_alt);
+    cub::DoubleBuffer<V> dv(vals, vals_alt);
+    size_t tmp = 0;
+    PGB_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, dk, dv, (int64_t)count, 0, end_bit, s));
+    void* t = scratch.get(tmp, s);
+    PGB_CUDA(cub::DeviceRadixSort::SortPairs(t, tmp, dk, dv, (int64_t)count, 0, end_bit, s));
+    *keys_out = dk.Current();
+    *vals_out = dv.Current();
+}
+
+// Section 3.6 block-list composition with the Section 4.4 default weight
+// (edges in the block-list) and decreasing order; ties by (i, j, k).
+static std::vector<pgb_triple> make_queue(uint32_t p, const std::vector<uint64_t>& be) {
+    std::vector<pgb_triple> q;
+    for (uint32_t i = 0; i < p; ++i)
+        for (uint32_t j = i; j < p; ++j) {
+            uint64_t a = be[(size_t)i * p + j];
+            if (!a) continue;
+            for (uint32_t k = j; k < p; ++k) {
+                uint64_t b = be[(size_t)i * p + k], c = be[(size_t)j * p + k];
+                if (b && c) q.push_back({i, j, k, a + b + c});
+            }
+        }
+    std::stable_sort(q.begin(), q.end(), [](const pgb_triple& x, const pgb_triple& y) { return x.w > y.w; });
+    return q;
+}
+
+void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, pgb_blocks* b) {
+    const uint32_t n = g->n;
+    const uint64_t m = g->m;
+    const uint32_t B = g->id_bits;
+    b->n = n;
+    b->p = p;
+    b->m = m;
+    b->stream = s;
+    Scratch scratch;
+
+    // --- degree order: stable sort of IDs by degree (ties keep ID order)
+    b->perm.alloc(n, s);
+    DevBuf<uint32_t> rank(n, s);
+    if (n > 0) {
+        DevBuf<uint32_t> kd(n, s), kalt(n, s), ids(n, s);
+        PGB_CUDA(cudaMemcpyAsync(kd.ptr, g->deg.ptr, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+        k_iota<<<grid_for(n), 256, 0, s>>>(ids.ptr, n);
+        PGB_CHECK_LAUNCH("k_iota");
+        uint32_t *ko, *vo;
+        sort_pairs(kd.ptr, kalt.ptr, ids.ptr, b->perm.ptr, n, num_bits(n), s, scratch, &ko, &vo);
+        if (vo != b->perm.ptr)
+            PGB_CUDA(cudaMemcpyAsync(b->perm.ptr, vo, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+        k_invert<<<grid_for(n), 256, 0, s>>>(b->perm.ptr, n, rank.ptr);
+        PGB_CHECK_LAUNCH("k_invert");
+    }
+
+    // --- orientation: sort (low rank, high rank) keys
+    b->rowptr.alloc((size_t)n + 1, s);
+    b->col.alloc(m, s);
+    b->rowidx.alloc(m, s);
+    if (m > 0) {
+        DevBuf<uint64_t> ok(m, s), oalt(m, s);
+        k_orient_keys<<<grid_for(m), 256, 0, s>>>(g->keys.ptr, m, B, rank.ptr, ok.ptr);
+        PGB_CHECK_LAUNCH("k_orient_keys");
+        cub::DoubleBuffer<uint64_t> db(ok.ptr, oalt.ptr);
+        size_t tmp = 0;
+        PGB_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp, db, (int64_t)m, 0, (int)(2 * B), s));
+        void* t = scratch.get(tmp, s);
+        PGB_CUDA(cub::DeviceRadixSort::SortKeys(t, tmp, db, (int64_t)m, 0, (int)(2 * B), s));
+        k_unpack_csr<<<grid_for(m), 256, 0, s>>>(db.Current(), m, n, B, b->rowidx.ptr, b->col.ptr, b->rowptr.ptr);
+        PGB_CHECK_LAUNCH("k_unpack_csr");
+    } else {
+        k_fill_u32<<<grid_for((uint64_t)n + 1), 256, 0, s>>>(b->rowptr.ptr, (uint64_t)n + 1, 0);
+        PGB_CHECK_LAUNCH("k_fill_u32");
+    }
+    rank.release();
+
+    // --- cuts
+    b->cuts_d.alloc((size_t)p + 1, s);
+    k_cuts<<<(p + 1 + 127) / 128, 128, 0, s>>>(b->rowptr.ptr, n, p, rule, b->cuts_d.ptr);
+    PGB_CHECK_LAUNCH("k_cuts");
+    b->cuts.assign((size_t)p + 1, 0);
+
+    // --- block histogram and block ids
+    const size_t pp = (size_t)p * p;
+    DevBuf<unsigned long long> hist(pp, s);
+    PGB_CUDA(cudaMemsetAsync(hist.ptr, 0, pp * 8, s));
+    DevBuf<uint32_t> bid;
+    if (m > 0) {
+        if (p > 1) bid.alloc(m, s);
+        size_t smem = ((size_t)p + 1) * 4 + (pp <= 4096 ? pp * 4 : 0);
+        k_block_ids<<<grid_for(m), 256, smem, s>>>(b->rowidx.ptr, b->col.ptr, m, b->cuts_d.ptr, p,
+                                                   p > 1 ? bid.ptr : nullptr, hist.ptr);
+        PGB_CHECK_LAUNCH("k_block_ids");
+    }
+
+    // --- wedge statistics for B_alg and the autotuner
+    DevBuf<unsigned long long> wsum(1, s);
+    DevBuf<unsigned int> wmax(1, s);
+    PGB_CUDA(cudaMemsetAsync(wsum.ptr, 0, 8, s));
+    PGB_CUDA(cudaMemsetAsync(wmax.ptr, 0, 4, s));
+    if (m > 0) {
+        DevBuf<uint32_t> indeg(n, s);
+        PGB_CUDA(cudaMemsetAsync(indeg.ptr, 0, (size_t)n * 4, s));
+        k_indeg<<<grid_for(m), 256, 0, s>>>(b->col.ptr, m, indeg.ptr);
+        PGB_CHECK_LAUNCH("k_indeg");
+        k_wedges<<<grid_for(n), 256, 0, s>>>(indeg.ptr, b->rowptr.ptr, n, wsum.ptr, wmax.ptr);
+        PGB_CHECK_LAUNCH("k_wedges");
+    }
+
+    // --- one sync: cuts, histogram, stats to the host
+    b->block_edges.assign(pp, 0);
+    unsigned long long hw = 0;
+    unsigned int hm = 0;
+    PGB_CUDA(cudaMemcpyAsync(b->cuts.data(), b->cuts_d.ptr, ((size_t)p + 1) * 4, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaMemcpyAsync(b->block_edges.data(), hist.ptr, pp * 8, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaMemcpyAsync(&hw, wsum.ptr, 8, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaMemcpyAsync(&hm, wmax.ptr, 4, cudaMemcpyDeviceToHost, s));
+
+    // --- group edges by block: stable radix sort of (block id, edge position)
+    b->bedge.alloc(m, s);
+    if (m > 0) {
+        if (p == 1) {
+            k_iota<<<grid_for(m), 256, 0, s>>>(b->bedge.ptr, m);
+            PGB_CHECK_LAUNCH("k_iota");
+        } else {
+            DevBuf<uint32_t> kalt(m, s), vals(m, s);
+            k_iota<<<grid_for(m), 256, 0, s>>>(vals.ptr, m);
+            PGB_CHECK_LAUNCH("k_iota");
+            uint32_t *ko, *vo;
+            sort_pairs(bid.ptr, kalt.ptr, vals.ptr, b->bedge.ptr, m, num_bits(pp - 1), s, scratch, &ko, &vo);
+            if (vo != b->bedge.ptr)
+                PGB_CUDA(cudaMemcpyAsync(b->bedge.ptr, vo, m * 4, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    PGB_CUDA(cudaStreamSynchronize(s));
+    b->wedges = hw;
+    b->max_outdeg = hm;
+    b->block_off.assign(pp + 1, 0);
+    for (size_t i = 0; i < pp; ++i) b->block_off[i + 1] = b->block_off[i] + b->block_edges[i];
+    b->triples = make_queue(p, b->block_edges);
+}
+
+}  // namespace pgb
+
+using namespace pgb;
+
+extern "C" {
+
+int pgb_partition(const pgb_graph* g, uint32_t p, int cut_rule, void* stream, pgb_blocks** out) {
+    return guard([&] {
+        if (!g || !out) fail(PGB_E_INVAL, "NULL argument");
+        if (p == 0 || p > 1024) fail(PGB_E_INVAL, "p must be in [1, 1024]");
+        if (g->n > 0 && p > g->n) fail(PGB_E_INVAL, "p must not exceed n");
+        if (cut_rule != PGB_CUT_NNZ && cut_rule != PGB_CUT_UNIFORM) fail(PGB_E_INVAL, "bad cut rule");
+        if (g->n == 0xFFFFFFFFu) fail(PGB_E_OVERFLOW, "n must be below 2^32 - 1");
+        std::unique_ptr<pgb_blocks> b(new pgb_blocks());
+        build_partition(g, p, cut_rule, (cudaStream_t)stream, b.get());
+        live_handles_add(1);
+        *out = b.release();
+    });
+}
+
+int pgb_blocks_info(const pgb_blocks* b, pgb_blocks_stats* out) {
+    return guard([&] {
+        if (!b || !out) fail(PGB_E_INVAL, "NULL argument");
+        std::memset(out, 0, sizeof(*out));
+        out->n = b->n;
+        out->p = b->p;
+        out->m = b->m;
+        uint64_t ne = 0;
+        for (uint64_t x : b->block_edges) ne += x ? 1 : 0;
+        out->nonempty_blocks = ne;
+        out->triples = b->triples.size();
+        out->wedges = b->wedges;
+        out->alg_bytes = 4 * b->m + 4 * b->wedges + 8 * ((uint64_t)b->n + 1);
+        out->max_outdeg = b->max_outdeg;
+    });
+}
+
+__global__ void k_widen(const uint32_t* __restrict__ x, uint64_t n, int64_t* __restrict__ y) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = x[i];
+}
+
+int pgb_blocks_export(const pgb_blocks* b, int what, void* dst, int mem, void* stream) {
+    return guard([&] {
+        if (!b) fail(PGB_E_INVAL, "blocks is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        auto host_or_dev = [&](const void* hsrc, size_t bytes) {
+            if (!bytes) return;
+            if (!dst) fail(PGB_E_INVAL, "NULL destination");
+            if (mem == PGB_MEM_DEVICE) {
+                PGB_CUDA(cudaMemcpyAsync(dst, hsrc, bytes, cudaMemcpyHostToDevice, s));
+                PGB_CUDA(cudaStreamSynchronize(s));
+            } else {
+                std::memcpy(dst, hsrc, bytes);
+            }
+        };
+        switch (what) {
+            case PGB_EXPORT_PERM: copy_out(dst, b->perm.ptr, (size_t)b->n * 4, mem, s); break;
+            case PGB_EXPORT_ROWPTR: {
+                DevBuf<int64_t> w((size_t)b->n + 1, s);
+                k_widen<<<grid_for((uint64_t)b->n + 1), 256, 0, s>>>(b->rowptr.ptr, (uint64_t)b->n + 1, w.ptr);
+                PGB_CHECK_LAUNCH("k_widen");
+                copy_out(dst, w.ptr, ((size_t)b->n + 1) * 8, mem, s);
+                PGB_CUDA(cudaStreamSynchronize(s));
+                break;
+            }
+            case PGB_EXPORT_COL: copy_out(dst, b->col.ptr, b->m * 4, mem, s); break;
+            case PGB_EXPORT_CUTS: host_or_dev(b->cuts.data(), b->cuts.size() * 4); break;
+            case PGB_EXPORT_BLOCK_EDGES: host_or_dev(b->block_edges.data(), b->block_edges.size() * 8); break;
+            case PGB_EXPORT_TRIPLES: {
+                std::vector<uint32_t> t(3 * b->triples.size());
+                for (size_t i = 0; i < b->triples.size(); ++i) {
+                    t[3 * i] = b->triples[i].i;
+                    t[3 * i + 1] = b->triples[i].j;
+                    t[3 * i + 2] = b->triples[i].k;
+                }
+                host_or_dev(t.data(), t.size() * 4);
+                break;
+            }
+            case PGB_EXPORT_WEIGHTS: {
+                std::vector<uint64_t> w(b->triples.size());
+                for (size_t i = 0; i < w.size(); ++i) w[i] = b->triples[i].w;
+                host_or_dev(w.data(), w.size() * 8);
+                break;
+            }
+            default: fail(PGB_E_INVAL, "unknown export id");
+        }
+    });
+}
+
+void pgb_blocks_free(pgb_blocks* b) {
+    if (!b) return;
+    delete b;
+    live_handles_add(-1);
+}
+
+}  // extern "C"

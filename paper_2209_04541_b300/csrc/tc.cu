@@ -1,0 +1,497 @@
+// Triangle counting over block tuples (PGAbB Section 3.6, Listing "tc-dev")
+// and its reduction (Section 3.3 reduce_dev).
+//
+// A block tuple is (A_ij, A_i[k0..k1], A_j[k0..k1]) with the third index a
+// run of consecutive column blocks; k0 == k1 is the paper's block triple.
+// For every oriented edge (u, v) of A_ij the kernel counts
+//     | N+(u) ∩ N+(v) ∩ [lo, hi) |,   lo = c_k0, hi = c_(k1+1),
+// where both partial lists are contiguous slices of the sorted rows (the
+// parts are contiguous rank ranges).  Only entries of N+(u) after v can
+// match (N+(v) holds ranks > v), so u's list starts right after v.
+//
+// Warp organisation (binary-search variant): 32 edges per warp step, one per
+// lane.  Each lane picks the shorter of its two lists; a warp prefix sum
+// flattens all (edge, element) work items of the 32 edges, so the warp's
+// lanes stay busy whatever the list lengths.  Each item is looked up by
+// binary search in the edge's longer list.  Counts stay in registers and are
+// reduced per CTA into a per-CTA slot (no global atomics for the total).
+#include <algorithm>
+#include <memory>
+
+#include "internal.cuh"
+
+namespace pgb {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct Tuple {
+    uint32_t e_begin;  // first position in bedge
+    uint32_t e_count;  // edges of A_ij covered
+    uint32_t lo, hi;   // third-vertex rank range [lo, hi)
+    uint32_t clip;     // 1 when lists must be clipped to [lo, hi)
+    uint32_t variant;
+};
+
+struct Graph {
+    const uint32_t* __restrict__ bedge;
+    const uint32_t* __restrict__ rowidx;
+    const uint32_t* __restrict__ col;
+    const uint32_t* __restrict__ rowptr;
+    unsigned long long* __restrict__ tv;  // per-vertex counts, rank space (may be null)
+};
+
+__device__ __forceinline__ uint32_t lower_bound(const uint32_t* __restrict__ a, uint32_t b, uint32_t e,
+                                                uint32_t x) {
+    uint32_t n = e - b;
+    while (n > 0) {
+        uint32_t half = n >> 1;
+        if (__ldg(a + b + half) < x) {
+            b += half + 1;
+            n -= half + 1;
+        } else {
+            n = half;
+        }
+    }
+    return b;
+}
+
+// One warp step over up to 32 edges (lane `lane` owns bedge[idx] if valid).
+template <bool PV>
+__device__ __forceinline__ void warp_step(const Graph& G, uint32_t idx, bool valid, uint32_t lo, uint32_t hi,
+                                          bool clip, unsigned long long& cnt, uint32_t* s_edge, int lane) {
+    uint32_t sb = 0, sl = 0, lb = 0, ll = 0, u = 0, v = 0;
+    if (valid) {
+        const uint32_t e = __ldg(G.bedge + idx);
+        u = __ldg(G.rowidx + e);
+        v = __ldg(G.col + e);
+        uint32_t xb = e + 1, xe = __ldg(G.rowptr + u + 1);
+        uint32_t yb = __ldg(G.rowptr + v), ye = __ldg(G.rowptr + v + 1);
+        if (clip) {
+            xb = lower_bound(G.col, xb, xe, lo);
+            xe = lower_bound(G.col, xb, xe, hi);
+            yb = lower_bound(G.col, yb, ye, lo);
+            ye = lower_bound(G.col, yb, ye, hi);
+        }
+        const uint32_t lx = xe - xb, ly = ye - yb;
+        if (lx <= ly) {
+            sb = xb; sl = lx; lb = yb; ll = ly;
+        } else {
+            sb = yb; sl = ly; lb = xb; ll = lx;
+        }
+        if (ll == 0) sl = 0;
+    }
+    uint32_t incl = sl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    const uint32_t excl = incl - sl;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t f = base + lane;
+        int o = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            uint32_t ex = __shfl_sync(kFull, excl, o + step);
+            if (ex <= f) o += step;
+        }
+        const uint32_t o_ex = __shfl_sync(kFull, excl, o);
+        const uint32_t o_sb = __shfl_sync(kFull, sb, o);
+        const uint32_t o_lb = __shfl_sync(kFull, lb, o);
+        const uint32_t o_ll = __shfl_sync(kFull, ll, o);
+        if (f < total) {
+            const uint32_t x = __ldg(G.col + o_sb + (f - o_ex));
+            const uint32_t end = o_lb + o_ll;
+            const uint32_t p = lower_bound(G.col, o_lb, end, x);
+            if (p < end && __ldg(G.col + p) == x) {
+                ++cnt;
+                if (PV) {
+                    atomicAdd(G.tv + x, 1ull);
+                    atomicAdd(s_edge + o, 1u);
+                }
+            }
+        }
+    }
+    if (PV) {
+        __syncwarp();
+        const uint32_t c = s_edge[lane];
+        if (c) {
+            atomicAdd(G.tv + u, (unsigned long long)c);
+            atomicAdd(G.tv + v, (unsigned long long)c);
+            s_edge[lane] = 0;
+        }
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void cta_reduce_store(unsigned long long cnt, unsigned long long* __restrict__ slot) {
+    __shared__ unsigned long long s_red[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
+    if (lane == 0) s_red[warp] = cnt;
+    __syncthreads();
+    if (warp == 0) {
+        cnt = lane < kWarps ? s_red[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
+        if (lane == 0) *slot = cnt;
+    }
+}
+
+// PLAIN mode: one launch per block triple; warps stride over its edges.
+template <bool PV>
+__global__ void __launch_bounds__(kThreads) k_tc_tuple(Graph G, Tuple t, unsigned long long* __restrict__ partials) {
+    __shared__ uint32_t s_edge[kWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (PV) s_edge[warp][lane] = 0;
+    __syncwarp();
+    unsigned long long cnt = 0;
+    const uint32_t gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
+    const uint32_t end = t.e_begin + t.e_count;
+    for (uint32_t i0 = t.e_begin + gw * 32; i0 < end; i0 += nw * 32) {
+        const uint32_t idx = i0 + lane;
+        warp_step<PV>(G, idx, idx < end, t.lo, t.hi, t.clip != 0, cnt, s_edge[warp], lane);
+    }
+    cta_reduce_store(cnt, partials + blockIdx.x);
+}
+
+// PERSISTENT mode: warps dequeue chunks of `chunk` edges from the tuple
+// queue (chunk_prefix[t] = chunks before tuple t) with one atomic each.
+template <bool PV>
+__global__ void __launch_bounds__(kThreads)
+    k_tc_persistent(Graph G, const Tuple* __restrict__ tuples, const uint32_t* __restrict__ chunk_prefix,
+                    uint32_t ntuples, uint32_t chunk, unsigned int* __restrict__ cursor,
+                    unsigned long long* __restrict__ partials) {
+    __shared__ uint32_t s_edge[kWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (PV) s_edge[warp][lane] = 0;
+    __syncwarp();
+    const uint32_t total_chunks = chunk_prefix[ntuples];
+    unsigned long long cnt = 0;
+    while (true) {
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(cursor, 1u);
+        c = __shfl_sync(kFull, c, 0);
+        if (c >= total_chunks) break;
+        // tuple t: largest t with chunk_prefix[t] <= c
+        uint32_t t = 0;
+        if (lane == 0) {
+            uint32_t lo = 0, hi = ntuples;
+            while (hi - lo > 1) {
+                uint32_t mid = (lo + hi) >> 1;
+                if (__ldg(chunk_prefix + mid) <= c) lo = mid; else hi = mid;
+            }
+            t = lo;
+        }
+        t = __shfl_sync(kFull, t, 0);
+        const Tuple tu = tuples[t];
+        const uint32_t i0 = tu.e_begin + (c - __ldg(chunk_prefix + t)) * chunk;
+        const uint32_t end = min(i0 + chunk, tu.e_begin + tu.e_count);
+        for (uint32_t i = i0; i < end; i += 32) {
+            const uint32_t idx = i + lane;
+            warp_step<PV>(G, idx, idx < end, tu.lo, tu.hi, tu.clip != 0, cnt, s_edge[warp], lane);
+        }
+    }
+    cta_reduce_store(cnt, partials + blockIdx.x);
+}
+
+// Sum of partials[0, n) into *out (one CTA).
+__global__ void k_reduce_sum(const unsigned long long* __restrict__ partials, uint64_t n,
+                             unsigned long long* __restrict__ out) {
+    __shared__ unsigned long long s[32];
+    unsigned long long acc = 0;
+    for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        acc = lane < (int)(blockDim.x >> 5) ? s[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+        if (lane == 0) *out = acc;
+    }
+}
+
+// Per-segment sums: out[t] = sum partials[seg[t], seg[t+1]) (one CTA each).
+__global__ void k_reduce_segments(const unsigned long long* __restrict__ partials, const uint64_t* __restrict__ seg,
+                                  unsigned long long* __restrict__ out) {
+    __shared__ unsigned long long s[32];
+    const uint64_t b = seg[blockIdx.x], e = seg[blockIdx.x + 1];
+    unsigned long long acc = 0;
+    for (uint64_t i = b + threadIdx.x; i < e; i += blockDim.x) acc += partials[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        acc = lane < (int)(blockDim.x >> 5) ? s[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+        if (lane == 0) out[blockIdx.x] = acc;
+    }
+}
+
+// Rank-space per-vertex counts to original IDs.
+__global__ void k_scatter_orig(const unsigned long long* __restrict__ tv, const uint32_t* __restrict__ perm,
+                               uint32_t n, unsigned long long* __restrict__ out) {
+    uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) out[perm[r]] = tv[r];
+}
+
+static int sm_count() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0;
+        PGB_CUDA(cudaGetDevice(&dev));
+        PGB_CUDA(cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return cached;
+}
+
+}  // namespace pgb
+
+struct pgb_tc_result {
+    cudaStream_t stream = nullptr;
+    uint32_t n = 0;
+    bool per_vertex = false;
+    bool per_triple = false;
+    uint64_t ntriples = 0;
+    pgb::DevBuf<unsigned long long> total;
+    pgb::DevBuf<unsigned long long> tv_orig;
+    pgb::DevBuf<unsigned long long> triple_counts;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    ~pgb_tc_result() {
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
+};
+
+namespace pgb {
+
+static Tuple make_tuple(const pgb_blocks* b, uint32_t i, uint32_t j, uint32_t k0, uint32_t k1) {
+    Tuple t;
+    const size_t ij = (size_t)i * b->p + j;
+    t.e_begin = (uint32_t)b->block_off[ij];
+    t.e_count = (uint32_t)b->block_edges[ij];
+    t.lo = b->cuts[k0];
+    t.hi = b->cuts[k1 + 1];
+    // v >= c_j and entries of both lists exceed v, so [c_j, n) needs no clipping
+    t.clip = (t.lo > b->cuts[j] || t.hi < b->n) ? 1u : 0u;
+    t.variant = PGB_VAR_BSEARCH;
+    return t;
+}
+
+static void run(const pgb_blocks* b, const pgb_tc_opts& o, cudaStream_t s, pgb_tc_result* r) {
+    const uint32_t n = b->n;
+    r->stream = s;
+    r->n = n;
+    r->per_vertex = o.per_vertex != 0;
+    r->per_triple = o.mode == PGB_MODE_PLAIN && o.per_triple != 0;
+    r->ntriples = b->triples.size();
+    r->total.alloc(1, s);
+    PGB_CUDA(cudaEventCreate(&r->ev0));
+    PGB_CUDA(cudaEventCreate(&r->ev1));
+
+    DevBuf<unsigned long long> tv;
+    if (r->per_vertex) {
+        tv.alloc(n, s);
+        if (n) PGB_CUDA(cudaMemsetAsync(tv.ptr, 0, (size_t)n * 8, s));
+    }
+    Graph G{b->bedge.ptr, b->rowidx.ptr, b->col.ptr, b->rowptr.ptr, tv.ptr};
+
+    DevBuf<unsigned long long> partials;
+    uint64_t npartials = 0;
+    if (o.mode == PGB_MODE_PLAIN) {
+        // one launch per block triple, in queue order
+        const uint64_t T = b->triples.size();
+        std::vector<uint64_t> seg(T + 1, 0);
+        std::vector<int> grids(T);
+        for (uint64_t t = 0; t < T; ++t) {
+            const pgb_triple& q = b->triples[t];
+            uint64_t e = b->block_edges[(size_t)q.i * b->p + q.j];
+            uint64_t g = (e + 32 * kWarps - 1) / (32 * kWarps);
+            g = std::min<uint64_t>(std::max<uint64_t>(g, 1), (uint64_t)sm_count() * 8);
+            grids[t] = (int)g;
+            seg[t + 1] = seg[t] + g;
+        }
+        npartials = seg[T];
+        partials.alloc(std::max<uint64_t>(npartials, 1), s);
+        PGB_CUDA(cudaEventRecord(r->ev0, s));
+        for (uint64_t t = 0; t < T; ++t) {
+            const pgb_triple& q = b->triples[t];
+            Tuple tu = make_tuple(b, q.i, q.j, q.k, q.k);
+            if (r->per_vertex)
+                k_tc_tuple<true><<<grids[t], kThreads, 0, s>>>(G, tu, partials.ptr + seg[t]);
+            else
+                k_tc_tuple<false><<<grids[t], kThreads, 0, s>>>(G, tu, partials.ptr + seg[t]);
+        }
+        PGB_CHECK_LAUNCHES("k_tc_tuple", T);
+        PGB_CUDA(cudaEventRecord(r->ev1, s));
+        if (r->per_triple && T > 0) {
+            DevBuf<uint64_t> dseg(T + 1, s);
+            PGB_CUDA(cudaMemcpyAsync(dseg.ptr, seg.data(), (T + 1) * 8, cudaMemcpyHostToDevice, s));
+            r->triple_counts.alloc(T, s);
+            k_reduce_segments<<<(unsigned)T, 256, 0, s>>>(partials.ptr, dseg.ptr, r->triple_counts.ptr);
+            PGB_CHECK_LAUNCH("k_reduce_segments");
+        }
+    } else {
+        // tuples (A_ij, A_i[j..p-1], A_j[j..p-1]): one per non-empty block
+        // pair on the queue, ordered by the summed weight of its triples
+        const uint32_t p = b->p;
+        std::vector<uint64_t> w((size_t)p * p, 0);
+        for (const pgb_triple& q : b->triples) w[(size_t)q.i * p + q.j] += q.w;
+        std::vector<uint32_t> ids;
+        for (uint32_t ij = 0; ij < p * p; ++ij)
+            if (w[ij]) ids.push_back(ij);
+        if (o.order == PGB_ORDER_LOCALITY) {
+            std::stable_sort(ids.begin(), ids.end(), [&](uint32_t x, uint32_t y) {
+                if (x % p != y % p) return x % p > y % p;
+                return w[x] > w[y];
+            });
+        } else {
+            std::stable_sort(ids.begin(), ids.end(), [&](uint32_t x, uint32_t y) { return w[x] > w[y]; });
+        }
+        const uint32_t chunk = o.chunk_edges ? ((o.chunk_edges + 31) / 32) * 32 : 64;
+        std::vector<Tuple> tuples;
+        std::vector<uint32_t> cp(1, 0);
+        for (uint32_t ij : ids) {
+            Tuple tu = make_tuple(b, ij / p, ij % p, ij % p, p - 1);
+            tuples.push_back(tu);
+            cp.push_back(cp.back() + (tu.e_count + chunk - 1) / chunk);
+        }
+        const uint32_t nt = (uint32_t)tuples.size();
+        DevBuf<Tuple> dt(std::max<uint32_t>(nt, 1), s);
+        DevBuf<uint32_t> dcp(cp.size(), s);
+        DevBuf<unsigned int> cursor(1, s);
+        if (nt) PGB_CUDA(cudaMemcpyAsync(dt.ptr, tuples.data(), nt * sizeof(Tuple), cudaMemcpyHostToDevice, s));
+        PGB_CUDA(cudaMemcpyAsync(dcp.ptr, cp.data(), cp.size() * 4, cudaMemcpyHostToDevice, s));
+        PGB_CUDA(cudaMemsetAsync(cursor.ptr, 0, 4, s));
+        int per_sm = 0;
+        if (r->per_vertex)
+            PGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_persistent<true>, kThreads, 0));
+        else
+            PGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_persistent<false>, kThreads, 0));
+        const int grid = std::max(1, per_sm) * sm_count();
+        npartials = (uint64_t)grid;
+        partials.alloc(npartials, s);
+        PGB_CUDA(cudaEventRecord(r->ev0, s));
+        if (r->per_vertex)
+            k_tc_persistent<true><<<grid, kThreads, 0, s>>>(G, dt.ptr, dcp.ptr, nt, chunk, cursor.ptr, partials.ptr);
+        else
+            k_tc_persistent<false><<<grid, kThreads, 0, s>>>(G, dt.ptr, dcp.ptr, nt, chunk, cursor.ptr, partials.ptr);
+        PGB_CHECK_LAUNCH("k_tc_persistent");
+        PGB_CUDA(cudaEventRecord(r->ev1, s));
+    }
+    if (npartials)
+        k_reduce_sum<<<1, 1024, 0, s>>>(partials.ptr, npartials, r->total.ptr);
+    else
+        PGB_CUDA(cudaMemsetAsync(r->total.ptr, 0, 8, s));
+    PGB_CHECK_LAUNCH("k_reduce_sum");
+    if (r->per_vertex) {
+        r->tv_orig.alloc(n, s);
+        if (n) {
+            k_scatter_orig<<<std::min<uint32_t>((n + 255) / 256, 148 * 32), 256, 0, s>>>(tv.ptr, b->perm.ptr, n,
+                                                                                      r->tv_orig.ptr);
+            PGB_CHECK_LAUNCH("k_scatter_orig");
+        }
+    }
+}
+
+}  // namespace pgb
+
+using namespace pgb;
+
+extern "C" {
+
+void pgb_tc_opts_default(pgb_tc_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->mode = PGB_MODE_PERSISTENT;
+    o->variant = PGB_VAR_AUTO;
+    o->per_vertex = 1;
+    o->order = PGB_ORDER_WEIGHT;
+}
+
+int pgb_tc_run(const pgb_blocks* b, const pgb_tc_opts* opts, void* stream, pgb_tc_result** out) {
+    return guard([&] {
+        if (!b || !out) fail(PGB_E_INVAL, "NULL argument");
+        pgb_tc_opts o;
+        if (opts) o = *opts; else pgb_tc_opts_default(&o);
+        if (o.mode != PGB_MODE_PLAIN && o.mode != PGB_MODE_PERSISTENT) fail(PGB_E_INVAL, "bad mode");
+        if (o.variant < PGB_VAR_AUTO || o.variant > PGB_VAR_HASH) fail(PGB_E_INVAL, "bad variant");
+        if (o.order != PGB_ORDER_WEIGHT && o.order != PGB_ORDER_LOCALITY) fail(PGB_E_INVAL, "bad order");
+        std::unique_ptr<pgb_tc_result> r(new pgb_tc_result());
+        run(b, o, (cudaStream_t)stream, r.get());
+        live_handles_add(1);
+        *out = r.release();
+    });
+}
+
+int pgb_tc_result_get(pgb_tc_result* r, uint64_t* total, uint64_t* per_vertex, int mem) {
+    return guard([&] {
+        if (!r) fail(PGB_E_INVAL, "result is NULL");
+        cudaStream_t s = r->stream;
+        if (per_vertex) {
+            if (!r->per_vertex) fail(PGB_E_STATE, "run was made without per-vertex counts");
+            copy_out(per_vertex, r->tv_orig.ptr, (size_t)r->n * 8, mem, s);
+        }
+        if (total) {
+            unsigned long long h = 0;
+            PGB_CUDA(cudaMemcpyAsync(&h, r->total.ptr, 8, cudaMemcpyDeviceToHost, s));
+            PGB_CUDA(cudaStreamSynchronize(s));
+            *total = h;
+        }
+        PGB_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+int pgb_tc_result_triples(pgb_tc_result* r, uint64_t* counts, int mem) {
+    return guard([&] {
+        if (!r) fail(PGB_E_INVAL, "result is NULL");
+        if (!r->per_triple) fail(PGB_E_STATE, "run was not PLAIN with per_triple = 1");
+        copy_out(counts, r->triple_counts.ptr, r->ntriples * 8, mem, r->stream);
+        PGB_CUDA(cudaStreamSynchronize(r->stream));
+    });
+}
+
+int pgb_tc_result_kernel_ms(pgb_tc_result* r, float* ms) {
+    return guard([&] {
+        if (!r || !ms) fail(PGB_E_INVAL, "NULL argument");
+        PGB_CUDA(cudaEventSynchronize(r->ev1));
+        PGB_CUDA(cudaEventElapsedTime(ms, r->ev0, r->ev1));
+    });
+}
+
+void pgb_tc_result_free(pgb_tc_result* r) {
+    if (!r) return;
+    delete r;
+    live_handles_add(-1);
+}
+
+int pgb_tc_count_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, uint32_t p,
+                       int cut_rule, const pgb_tc_opts* opts, int mem, void* stream, uint64_t* total,
+                       uint64_t* per_vertex) {
+    pgb_graph* g = nullptr;
+    pgb_blocks* b = nullptr;
+    pgb_tc_result* r = nullptr;
+    int rc = pgb_graph_from_edges(src, dst, m, n, mem, stream, &g);
+    if (rc == PGB_OK) rc = pgb_partition(g, p, cut_rule, stream, &b);
+    pgb_graph_free(g);
+    pgb_tc_opts o;
+    if (opts) o = *opts; else pgb_tc_opts_default(&o);
+    if (!per_vertex) o.per_vertex = 0;
+    if (rc == PGB_OK) rc = pgb_tc_run(b, &o, stream, &r);
+    if (rc == PGB_OK) rc = pgb_tc_result_get(r, total, per_vertex, mem);
+    pgb_tc_result_free(r);
+    pgb_blocks_free(b);
+    return rc;
+}
+
+}  // extern "C"

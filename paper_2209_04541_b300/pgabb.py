@@ -1,0 +1,432 @@
+"""Python binding of the C ABI declared in ``include/pgabb.h``.
+
+Argument marshalling only: every step (ingest, ordering, partition, queue,
+counting, reduction) runs in the CUDA library ``libpgabb.so``.  Functions
+keep the C names.  Arrays may be numpy arrays (host) or torch tensors (host
+or CUDA); the memory kind passed to the library follows the array.  Streams
+default to torch's current CUDA stream.  When CUDA is available the library
+is pointed at torch's caching allocator, so all device memory comes from
+torch.
+
+If the shared library is missing and cannot be built, importing it raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PGB_OK = 0
+PGB_E_INVAL = -1
+PGB_E_NOMEM = -2
+PGB_E_OVERFLOW = -3
+PGB_E_CUDA = -4
+PGB_E_BUDGET = -5
+PGB_E_TIMEOUT = -6
+PGB_E_CANCELLED = -7
+PGB_E_STATE = -8
+
+PGB_MEM_HOST = 0
+PGB_MEM_DEVICE = 1
+
+PGB_CUT_NNZ = 0
+PGB_CUT_UNIFORM = 1
+
+PGB_MODE_PLAIN = 0
+PGB_MODE_PERSISTENT = 1
+
+PGB_VAR_AUTO = 0
+PGB_VAR_BSEARCH = 1
+PGB_VAR_MERGE = 2
+PGB_VAR_HASH = 3
+
+PGB_ORDER_WEIGHT = 0
+PGB_ORDER_LOCALITY = 1
+
+PGB_EXPORT_PERM = 0
+PGB_EXPORT_ROWPTR = 1
+PGB_EXPORT_COL = 2
+PGB_EXPORT_CUTS = 3
+PGB_EXPORT_BLOCK_EDGES = 4
+PGB_EXPORT_TRIPLES = 5
+PGB_EXPORT_WEIGHTS = 6
+
+HEADER = os.path.join(_build.INCLUDE, "pgabb.h")
+
+
+class PgbError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where} failed ({code}): {msg}")
+        self.code = code
+
+
+class TcOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("variant", ctypes.c_int32), ("per_vertex", ctypes.c_int32),
+                ("per_triple", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("device_budget", ctypes.c_uint64), ("chunk_edges", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 7)]
+
+
+class BlocksStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("p", ctypes.c_uint32), ("m", ctypes.c_uint64),
+                ("nonempty_blocks", ctypes.c_uint64), ("triples", ctypes.c_uint64),
+                ("wedges", ctypes.c_uint64), ("alg_bytes", ctypes.c_uint64),
+                ("max_outdeg", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lock = threading.Lock()
+_lib = None
+_callbacks = []
+
+_VP = ctypes.c_void_p
+_SIGS = {
+    "pgb_set_allocator": (ctypes.c_int, [_ALLOC_FN, _FREE_FN, _VP]),
+    "pgb_graph_from_edges": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, _VP,
+                                            ctypes.POINTER(_VP)]),
+    "pgb_graph_from_csr": (ctypes.c_int, [ctypes.c_uint32, _VP, _VP, ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
+    "pgb_graph_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)]),
+    "pgb_graph_export": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
+    "pgb_graph_free": (None, [_VP]),
+    "pgb_partition": (ctypes.c_int, [_VP, ctypes.c_uint32, ctypes.c_int, _VP, ctypes.POINTER(_VP)]),
+    "pgb_blocks_info": (ctypes.c_int, [_VP, ctypes.POINTER(BlocksStats)]),
+    "pgb_blocks_export": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP]),
+    "pgb_blocks_free": (None, [_VP]),
+    "pgb_tc_opts_default": (None, [ctypes.POINTER(TcOpts)]),
+    "pgb_tc_run": (ctypes.c_int, [_VP, ctypes.POINTER(TcOpts), _VP, ctypes.POINTER(_VP)]),
+    "pgb_tc_result_get": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), _VP, ctypes.c_int]),
+    "pgb_tc_result_triples": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
+    "pgb_tc_result_kernel_ms": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "pgb_tc_result_free": (None, [_VP]),
+    "pgb_tc_count_edges": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                          ctypes.c_int, ctypes.POINTER(TcOpts), ctypes.c_int, _VP,
+                                          ctypes.POINTER(ctypes.c_uint64), _VP]),
+    "pgb_last_error": (ctypes.c_char_p, []),
+    "pgb_version": (ctypes.c_char_p, []),
+    "pgb_kernel_launches": (ctypes.c_uint64, []),
+}
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/pgabb.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(pgb_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(n for n in names if not n.endswith("_fn")))
+
+
+def load(register_torch_allocator: bool = True):
+    """Load (building if needed) ``libpgabb.so`` and bind every entry point."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+            if register_torch_allocator:
+                _maybe_use_torch_allocator(lib)
+    return _lib
+
+
+def _maybe_use_torch_allocator(lib):
+    try:
+        import torch
+    except ImportError:
+        return
+    if not torch.cuda.is_available():
+        return
+    raw_alloc = torch._C._cuda_cudaCachingAllocator_raw_alloc
+    raw_delete = torch._C._cuda_cudaCachingAllocator_raw_delete
+
+    def _alloc(size, stream, ctx):
+        try:
+            return raw_alloc(int(size), int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, size, stream, ctx):
+        try:
+            raw_delete(int(ptr))
+        except Exception:
+            pass
+
+    fa, ff = _ALLOC_FN(_alloc), _FREE_FN(_free)
+    _callbacks.append((fa, ff))
+    _check(lib.pgb_set_allocator(fa, ff, None), "pgb_set_allocator")
+
+
+def _check(rc: int, where: str):
+    if rc != PGB_OK:
+        raise PgbError(rc, where, pgb_last_error())
+
+
+def _stream(stream):
+    if stream is not None:
+        return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return 0
+
+
+def _arr(x, dtype):
+    """(pointer, mem kind, keep-alive object) for a numpy array or torch tensor."""
+    if x is None:
+        return None, PGB_MEM_HOST, None
+    if isinstance(x, np.ndarray):
+        x = np.ascontiguousarray(x, dtype=dtype)
+        return x.ctypes.data, PGB_MEM_HOST, x
+    import torch
+    if isinstance(x, torch.Tensor):
+        tdt = {np.uint32: torch.uint32, np.int64: torch.int64, np.uint64: torch.uint64}[dtype]
+        if x.dtype != tdt:
+            raise TypeError(f"expected {tdt}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), (PGB_MEM_DEVICE if x.is_cuda else PGB_MEM_HOST), x
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+class _Handle:
+    _free_name = ""
+
+    def __init__(self, ptr, stream):
+        self.ptr = ptr
+        self.stream = stream
+
+    def free(self):
+        if self.ptr:
+            getattr(load(), self._free_name)(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        if not self.ptr:
+            raise ValueError("handle already freed")
+        return ctypes.c_void_p(self.ptr)
+
+
+class Graph(_Handle):
+    _free_name = "pgb_graph_free"
+
+
+class Blocks(_Handle):
+    _free_name = "pgb_blocks_free"
+
+
+class Result(_Handle):
+    _free_name = "pgb_tc_result_free"
+
+    def __init__(self, ptr, stream, n, ntriples):
+        super().__init__(ptr, stream)
+        self.n = n
+        self.ntriples = ntriples
+
+
+# ----------------------------------------------------------------- C names
+
+def pgb_last_error() -> str:
+    return load().pgb_last_error().decode()
+
+
+def pgb_version() -> str:
+    return load().pgb_version().decode()
+
+
+def pgb_kernel_launches() -> int:
+    return int(load().pgb_kernel_launches())
+
+
+def pgb_set_allocator(alloc=None, free=None, ctx=None):
+    """Install raw ctypes callbacks (``_ALLOC_FN``/``_FREE_FN``) or restore the default."""
+    lib = load()
+    fa = alloc if alloc is not None else ctypes.cast(None, _ALLOC_FN)
+    ff = free if free is not None else ctypes.cast(None, _FREE_FN)
+    _check(lib.pgb_set_allocator(fa, ff, ctx), "pgb_set_allocator")
+
+
+def pgb_graph_from_edges(src, dst, n: int, stream=None) -> Graph:
+    lib = load()
+    ps, ms, ks = _arr(src, np.uint32)
+    pd, md, kd = _arr(dst, np.uint32)
+    m = 0 if ks is None else int(ks.numel() if hasattr(ks, "numel") else ks.size)
+    if ms != md:
+        raise ValueError("src and dst must live in the same memory")
+    st = _stream(stream)
+    out = ctypes.c_void_p()
+    _check(lib.pgb_graph_from_edges(ps, pd, m, n, ms, st, ctypes.byref(out)), "pgb_graph_from_edges")
+    return Graph(out.value, st)
+
+
+def pgb_graph_from_csr(n: int, offs, cols, stream=None) -> Graph:
+    lib = load()
+    po, mo, _ko = _arr(offs, np.int64)
+    pc, mc, _kc = _arr(cols, np.uint32)
+    st = _stream(stream)
+    out = ctypes.c_void_p()
+    _check(lib.pgb_graph_from_csr(n, po, pc, mo, st, ctypes.byref(out)), "pgb_graph_from_csr")
+    return Graph(out.value, st)
+
+
+def pgb_graph_info(g: Graph):
+    n, m = ctypes.c_uint32(), ctypes.c_uint64()
+    _check(load().pgb_graph_info(g, ctypes.byref(n), ctypes.byref(m)), "pgb_graph_info")
+    return int(n.value), int(m.value)
+
+
+def pgb_graph_export(g: Graph):
+    """(a, b, deg) numpy arrays of the cleaned graph (a < b, sorted)."""
+    n, m = pgb_graph_info(g)
+    a = np.empty(m, np.uint32)
+    b = np.empty(m, np.uint32)
+    d = np.empty(n, np.uint32)
+    _check(load().pgb_graph_export(g, a.ctypes.data if m else None, b.ctypes.data if m else None,
+                                   d.ctypes.data if n else None, PGB_MEM_HOST, g.stream), "pgb_graph_export")
+    return a, b, d
+
+
+def pgb_graph_free(g: Graph):
+    g.free()
+
+
+def pgb_partition(g: Graph, p: int, cut_rule: int = PGB_CUT_NNZ, stream=None) -> Blocks:
+    st = _stream(stream) if stream is not None else g.stream
+    out = ctypes.c_void_p()
+    _check(load().pgb_partition(g, p, cut_rule, st, ctypes.byref(out)), "pgb_partition")
+    return Blocks(out.value, st)
+
+
+def pgb_blocks_info(b: Blocks) -> dict:
+    s = BlocksStats()
+    _check(load().pgb_blocks_info(b, ctypes.byref(s)), "pgb_blocks_info")
+    return {k: int(getattr(s, k)) for k, _ in BlocksStats._fields_ if k != "reserved"}
+
+
+def pgb_blocks_export(b: Blocks, what: int) -> np.ndarray:
+    info = pgb_blocks_info(b)
+    n, p, m, T = info["n"], info["p"], info["m"], info["triples"]
+    spec = {
+        PGB_EXPORT_PERM: (np.uint32, n),
+        PGB_EXPORT_ROWPTR: (np.int64, n + 1),
+        PGB_EXPORT_COL: (np.uint32, m),
+        PGB_EXPORT_CUTS: (np.uint32, p + 1),
+        PGB_EXPORT_BLOCK_EDGES: (np.uint64, p * p),
+        PGB_EXPORT_TRIPLES: (np.uint32, 3 * T),
+        PGB_EXPORT_WEIGHTS: (np.uint64, T),
+    }
+    dt, cnt = spec[what]
+    out = np.zeros(cnt, dtype=dt)
+    _check(load().pgb_blocks_export(b, what, out.ctypes.data if cnt else None, PGB_MEM_HOST, b.stream),
+           "pgb_blocks_export")
+    if what == PGB_EXPORT_BLOCK_EDGES:
+        return out.reshape(p, p)
+    if what == PGB_EXPORT_TRIPLES:
+        return out.reshape(T, 3)
+    return out
+
+
+def pgb_blocks_free(b: Blocks):
+    b.free()
+
+
+def pgb_tc_opts_default(**kw) -> TcOpts:
+    o = TcOpts()
+    load().pgb_tc_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def pgb_tc_run(b: Blocks, opts: TcOpts | None = None, stream=None) -> Result:
+    st = _stream(stream) if stream is not None else b.stream
+    out = ctypes.c_void_p()
+    _check(load().pgb_tc_run(b, ctypes.byref(opts) if opts is not None else None, st, ctypes.byref(out)),
+           "pgb_tc_run")
+    info = pgb_blocks_info(b)
+    return Result(out.value, st, info["n"], info["triples"])
+
+
+def pgb_tc_result_get(r: Result, per_vertex=True):
+    """(total, t) with t a numpy uint64[n] in original IDs (or None).
+
+    ``per_vertex`` may also be a CUDA uint64 tensor of length n to receive t
+    on the device (then that tensor is returned as t)."""
+    tot = ctypes.c_uint64()
+    out = None
+    ptr, mem = None, PGB_MEM_HOST
+    if per_vertex is True:
+        out = np.zeros(r.n, np.uint64)
+        ptr = out.ctypes.data if r.n else None
+    elif per_vertex is not None and per_vertex is not False:
+        ptr, mem, out = _arr(per_vertex, np.uint64)
+    _check(load().pgb_tc_result_get(r, ctypes.byref(tot), ptr, mem), "pgb_tc_result_get")
+    return int(tot.value), out
+
+
+def pgb_tc_result_triples(r: Result) -> np.ndarray:
+    out = np.zeros(r.ntriples, np.uint64)
+    _check(load().pgb_tc_result_triples(r, out.ctypes.data if r.ntriples else None, PGB_MEM_HOST),
+           "pgb_tc_result_triples")
+    return out
+
+
+def pgb_tc_result_kernel_ms(r: Result) -> float:
+    ms = ctypes.c_float()
+    _check(load().pgb_tc_result_kernel_ms(r, ctypes.byref(ms)), "pgb_tc_result_kernel_ms")
+    return float(ms.value)
+
+
+def pgb_tc_result_free(r: Result):
+    r.free()
+
+
+def pgb_tc_count_edges(src, dst, n: int, p: int, cut_rule: int = PGB_CUT_NNZ, opts: TcOpts | None = None,
+                       stream=None, per_vertex=True):
+    """One call from raw edges to (total, t).  Host arrays in -> host t out."""
+    lib = load()
+    ps, ms, ks = _arr(src, np.uint32)
+    pd, md, kd = _arr(dst, np.uint32)
+    if ms != md:
+        raise ValueError("src and dst must live in the same memory")
+    m = 0 if ks is None else int(ks.numel() if hasattr(ks, "numel") else ks.size)
+    st = _stream(stream)
+    tot = ctypes.c_uint64()
+    t = None
+    tptr = None
+    if per_vertex is True:
+        if ms == PGB_MEM_DEVICE:
+            import torch
+            t = torch.zeros(n, dtype=torch.uint64, device=ks.device)
+            tptr = t.data_ptr()
+        else:
+            t = np.zeros(n, np.uint64)
+            tptr = t.ctypes.data if n else None
+    elif per_vertex is not None and per_vertex is not False:
+        tptr, _, t = _arr(per_vertex, np.uint64)
+    rc = lib.pgb_tc_count_edges(ps, pd, m, n, p, cut_rule, ctypes.byref(opts) if opts is not None else None,
+                                ms, st, ctypes.byref(tot), tptr)
+    _check(rc, "pgb_tc_count_edges")
+    return int(tot.value), t

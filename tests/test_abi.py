@@ -1,0 +1,69 @@
+"""Host-side checks of the C ABI: the library builds, loads, exports every
+function declared in include/pgabb.h, and rejects bad arguments before
+touching the GPU.  No compute call is made here (no GPU needed)."""
+import ctypes
+import subprocess
+
+import pytest
+
+from paper_2209_04541_b300 import build, pgabb
+
+
+def test_library_exports_every_header_symbol():
+    lib = pgabb.load(register_torch_allocator=False)
+    names = pgabb.header_functions()
+    assert len(names) >= 19
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in pgabb.h but not exported"
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_covers_every_header_function():
+    names = pgabb.header_functions()
+    for name in names:
+        assert callable(getattr(pgabb, name, None)), f"binding lacks {name}"
+
+
+def test_built_for_sm103a():
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert build.up_to_date()
+
+
+def test_version_and_errors_without_gpu():
+    lib = pgabb.load(register_torch_allocator=False)
+    assert pgabb.pgb_version().startswith("pgabb-b300")
+    n = ctypes.c_uint32()
+    assert lib.pgb_graph_info(None, ctypes.byref(n), None) == pgabb.PGB_E_INVAL
+    assert "NULL" in pgabb.pgb_last_error()
+    out = ctypes.c_void_p()
+    assert lib.pgb_partition(None, 4, 0, None, ctypes.byref(out)) == pgabb.PGB_E_INVAL
+    assert lib.pgb_tc_run(None, None, None, ctypes.byref(out)) == pgabb.PGB_E_INVAL
+    assert lib.pgb_graph_from_edges(None, None, 5, 10, 0, None, ctypes.byref(out)) == pgabb.PGB_E_INVAL
+    assert lib.pgb_graph_from_edges(None, None, 0, 10, 7, None, ctypes.byref(out)) == pgabb.PGB_E_INVAL
+    assert lib.pgb_tc_result_get(None, None, None, 0) == pgabb.PGB_E_INVAL
+    # freeing NULL handles is a no-op
+    lib.pgb_graph_free(None)
+    lib.pgb_blocks_free(None)
+    lib.pgb_tc_result_free(None)
+
+
+def test_opts_default():
+    o = pgabb.pgb_tc_opts_default()
+    assert o.mode == pgabb.PGB_MODE_PERSISTENT
+    assert o.variant == pgabb.PGB_VAR_AUTO
+    assert o.per_vertex == 1 and o.per_triple == 0 and o.use_graph == 0
+    assert o.device_budget == 0
+    assert ctypes.sizeof(pgabb.TcOpts) == 64
+    assert ctypes.sizeof(pgabb.BlocksStats) == 56
+    with pytest.raises(AttributeError):
+        pgabb.pgb_tc_opts_default(bogus=1)
+
+
+def test_allocator_pairing_checked():
+    lib = pgabb.load(register_torch_allocator=False)
+    fa = pgabb._ALLOC_FN(lambda size, stream, ctx: None)
+    ff = ctypes.cast(None, pgabb._FREE_FN)
+    assert lib.pgb_set_allocator(fa, ff, None) == pgabb.PGB_E_INVAL
