@@ -225,6 +225,40 @@ int pgb_tc_count_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, uin
                        int cut_rule, const pgb_tc_opts* opts, int mem, void* stream, uint64_t* total,
                        uint64_t* per_vertex);
 
+/* ------------------------------------------------- no-allocation count */
+/* The paper has no counterpart to this call.  It is for callers that must
+ * not allocate device memory while they run: code whose host framework
+ * hands out all device memory from its own pool and forbids any other
+ * allocation, and latency-critical loops that cannot take the device-wide
+ * synchronisation cudaMalloc / cudaFree may cause.  It allocates nothing:
+ * no cudaMalloc, no cudaFree, no allocator callback.  Its working memory (a
+ * work cursor, per-CTA partial counts and a per-vertex accumulator of
+ * PGB_NOALLOC_MAX_VERTICES entries, about 8 MiB) is one fixed device array
+ * inside the library, held on every GPU that loads the library until the
+ * process exits.
+ *
+ * Input: an already degree-ordered, upper-oriented graph in device memory
+ * (e.g. from PGB_EXPORT_ROWPTR narrowed to uint32 and PGB_EXPORT_COL):
+ *   rowptr uint32[n+1] with rowptr[0] = 0 and rowptr[n] = m; col uint32[m]
+ *   with row u listing its out-neighbours, all > u, ascending;
+ *   perm   uint32[n] rank -> original ID, or NULL to index output by rank.
+ * Output (device memory, written, not accumulated): total uint64[1];
+ *   per_vertex uint64[n] or NULL.
+ * Counts equal those of pgb_tc_run on the same graph.
+ * The call returns after the work on `stream` has finished.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) for
+ * that device; make that first call before any stream capture begins.
+ * Every call on a device shares the one array and clears what it needs at
+ * the start, so calls whose work overlaps on the GPU (other streams or
+ * threads) race and give wrong counts: serialise them.
+ * Errors: PGB_E_INVAL (n > PGB_NOALLOC_MAX_VERTICES, NULL pointers,
+ * malformed offsets, columns or perm, detected on the device),
+ * PGB_E_OVERFLOW (m >= 2^32), PGB_E_CUDA. */
+#define PGB_NOALLOC_MAX_VERTICES (1u << 20)
+int pgb_tc_count_oriented_noalloc(uint32_t n, uint64_t m, const uint32_t* rowptr, const uint32_t* col,
+                                  const uint32_t* perm, unsigned long long* total,
+                                  unsigned long long* per_vertex, void* stream);
+
 /* ----------------------------------------------------------------- misc */
 const char* pgb_last_error(void);   /* thread-local; never NULL */
 const char* pgb_version(void);

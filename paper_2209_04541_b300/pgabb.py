@@ -112,7 +112,11 @@ _SIGS = {
     "pgb_last_error": (ctypes.c_char_p, []),
     "pgb_version": (ctypes.c_char_p, []),
     "pgb_kernel_launches": (ctypes.c_uint64, []),
+    "pgb_tc_count_oriented_noalloc": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, _VP, _VP, _VP, _VP, _VP,
+                                                     _VP]),
 }
+
+PGB_NOALLOC_MAX_VERTICES = 1 << 20
 
 
 def header_functions() -> list[str]:
@@ -430,3 +434,21 @@ def pgb_tc_count_edges(src, dst, n: int, p: int, cut_rule: int = PGB_CUT_NNZ, op
                                 ms, st, ctypes.byref(tot), tptr)
     _check(rc, "pgb_tc_count_edges")
     return int(tot.value), t
+
+
+def pgb_tc_count_oriented_noalloc(n: int, m: int, rowptr, col, perm, total, per_vertex=None, stream=None):
+    """Allocation-free count over an oriented graph already in device memory.
+
+    ``rowptr`` (uint32[n+1]), ``col`` (uint32[m]), ``perm`` (uint32[n] or
+    None), ``total`` (uint64[1]) and ``per_vertex`` (uint64[n] or None) are
+    CUDA tensors; results are written into ``total`` and ``per_vertex``.
+    For callers that may not allocate device memory during the call; see
+    include/pgabb.h for the limits and the sharing rules."""
+    args = []
+    for x, dt in ((rowptr, np.uint32), (col, np.uint32), (perm, np.uint32), (total, np.uint64),
+                  (per_vertex, np.uint64)):
+        ptr, mem, _ = _arr(x, dt)
+        if x is not None and mem != PGB_MEM_DEVICE:
+            raise ValueError("pgb_tc_count_oriented_noalloc takes device tensors only")
+        args.append(ptr)
+    _check(load().pgb_tc_count_oriented_noalloc(n, m, *args, _stream(stream)), "pgb_tc_count_oriented_noalloc")
