@@ -85,11 +85,14 @@ def measured_peaks():
         return 6400.0, "of fallback"
 
 
+KERNEL_SOURCE = {"k_tc_hash": "tc_hash.cu", "k_tc_persistent": "tc.cu", "k_tc_tuple": "tc.cu"}
+
+
 def kernel_traffic(kernel: str, workload: str):
     """Per-launch DRAM bytes from the committed ncu summary for this kernel
     and workload, or None when absent or taken on an older kernel source."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
-    src = os.path.join(ROOT, "paper_2209_04541_b300", "csrc", "tc.cu")
+    src = os.path.join(ROOT, "paper_2209_04541_b300", "csrc", KERNEL_SOURCE.get(kernel, "tc.cu"))
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -219,6 +222,7 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat24")
     ap.add_argument("--mode", choices=["persistent", "plain"], default="persistent")
     ap.add_argument("--order", choices=["weight", "locality"], default="weight")
+    ap.add_argument("--variant", choices=["auto", "bsearch", "hash"], default="auto")
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--per-vertex", type=int, default=1)
     ap.add_argument("--p", type=int, default=0, help="override the workload's p")
@@ -259,7 +263,8 @@ def main(argv=None):
     tv = torch.zeros(n, dtype=torch.uint64, device="cuda")
     P.load()
     mode = P.PGB_MODE_PERSISTENT if args.mode == "persistent" else P.PGB_MODE_PLAIN
-    opts = P.pgb_tc_opts_default(mode=mode, per_vertex=args.per_vertex, chunk_edges=args.chunk,
+    variant = {"auto": P.PGB_VAR_AUTO, "bsearch": P.PGB_VAR_BSEARCH, "hash": P.PGB_VAR_HASH}[args.variant]
+    opts = P.pgb_tc_opts_default(mode=mode, per_vertex=args.per_vertex, chunk_edges=args.chunk, variant=variant,
                                  order=P.PGB_ORDER_WEIGHT if args.order == "weight" else P.PGB_ORDER_LOCALITY)
     info = {}
 
@@ -311,7 +316,10 @@ def main(argv=None):
 
     kernel_ms = statistics.mean(kms_all)
     peak, peak_note = measured_peaks()
-    kname = "k_tc_persistent" if mode == P.PGB_MODE_PERSISTENT else "k_tc_tuple"
+    if mode == P.PGB_MODE_PLAIN:
+        kname = "k_tc_tuple"
+    else:
+        kname = "k_tc_persistent" if variant == P.PGB_VAR_BSEARCH else "k_tc_hash"
     achieved = info["alg_bytes"] / (kernel_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_note, "alg_bytes": info["alg_bytes"],
@@ -343,6 +351,7 @@ def main(argv=None):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                 "config": {"workload": w["desc"], "name": args.workload, "p": w["p"], "mode": args.mode,
+                           "variant": args.variant, "kernel": kname,
                            "order": args.order, "per_vertex": bool(args.per_vertex), "n": n,
                            "raw_edges": mraw, "unique_edges": m_u, "triangles": T,
                            "wedges": info["wedges"], "triples": info["triples"],

@@ -149,6 +149,8 @@ struct pgb_blocks {
     pgb::DevBuf<uint32_t> col;     // m oriented columns, rank space, rows sorted
     pgb::DevBuf<uint32_t> rowidx;  // m row of each oriented edge
     pgb::DevBuf<uint32_t> bedge;   // m CSR edge positions grouped by block (i, j) row-major
+    pgb::DevBuf<uint32_t> colptr;  // n + 1 first in-edge of each head v (in-edge index order)
+    pgb::DevBuf<unsigned long long> xr;  // m in-edges grouped by head: tail-row range after v
     pgb::DevBuf<uint32_t> cuts_d;  // p + 1
     std::vector<uint32_t> cuts;    // p + 1
     std::vector<uint64_t> block_edges;  // p * p

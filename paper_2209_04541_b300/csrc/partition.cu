@@ -50,22 +50,43 @@ __global__ void k_orient_keys(const uint64_t* __restrict__ keys, uint64_t m, uin
     }
 }
 
-// Unpack sorted oriented keys into COO rows / CSR columns and write every
-// rowptr entry exactly once: rowptr[r] = first edge whose row is >= r.
-__global__ void k_unpack_csr(const uint64_t* __restrict__ okeys, uint64_t m, uint32_t n, uint32_t B,
-                             uint32_t* __restrict__ rowidx, uint32_t* __restrict__ col,
-                             uint32_t* __restrict__ rowptr) {
+// Unpack sorted oriented keys into COO rows and CSR columns.
+__global__ void k_unpack_csr(const uint64_t* __restrict__ okeys, uint64_t m, uint32_t B,
+                             uint32_t* __restrict__ rowidx, uint32_t* __restrict__ col) {
     const uint64_t mask = (1ull << B) - 1;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         uint64_t k = okeys[e];
-        uint32_t u = (uint32_t)(k >> B);
-        rowidx[e] = u;
+        rowidx[e] = (uint32_t)(k >> B);
         col[e] = (uint32_t)(k & mask);
-        uint32_t prev = (e == 0) ? 0 : (uint32_t)(okeys[e - 1] >> B) + 1;
-        for (uint32_t r = prev; r <= u; ++r) rowptr[r] = (uint32_t)e;
-        if (e == m - 1)
-            for (uint32_t r = u + 1; r <= n; ++r) rowptr[r] = (uint32_t)m;
+    }
+}
+
+// Offsets of a sorted key array: off[r] = first position whose key is >= r,
+// for r in [0, n] (one binary search per entry, so runs of empty rows cost
+// nothing extra).
+__global__ void k_offsets_from_sorted(const uint32_t* __restrict__ keys, uint64_t m, uint32_t n,
+                                      uint32_t* __restrict__ off) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= n; r += stride) {
+        uint64_t lo = 0, hi = m;
+        while (lo < hi) {
+            uint64_t mid = (lo + hi) >> 1;
+            if (keys[mid] < r) lo = mid + 1; else hi = mid;
+        }
+        off[r] = (uint32_t)lo;
+    }
+}
+
+// In-edge descriptors: for the edge u -> v at CSR position e, the range of
+// u's row after v, packed as (e + 1) | (rowptr[u + 1] << 32).
+__global__ void k_in_ranges(const uint32_t* __restrict__ eidx, uint64_t m, const uint32_t* __restrict__ rowidx,
+                            const uint32_t* __restrict__ rowptr, unsigned long long* __restrict__ xr) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        uint32_t e = eidx[i];
+        uint32_t xe = rowptr[rowidx[e] + 1];
+        xr[i] = (unsigned long long)(e + 1) | ((unsigned long long)xe << 32);
     }
 }
 
@@ -247,8 +268,10 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
         PGB_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp, db, (int64_t)m, 0, (int)(2 * B), s));
         void* t = scratch.get(tmp, s);
         PGB_CUDA(cub::DeviceRadixSort::SortKeys(t, tmp, db, (int64_t)m, 0, (int)(2 * B), s));
-        k_unpack_csr<<<grid_for(m), 256, 0, s>>>(db.Current(), m, n, B, b->rowidx.ptr, b->col.ptr, b->rowptr.ptr);
+        k_unpack_csr<<<grid_for(m), 256, 0, s>>>(db.Current(), m, B, b->rowidx.ptr, b->col.ptr);
         PGB_CHECK_LAUNCH("k_unpack_csr");
+        k_offsets_from_sorted<<<grid_for((uint64_t)n + 1), 256, 0, s>>>(b->rowidx.ptr, m, n, b->rowptr.ptr);
+        PGB_CHECK_LAUNCH("k_offsets_from_sorted");
     } else {
         k_fill_u32<<<grid_for((uint64_t)n + 1), 256, 0, s>>>(b->rowptr.ptr, (uint64_t)n + 1, 0);
         PGB_CHECK_LAUNCH("k_fill_u32");
@@ -312,6 +335,27 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
             if (vo != b->bedge.ptr)
                 PGB_CUDA(cudaMemcpyAsync(b->bedge.ptr, vo, m * 4, cudaMemcpyDeviceToDevice, s));
         }
+    }
+
+    // --- in-edge index for the middle-vertex variant: edges grouped by head
+    // v (stable radix sort, so tails ascend within a head), colptr[v] = first
+    // in-edge of v, xr = the tail's row range after v
+    b->colptr.alloc((size_t)n + 1, s);
+    b->xr.alloc(m, s);
+    if (m > 0) {
+        DevBuf<uint32_t> kc(m, s), kalt(m, s), vals(m, s), valt(m, s);
+        PGB_CUDA(cudaMemcpyAsync(kc.ptr, b->col.ptr, m * 4, cudaMemcpyDeviceToDevice, s));
+        k_iota<<<grid_for(m), 256, 0, s>>>(vals.ptr, m);
+        PGB_CHECK_LAUNCH("k_iota");
+        uint32_t *ko, *vo;
+        sort_pairs(kc.ptr, kalt.ptr, vals.ptr, valt.ptr, m, num_bits(n > 0 ? n - 1 : 0), s, scratch, &ko, &vo);
+        k_offsets_from_sorted<<<grid_for((uint64_t)n + 1), 256, 0, s>>>(ko, m, n, b->colptr.ptr);
+        PGB_CHECK_LAUNCH("k_offsets_from_sorted");
+        k_in_ranges<<<grid_for(m), 256, 0, s>>>(vo, m, b->rowidx.ptr, b->rowptr.ptr, b->xr.ptr);
+        PGB_CHECK_LAUNCH("k_in_ranges");
+    } else {
+        k_fill_u32<<<grid_for((uint64_t)n + 1), 256, 0, s>>>(b->colptr.ptr, (uint64_t)n + 1, 0);
+        PGB_CHECK_LAUNCH("k_fill_u32");
     }
     PGB_CUDA(cudaStreamSynchronize(s));
     b->wedges = hw;

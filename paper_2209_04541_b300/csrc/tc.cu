@@ -19,6 +19,7 @@
 #include <memory>
 
 #include "internal.cuh"
+#include "tc_hash.cuh"
 
 namespace pgb {
 
@@ -341,6 +342,10 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o, cudaStream_t s, pgb_t
             k_reduce_segments<<<(unsigned)T, 256, 0, s>>>(partials.ptr, dseg.ptr, r->triple_counts.ptr);
             PGB_CHECK_LAUNCH("k_reduce_segments");
         }
+    } else if (o.variant != PGB_VAR_BSEARCH) {
+        // middle-vertex hash variant (tc_hash.cu)
+        HashGraph H{b->rowptr.ptr, b->col.ptr, b->rowidx.ptr, b->colptr.ptr, b->xr.ptr, tv.ptr};
+        run_hash(b, H, r->per_vertex, s, partials, npartials, r->ev0, r->ev1, nullptr);
     } else {
         // tuples (A_ij, A_i[j..p-1], A_j[j..p-1]): one per non-empty block
         // pair on the queue, ordered by the summed weight of its triples
@@ -426,6 +431,9 @@ int pgb_tc_run(const pgb_blocks* b, const pgb_tc_opts* opts, void* stream, pgb_t
         if (opts) o = *opts; else pgb_tc_opts_default(&o);
         if (o.mode != PGB_MODE_PLAIN && o.mode != PGB_MODE_PERSISTENT) fail(PGB_E_INVAL, "bad mode");
         if (o.variant < PGB_VAR_AUTO || o.variant > PGB_VAR_HASH) fail(PGB_E_INVAL, "bad variant");
+        if (o.variant == PGB_VAR_MERGE) fail(PGB_E_INVAL, "the merge variant is not available in this build");
+        if (o.mode == PGB_MODE_PLAIN && o.variant == PGB_VAR_HASH)
+            fail(PGB_E_INVAL, "PLAIN mode runs the binary-search variant only");
         if (o.order != PGB_ORDER_WEIGHT && o.order != PGB_ORDER_LOCALITY) fail(PGB_E_INVAL, "bad order");
         std::unique_ptr<pgb_tc_result> r(new pgb_tc_result());
         run(b, o, (cudaStream_t)stream, r.get());

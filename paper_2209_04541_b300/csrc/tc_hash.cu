@@ -1,0 +1,429 @@
+// Middle-vertex shared-memory hash variant of the block-tuple kernel
+// (PGAbB Section 3.6: "list or hashmap-based intersection").
+//
+// Listing "tc-dev" loops over u, then over v in N(u), intersecting u's and
+// v's partial lists.  This variant interchanges the two outer loops: a CTA
+// takes a middle vertex v (or a group of up to 32 consecutive middle
+// vertices), puts v's partial list N+(v) ∩ [lo, hi) into a shared-memory
+// hash table once, then streams every in-neighbour u's list after v and
+// looks each element up in the table.  A triangle u < v < w is found once,
+// as the element w of u's list that hits v's table.  Each lookup costs one
+// or two shared-memory loads instead of a chain of dependent global loads,
+// and u's list is read with coalesced loads.
+//
+// Work items (built on the device, heaviest middle vertices first):
+//   group item:     up to 32 consecutive ranks whose partial lists hold at
+//                   most kKeyCap entries in total and whose in-edges number
+//                   at most kInChunk; table entries carry a 32-bit mask of
+//                   the group members that own the key;
+//   singleton item: one middle vertex, a run of at most kInChunk of its
+//                   in-edges, and a slice of at most kKeyCap entries of its
+//                   list (the slice is a third-vertex rank range [lo, hi),
+//                   i.e. a narrower column-block run; both lists are clipped).
+// Per-vertex counts: a shared counter per table slot collects t[w], a
+// per-edge tally collects t[u] and t[v]; all are flushed with one global
+// atomic per (slot, item) and per in-edge instead of one per triangle.
+#include <cub/device/device_scan.cuh>
+
+#include <algorithm>
+
+#include "internal.cuh"
+#include "tc_hash.cuh"
+
+namespace pgb {
+
+namespace {
+
+constexpr int kHThreads = 256;
+constexpr int kHWarps = kHThreads / 32;
+constexpr uint32_t kKeyCap = 2048;     // table keys per item (load factor <= 1/2)
+constexpr uint32_t kInChunk = 1024;    // in-edges per item
+constexpr int kMaxSlotsLog2 = 12;      // 4096 slots
+constexpr uint32_t kMaxSlots = 1u << kMaxSlotsLog2;
+constexpr uint32_t kEmpty = 0xffffffffu;
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kUnroll = 8;             // probe rounds whose loads are issued together
+
+struct VItem {
+    uint32_t v0;        // first middle vertex (rank)
+    uint32_t nv;        // consecutive middle vertices in the item (<= 32)
+    uint32_t in_begin;  // in-edge range [in_begin, in_end) of the in-edge index
+    uint32_t in_end;
+    uint32_t lo, hi;    // third-vertex rank range
+    uint32_t slots_log2;
+    uint32_t clip;      // 1 when lists are clipped to [lo, hi)
+};
+
+__device__ __forceinline__ uint32_t hslot(uint32_t x, uint32_t log2s) { return (x * 0x9E3779B1u) >> (32 - log2s); }
+
+__device__ __forceinline__ uint32_t ceil_log2(uint32_t x) { return x <= 1 ? 0 : 32 - __clz(x - 1); }
+
+__device__ __forceinline__ uint32_t slots_for(uint32_t keys) {
+    uint32_t l = ceil_log2(2 * keys);
+    return l < 6 ? 6 : l;
+}
+
+__device__ __forceinline__ uint32_t hlower_bound(const uint32_t* __restrict__ a, uint32_t b, uint32_t e, uint32_t x) {
+    uint32_t n = e - b;
+    while (n > 0) {
+        uint32_t half = n >> 1;
+        if (__ldg(a + b + half) < x) {
+            b += half + 1;
+            n -= half + 1;
+        } else {
+            n = half;
+        }
+    }
+    return b;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFullMask, x, o);
+    return x;
+}
+
+// Item decisions for the window of 32 ranks starting at 32 * w (one warp).
+struct WindowInfo {
+    uint32_t v, dp, dm;
+    bool act;
+    uint32_t keys, ins;
+    bool group;
+    uint32_t mine;  // singleton items of this lane
+};
+
+__device__ __forceinline__ WindowInfo window_info(const uint32_t* __restrict__ rowptr,
+                                                  const uint32_t* __restrict__ colptr, uint32_t n, uint32_t w,
+                                                  int lane) {
+    WindowInfo W;
+    W.v = w * 32 + lane;
+    W.dp = W.dm = 0;
+    if (W.v < n) {
+        W.dp = rowptr[W.v + 1] - rowptr[W.v];
+        W.dm = colptr[W.v + 1] - colptr[W.v];
+    }
+    W.act = W.dp > 0 && W.dm > 0;
+    W.keys = warp_sum(W.act ? W.dp : 0);
+    W.ins = warp_sum(W.act ? W.dm : 0);
+    W.group = W.keys > 0 && W.keys <= kKeyCap && W.ins <= kInChunk;
+    W.mine = (W.act && !W.group) ? ((W.dm + kInChunk - 1) / kInChunk) * ((W.dp + kKeyCap - 1) / kKeyCap) : 0;
+    return W;
+}
+
+// counts[nwin - 1 - w] = items of window w (windows of high ranks first).
+__global__ void k_items_count(const uint32_t* __restrict__ rowptr, const uint32_t* __restrict__ colptr, uint32_t n,
+                              uint32_t nwin, uint32_t* __restrict__ counts) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwin; w += nw) {
+        WindowInfo W = window_info(rowptr, colptr, n, w, lane);
+        uint32_t c = W.keys == 0 ? 0 : (W.group ? 1 : warp_sum(W.mine));
+        if (lane == 0) counts[nwin - 1 - w] = c;
+    }
+}
+
+__global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t* __restrict__ colptr,
+                             const uint32_t* __restrict__ col, uint32_t n, uint32_t nwin,
+                             const uint32_t* __restrict__ offs, VItem* __restrict__ items) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwin; w += nw) {
+        WindowInfo W = window_info(rowptr, colptr, n, w, lane);
+        if (W.keys == 0) continue;
+        const uint32_t base = offs[nwin - 1 - w];
+        if (W.group) {
+            if (lane == 0) {
+                VItem it;
+                it.v0 = w * 32;
+                it.nv = min(32u, n - w * 32);
+                it.in_begin = colptr[it.v0];
+                it.in_end = colptr[it.v0 + it.nv];
+                it.lo = 0;
+                it.hi = n;
+                it.slots_log2 = slots_for(W.keys);
+                it.clip = 0;
+                items[base] = it;
+            }
+            continue;
+        }
+        uint32_t excl = W.mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFullMask, excl, o);
+            if (lane >= o) excl += y;
+        }
+        excl -= W.mine;
+        if (!W.mine) continue;
+        const uint32_t na = (W.dm + kInChunk - 1) / kInChunk;
+        const uint32_t nk = (W.dp + kKeyCap - 1) / kKeyCap;
+        const uint32_t rb = rowptr[W.v], cb = colptr[W.v];
+        uint32_t out = base + excl;
+        for (uint32_t a = 0; a < na; ++a) {
+            for (uint32_t kk = 0; kk < nk; ++kk) {
+                VItem it;
+                it.v0 = W.v;
+                it.nv = 1;
+                it.in_begin = cb + a * kInChunk;
+                it.in_end = min(it.in_begin + kInChunk, cb + W.dm);
+                if (nk > 1) {
+                    it.lo = col[rb + kk * kKeyCap];
+                    it.hi = (kk + 1 < nk) ? col[rb + (kk + 1) * kKeyCap] : n;
+                    it.clip = 1;
+                } else {
+                    it.lo = 0;
+                    it.hi = n;
+                    it.clip = 0;
+                }
+                it.slots_log2 = slots_for(min(kKeyCap, W.dp - kk * kKeyCap));
+                items[out++] = it;
+            }
+        }
+    }
+}
+
+template <bool PV>
+__global__ void __launch_bounds__(kHThreads, 4)
+    k_tc_hash(HashGraph G, const VItem* __restrict__ items, uint32_t nitems, unsigned int* __restrict__ cursor,
+              unsigned long long* __restrict__ partials) {
+    extern __shared__ uint32_t hsm[];
+    uint32_t* keys = hsm;
+    uint32_t* masks = hsm + kMaxSlots;
+    uint32_t* cnts = hsm + 2 * kMaxSlots;  // PV only
+    __shared__ uint32_t s_item, s_vmask, s_next;
+    __shared__ uint32_t s_edge[kHWarps][32];
+    __shared__ uint32_t s_vcnt[32];
+    __shared__ unsigned long long s_red[kHWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (PV) s_edge[warp][lane] = 0;
+    unsigned long long cnt = 0;
+    for (;;) {
+        if (tid == 0) {
+            s_item = atomicAdd(cursor, 1u);
+            s_vmask = 0;
+            s_next = 0;
+        }
+        if (PV && tid < 32) s_vcnt[tid] = 0;
+        __syncthreads();
+        const uint32_t itx = s_item;
+        if (itx >= nitems) break;
+        const VItem I = items[itx];
+        const uint32_t L = I.slots_log2, S = 1u << L, smask = S - 1;
+        const bool single = I.nv == 1;
+        for (uint32_t i = tid; i < S; i += kHThreads) {
+            keys[i] = kEmpty;
+            masks[i] = 0;
+            if (PV) cnts[i] = 0;
+        }
+        __syncthreads();
+        // build: warp t inserts the partial lists of members t, t + 8, ...
+        for (uint32_t t = warp; t < I.nv; t += kHWarps) {
+            const uint32_t v = I.v0 + t;
+            if (__ldg(G.colptr + v + 1) == __ldg(G.colptr + v)) continue;
+            uint32_t b = __ldg(G.rowptr + v), e = __ldg(G.rowptr + v + 1);
+            if (I.clip) {
+                b = hlower_bound(G.col, b, e, I.lo);
+                e = hlower_bound(G.col, b, e, I.hi);
+            }
+            if (b >= e) continue;
+            const uint32_t bit = 1u << t;
+            if (lane == 0) atomicOr(&s_vmask, bit);
+            for (uint32_t q = b + lane; q < e; q += 32) {
+                const uint32_t x = __ldg(G.col + q);
+                uint32_t h = hslot(x, L);
+                for (uint32_t probe = 0; probe < S; ++probe) {
+                    const uint32_t old = atomicCAS(&keys[h], kEmpty, x);
+                    if (old == kEmpty || old == x) {
+                        atomicOr(&masks[h], bit);
+                        break;
+                    }
+                    h = (h + 1) & smask;
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t vmask = s_vmask;
+        // probe: warps take batches of 32 in-edges from a shared counter (so a
+        // warp with short lists takes more batches), with the (in-edge,
+        // element) work of a batch flattened across the lanes
+        for (;;) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&s_next, 32u);
+            base = I.in_begin + __shfl_sync(kFullMask, base, 0);
+            if (base >= I.in_end) break;
+            const uint32_t idx = base + lane;
+            uint32_t sb = 0, sl = 0, vbit = 0, e = 0;
+            if (idx < I.in_end) {
+                const unsigned long long r = __ldg(G.xr + idx);
+                uint32_t xb = (uint32_t)r, xe = (uint32_t)(r >> 32);
+                e = xb - 1;
+                // a singleton item's in-edges all end at v0; a group's need
+                // the head read back to pick the member bit
+                const uint32_t v = single ? I.v0 : __ldg(G.col + e);
+                vbit = 1u << (v - I.v0);
+                if (vmask & vbit) {
+                    if (I.clip) {
+                        xb = hlower_bound(G.col, xb, xe, I.lo);
+                        xe = hlower_bound(G.col, xb, xe, I.hi);
+                    }
+                    sb = xb;
+                    sl = xe - xb;
+                }
+            }
+            uint32_t incl = sl;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(kFullMask, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t total = __shfl_sync(kFullMask, incl, 31);
+            const uint32_t excl = incl - sl;
+            // kUnroll rounds of 32 elements at a time: every lane issues its
+            // kUnroll list loads before the first lookup, so several loads
+            // per lane are in flight
+            for (uint32_t r0 = 0; r0 < total; r0 += 32 * kUnroll) {
+                uint32_t xs[kUnroll], os[kUnroll], bits[kUnroll];
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) {
+                    const uint32_t f = r0 + 32 * j + lane;
+                    int o = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        uint32_t ex = __shfl_sync(kFullMask, excl, o + step);
+                        if (ex <= f) o += step;
+                    }
+                    const uint32_t o_ex = __shfl_sync(kFullMask, excl, o);
+                    const uint32_t o_sb = __shfl_sync(kFullMask, sb, o);
+                    bits[j] = __shfl_sync(kFullMask, vbit, o);
+                    os[j] = o;
+                    xs[j] = f < total ? __ldg(G.col + o_sb + (f - o_ex)) : kEmpty;
+                }
+#pragma unroll
+                for (int j = 0; j < kUnroll; ++j) {
+                    const uint32_t x = xs[j];
+                    bool hit = false;
+                    uint32_t h = 0;
+                    if (x != kEmpty) {
+                        h = hslot(x, L);
+                        for (uint32_t probe = 0; probe < S; ++probe) {
+                            const uint32_t k = keys[h];
+                            if (k == x) {
+                                hit = single || (masks[h] & bits[j]);
+                                break;
+                            }
+                            if (k == kEmpty) break;
+                            h = (h + 1) & smask;
+                        }
+                    }
+                    if (hit) {
+                        ++cnt;
+                        if (PV) atomicAdd(&cnts[h], 1u);
+                    }
+                    if (PV) {
+                        // one shared add per in-edge with hits in this round:
+                        // lanes of the same owner are grouped, the lowest adds
+                        const unsigned hm = __ballot_sync(kFullMask, hit);
+                        if (hm) {
+                            const unsigned grp = __match_any_sync(kFullMask, os[j]) & hm;
+                            if (hit && (int)(__ffs(grp) - 1) == lane) atomicAdd(&s_edge[warp][os[j]], __popc(grp));
+                        }
+                    }
+                }
+            }
+            if (PV) {
+                __syncwarp();
+                const uint32_t c = s_edge[warp][lane];
+                if (c) {
+                    s_edge[warp][lane] = 0;
+                    atomicAdd(G.tv + __ldg(G.rowidx + e), (unsigned long long)c);
+                    atomicAdd(&s_vcnt[31 - __clz(vbit)], c);
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        if (PV) {
+            for (uint32_t i = tid; i < S; i += kHThreads) {
+                const uint32_t c = cnts[i];
+                if (c) atomicAdd(G.tv + keys[i], (unsigned long long)c);
+            }
+            if (tid < I.nv && s_vcnt[tid]) atomicAdd(G.tv + I.v0 + tid, (unsigned long long)s_vcnt[tid]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFullMask, cnt, o);
+    if (lane == 0) s_red[warp] = cnt;
+    __syncthreads();
+    if (warp == 0) {
+        cnt = lane < kHWarps ? s_red[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFullMask, cnt, o);
+        if (lane == 0) partials[blockIdx.x] = cnt;
+    }
+}
+
+template <bool PV>
+size_t hash_smem() {
+    return (size_t)(PV ? 3 : 2) * kMaxSlots * sizeof(uint32_t);
+}
+
+}  // namespace
+
+void run_hash(const pgb_blocks* b, const HashGraph& G, bool pv, cudaStream_t s, DevBuf<unsigned long long>& partials,
+              uint64_t& npartials, cudaEvent_t ev0, cudaEvent_t ev1, HashRunStats* stats) {
+    const uint32_t n = b->n;
+    const uint32_t nwin = (n + 31) / 32;
+    npartials = 0;
+    if (b->m == 0 || nwin == 0) {
+        PGB_CUDA(cudaEventRecord(ev0, s));
+        PGB_CUDA(cudaEventRecord(ev1, s));
+        return;
+    }
+    DevBuf<uint32_t> counts((size_t)nwin + 1, s), offs((size_t)nwin + 1, s);
+    PGB_CUDA(cudaMemsetAsync(counts.ptr + nwin, 0, 4, s));
+    const int wgrid = (int)std::min<uint64_t>(((uint64_t)nwin * 32 + 255) / 256, 148ull * 64);
+    k_items_count<<<wgrid, 256, 0, s>>>(b->rowptr.ptr, b->colptr.ptr, n, nwin, counts.ptr);
+    PGB_CHECK_LAUNCH("k_items_count");
+    Scratch scratch;
+    size_t tmp = 0;
+    PGB_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, counts.ptr, offs.ptr, (int64_t)nwin + 1, s));
+    void* t = scratch.get(tmp, s);
+    PGB_CUDA(cub::DeviceScan::ExclusiveSum(t, tmp, counts.ptr, offs.ptr, (int64_t)nwin + 1, s));
+    uint32_t nitems = 0;
+    PGB_CUDA(cudaMemcpyAsync(&nitems, offs.ptr + nwin, 4, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaStreamSynchronize(s));
+    DevBuf<VItem> items(std::max<uint32_t>(nitems, 1), s);
+    if (nitems) {
+        k_items_emit<<<wgrid, 256, 0, s>>>(b->rowptr.ptr, b->colptr.ptr, b->col.ptr, n, nwin, offs.ptr, items.ptr);
+        PGB_CHECK_LAUNCH("k_items_emit");
+    }
+    DevBuf<unsigned int> cursor(1, s);
+    PGB_CUDA(cudaMemsetAsync(cursor.ptr, 0, 4, s));
+    int dev = 0, sms = 0, per_sm = 0;
+    PGB_CUDA(cudaGetDevice(&dev));
+    PGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smem = pv ? hash_smem<true>() : hash_smem<false>();
+    if (pv) {
+        PGB_CUDA(cudaFuncSetAttribute(k_tc_hash<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_hash<true>, kHThreads, smem));
+    } else {
+        PGB_CUDA(cudaFuncSetAttribute(k_tc_hash<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        PGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_hash<false>, kHThreads, smem));
+    }
+    const int grid = std::max(1, per_sm) * sms;
+    npartials = (uint64_t)grid;
+    partials.alloc(npartials, s);
+    PGB_CUDA(cudaEventRecord(ev0, s));
+    if (pv)
+        k_tc_hash<true><<<grid, kHThreads, smem, s>>>(G, items.ptr, nitems, cursor.ptr, partials.ptr);
+    else
+        k_tc_hash<false><<<grid, kHThreads, smem, s>>>(G, items.ptr, nitems, cursor.ptr, partials.ptr);
+    PGB_CHECK_LAUNCH("k_tc_hash");
+    PGB_CUDA(cudaEventRecord(ev1, s));
+    if (stats) {
+        stats->items = nitems;
+        stats->grid = grid;
+    }
+}
+
+}  // namespace pgb

@@ -23,7 +23,7 @@ P = pgabb
 
 
 def gpu_count(src, dst, n, p, rule=P.PGB_CUT_NNZ, mode=P.PGB_MODE_PERSISTENT, per_vertex=True,
-              device=True, chunk=0, order=P.PGB_ORDER_WEIGHT, per_triple=False):
+              device=True, chunk=0, order=P.PGB_ORDER_WEIGHT, per_triple=False, variant=P.PGB_VAR_AUTO):
     if device:
         s = torch.from_numpy(np.ascontiguousarray(src, np.uint32)).cuda()
         d = torch.from_numpy(np.ascontiguousarray(dst, np.uint32)).cuda()
@@ -32,7 +32,7 @@ def gpu_count(src, dst, n, p, rule=P.PGB_CUT_NNZ, mode=P.PGB_MODE_PERSISTENT, pe
     g = P.pgb_graph_from_edges(s, d, n)
     b = P.pgb_partition(g, p, rule)
     opts = P.pgb_tc_opts_default(mode=mode, per_vertex=int(per_vertex), chunk_edges=chunk, order=order,
-                                 per_triple=int(per_triple))
+                                 per_triple=int(per_triple), variant=variant)
     r = P.pgb_tc_run(b, opts)
     T, t = P.pgb_tc_result_get(r, per_vertex=per_vertex)
     tri = P.pgb_tc_result_triples(r) if per_triple else None
@@ -193,3 +193,64 @@ def test_from_csr_matches_edges():
     b = P.pgb_partition(g, 4)
     T, t = P.pgb_tc_result_get(P.pgb_tc_run(b))
     assert T == oT and np.array_equal(t, ot)
+
+
+VARIANTS = [P.PGB_VAR_BSEARCH, P.PGB_VAR_HASH]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("per_vertex", [True, False])
+def test_persistent_variants_rmat(variant, per_vertex):
+    src, dst, n = graphgen.rmat(15, 16, 21)
+    og = oracle.clean(src, dst, n)
+    oT, ot = oracle.tc_node_iterator(og)
+    gT, gt, _, _, _ = gpu_count(src, dst, n, 8, variant=variant, per_vertex=per_vertex)
+    assert gT == oT
+    if per_vertex:
+        assert np.array_equal(gt, ot)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_persistent_variants_messy(variant):
+    for seed in range(6):
+        rng = np.random.default_rng(500 + seed)
+        n = int(rng.integers(2, 3000))
+        src, dst = messy_random(n, int(rng.integers(0, 20 * n)), rng)
+        T, t, _ = oracle_count(src, dst, n)
+        gT, gt, _, _, _ = gpu_count(src, dst, n, int(rng.integers(1, 9)), variant=variant)
+        assert gT == T and np.array_equal(gt, t)
+
+
+def test_hash_splits_heavy_middle_vertices():
+    """K_2100 plus 300 vertices each joined to clique vertices 0, 1, 2.
+
+    In degree order the clique's low members have more than 2048 higher
+    neighbours (their tables are split into key-range slices) and the middle
+    members have more than 256 in-edges (their in-edges are split into
+    chunks).  Closed form: C(2100, 3) clique triangles plus 3 per extra
+    vertex; t = C(2099, 2) on clique vertices, + 2 * 300 on 0, 1, 2, and 3 on
+    each extra vertex."""
+    from math import comb
+    k, extra = 2100, 300
+    a, b = np.triu_indices(k, 1)
+    xs = np.repeat(np.arange(k, k + extra), 3)
+    ys = np.tile(np.array([0, 1, 2]), extra)
+    src = np.concatenate([a, xs]).astype(np.uint32)
+    dst = np.concatenate([b, ys]).astype(np.uint32)
+    n = k + extra
+    want_t = np.full(n, comb(k - 1, 2), dtype=np.uint64)
+    want_t[:3] += 2 * extra
+    want_t[k:] = 3
+    for variant in VARIANTS:
+        for p in (1, 5):
+            gT, gt, _, _, _ = gpu_count(src, dst, n, p, variant=variant)
+            assert gT == comb(k, 3) + 3 * extra
+            assert np.array_equal(gt, want_t)
+
+
+def test_plain_mode_rejects_hash_and_merge_is_unavailable():
+    src, dst, n = graphgen.rmat(8, 8, 1)
+    with pytest.raises(P.PgbError):
+        gpu_count(src, dst, n, 2, mode=P.PGB_MODE_PLAIN, variant=P.PGB_VAR_HASH)
+    with pytest.raises(P.PgbError):
+        gpu_count(src, dst, n, 2, variant=P.PGB_VAR_MERGE)
