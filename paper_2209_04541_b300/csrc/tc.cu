@@ -344,7 +344,7 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o, cudaStream_t s, pgb_t
         }
     } else if (o.variant != PGB_VAR_BSEARCH) {
         // middle-vertex hash variant (tc_hash.cu)
-        HashGraph H{b->rowptr.ptr, b->col.ptr, b->rowidx.ptr, b->colptr.ptr, b->xr.ptr, tv.ptr};
+        HashGraph H{b->rowptr.ptr, b->col.ptr, b->rowidx.ptr, b->colptr.ptr, b->xr.ptr, tv.ptr, b->n};
         run_hash(b, H, r->per_vertex, s, partials, npartials, r->ev0, r->ev1, nullptr);
     } else {
         // tuples (A_ij, A_i[j..p-1], A_j[j..p-1]): one per non-empty block

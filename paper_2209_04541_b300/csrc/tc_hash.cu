@@ -42,7 +42,9 @@ constexpr int kMaxSlotsLog2 = 12;      // 4096 slots
 constexpr uint32_t kMaxSlots = 1u << kMaxSlotsLog2;
 constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr unsigned kFullMask = 0xffffffffu;
-constexpr int kUnroll = 8;             // probe rounds whose loads are issued together
+constexpr int kUnroll = 4;             // 16-byte quad loads per lane issued together
+constexpr uint32_t kRegionA = 2 * kMaxSlots;        // words: hash keys + masks, or a bitmap
+constexpr uint32_t kBitmapBits = 32 * kRegionA;    // widest third-vertex range held as a bitmap
 
 struct VItem {
     uint32_t v0;        // first middle vertex (rank)
@@ -81,6 +83,35 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFullMask, x, o);
     return x;
+}
+
+// Insert x into the open-addressing table (linear probing) and set `bit` in
+// its member mask.  The table is never more than half full, so a free slot
+// is always found.
+__device__ __forceinline__ void table_insert(uint32_t* keys, uint32_t* masks, uint32_t x, uint32_t bit, uint32_t L) {
+    const uint32_t smask = (1u << L) - 1;
+    uint32_t h = hslot(x, L);
+    for (uint32_t probe = 0; probe <= smask; ++probe) {
+        const uint32_t old = atomicCAS(&keys[h], kEmpty, x);
+        if (old == kEmpty || old == x) {
+            if (bit) atomicOr(&masks[h], bit);
+            return;
+        }
+        h = (h + 1) & smask;
+    }
+}
+
+// Slot of x in the table, or kEmpty when x is absent.
+__device__ __forceinline__ uint32_t table_find(const uint32_t* keys, uint32_t x, uint32_t L) {
+    const uint32_t smask = (1u << L) - 1;
+    uint32_t h = hslot(x, L);
+    for (uint32_t probe = 0; probe <= smask; ++probe) {
+        const uint32_t k = keys[h];
+        if (k == x) return h;
+        if (k == kEmpty) return kEmpty;
+        h = (h + 1) & smask;
+    }
+    return kEmpty;
 }
 
 // Item decisions for the window of 32 ranks starting at 32 * w (one warp).
@@ -182,69 +213,93 @@ __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t
 }
 
 template <bool PV>
-__global__ void __launch_bounds__(kHThreads, 4)
+__global__ void __launch_bounds__(kHThreads, 3)
     k_tc_hash(HashGraph G, const VItem* __restrict__ items, uint32_t nitems, unsigned int* __restrict__ cursor,
               unsigned long long* __restrict__ partials) {
     extern __shared__ uint32_t hsm[];
-    uint32_t* keys = hsm;
-    uint32_t* masks = hsm + kMaxSlots;
-    uint32_t* cnts = hsm + 2 * kMaxSlots;  // PV only
+    // Region A: the bitmap of a bitmap-mode item, or the keys and member
+    // masks of a hash-mode item; all zero between items.  Region B (per-vertex
+    // counts only): keys and counters that index t[w] by table slot.
+    uint32_t* regA = hsm;
+    uint32_t* regB = hsm + kRegionA;
+    __shared__ VItem s_it;
     __shared__ uint32_t s_item, s_vmask, s_next;
     __shared__ uint32_t s_edge[kHWarps][32];
     __shared__ uint32_t s_vcnt[32];
     __shared__ unsigned long long s_red[kHWarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint32_t i = tid; i < kRegionA; i += kHThreads) regA[i] = 0;
     if (PV) s_edge[warp][lane] = 0;
+    // thread 0 keeps the next item (index and descriptor) fetched ahead
+    uint32_t pending = 0;
+    VItem pit{};
+    if (tid == 0) {
+        pending = atomicAdd(cursor, 1u);
+        if (pending < nitems) pit = items[pending];
+    }
     unsigned long long cnt = 0;
     for (;;) {
         if (tid == 0) {
-            s_item = atomicAdd(cursor, 1u);
+            s_item = pending;
+            s_it = pit;
             s_vmask = 0;
             s_next = 0;
         }
         if (PV && tid < 32) s_vcnt[tid] = 0;
         __syncthreads();
-        const uint32_t itx = s_item;
-        if (itx >= nitems) break;
-        const VItem I = items[itx];
-        const uint32_t L = I.slots_log2, S = 1u << L, smask = S - 1;
+        if (s_item >= nitems) break;
+        const VItem I = s_it;
         const bool single = I.nv == 1;
-        for (uint32_t i = tid; i < S; i += kHThreads) {
-            keys[i] = kEmpty;
-            masks[i] = 0;
-            if (PV) cnts[i] = 0;
-        }
+        // third-vertex range of the item: a singleton's partner entries all
+        // exceed v, so its range starts at v + 1
+        const uint32_t rlo = I.clip ? I.lo : (single ? I.v0 + 1 : 0);
+        const uint32_t rhi = I.clip ? I.hi : G.n;
+        const bool bitmap = single && rhi - rlo <= kBitmapBits;
+        const uint32_t L = I.slots_log2, S = 1u << L;
+        uint32_t* keys = bitmap ? regB : regA;
+        uint32_t* masks = regA + kMaxSlots;
+        uint32_t* cnts = regB + kMaxSlots;
+        if (!bitmap || PV)
+            for (uint32_t i = tid; i < S; i += kHThreads) keys[i] = kEmpty;
+        if (PV)
+            for (uint32_t i = tid; i < S; i += kHThreads) cnts[i] = 0;
         __syncthreads();
-        // build: warp t inserts the partial lists of members t, t + 8, ...
-        for (uint32_t t = warp; t < I.nv; t += kHWarps) {
-            const uint32_t v = I.v0 + t;
-            if (__ldg(G.colptr + v + 1) == __ldg(G.colptr + v)) continue;
-            uint32_t b = __ldg(G.rowptr + v), e = __ldg(G.rowptr + v + 1);
+        // build: a singleton's list is inserted by the whole CTA (bitmap bits,
+        // plus table keys for per-vertex counts); a group's members are
+        // spread over the warps (member t to warp t mod 8)
+        uint32_t rb = 0, re = 0;
+        if (single) {
+            rb = __ldg(G.rowptr + I.v0);
+            re = __ldg(G.rowptr + I.v0 + 1);
             if (I.clip) {
-                b = hlower_bound(G.col, b, e, I.lo);
-                e = hlower_bound(G.col, b, e, I.hi);
+                rb = hlower_bound(G.col, rb, re, I.lo);
+                re = hlower_bound(G.col, rb, re, I.hi);
             }
-            if (b >= e) continue;
-            const uint32_t bit = 1u << t;
-            if (lane == 0) atomicOr(&s_vmask, bit);
-            for (uint32_t q = b + lane; q < e; q += 32) {
+            if (tid == 0 && rb < re) s_vmask = 1u;
+            for (uint32_t q = rb + tid; q < re; q += kHThreads) {
                 const uint32_t x = __ldg(G.col + q);
-                uint32_t h = hslot(x, L);
-                for (uint32_t probe = 0; probe < S; ++probe) {
-                    const uint32_t old = atomicCAS(&keys[h], kEmpty, x);
-                    if (old == kEmpty || old == x) {
-                        atomicOr(&masks[h], bit);
-                        break;
-                    }
-                    h = (h + 1) & smask;
-                }
+                if (bitmap) atomicOr(&regA[(x - rlo) >> 5], 1u << ((x - rlo) & 31));
+                if (!bitmap || PV) table_insert(keys, masks, x, 0u, L);
+            }
+        } else {
+            for (uint32_t t = warp; t < I.nv; t += kHWarps) {
+                const uint32_t v = I.v0 + t;
+                if (__ldg(G.colptr + v + 1) == __ldg(G.colptr + v)) continue;
+                const uint32_t b = __ldg(G.rowptr + v), e = __ldg(G.rowptr + v + 1);
+                if (b >= e) continue;
+                const uint32_t bit = 1u << t;
+                if (lane == 0) atomicOr(&s_vmask, bit);
+                for (uint32_t q = b + lane; q < e; q += 32) table_insert(keys, masks, __ldg(G.col + q), bit, L);
             }
         }
         __syncthreads();
+        if (tid == 0) {
+            pending = atomicAdd(cursor, 1u);
+            if (pending < nitems) pit = items[pending];
+        }
         const uint32_t vmask = s_vmask;
         // probe: warps take batches of 32 in-edges from a shared counter (so a
-        // warp with short lists takes more batches), with the (in-edge,
-        // element) work of a batch flattened across the lanes
+        // warp with short lists takes more batches)
         for (;;) {
             uint32_t base = 0;
             if (lane == 0) base = atomicAdd(&s_next, 32u);
@@ -269,19 +324,25 @@ __global__ void __launch_bounds__(kHThreads, 4)
                     sl = xe - xb;
                 }
             }
-            uint32_t incl = sl;
+            // The lists of the batch, cut into aligned 4-entry quads, form one
+            // sequence that the lanes share: each lane takes kUnroll quads
+            // per step with one 16-byte load each, so many loads per lane are
+            // in flight across in-edge boundaries, and the owner lookup is paid
+            // once per 4 entries.
+            const uint32_t qa = sb >> 2;
+            const uint32_t nq = sl ? ((sb + sl + 3) >> 2) - qa : 0;
+            uint32_t incl = nq;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 uint32_t y = __shfl_up_sync(kFullMask, incl, o);
                 if (lane >= o) incl += y;
             }
             const uint32_t total = __shfl_sync(kFullMask, incl, 31);
-            const uint32_t excl = incl - sl;
-            // kUnroll rounds of 32 elements at a time: every lane issues its
-            // kUnroll list loads before the first lookup, so several loads
-            // per lane are in flight
+            const uint32_t excl = incl - nq;
+            const uint32_t send = sb + sl;
             for (uint32_t r0 = 0; r0 < total; r0 += 32 * kUnroll) {
-                uint32_t xs[kUnroll], os[kUnroll], bits[kUnroll];
+                uint4 qv[kUnroll];
+                uint32_t qb[kUnroll], lo_[kUnroll], hi_[kUnroll], bits[kUnroll], own[kUnroll];
 #pragma unroll
                 for (int j = 0; j < kUnroll; ++j) {
                     const uint32_t f = r0 + 32 * j + lane;
@@ -292,40 +353,53 @@ __global__ void __launch_bounds__(kHThreads, 4)
                         if (ex <= f) o += step;
                     }
                     const uint32_t o_ex = __shfl_sync(kFullMask, excl, o);
-                    const uint32_t o_sb = __shfl_sync(kFullMask, sb, o);
+                    lo_[j] = __shfl_sync(kFullMask, sb, o);
+                    hi_[j] = __shfl_sync(kFullMask, send, o);
                     bits[j] = __shfl_sync(kFullMask, vbit, o);
-                    os[j] = o;
-                    xs[j] = f < total ? __ldg(G.col + o_sb + (f - o_ex)) : kEmpty;
+                    own[j] = o;
+                    qb[j] = 4 * ((lo_[j] >> 2) + (f - o_ex));
+                    qv[j] = f < total ? __ldg(reinterpret_cast<const uint4*>(G.col + qb[j]))
+                                      : make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+                    if (f >= total) hi_[j] = 0;
                 }
 #pragma unroll
                 for (int j = 0; j < kUnroll; ++j) {
-                    const uint32_t x = xs[j];
-                    bool hit = false;
-                    uint32_t h = 0;
-                    if (x != kEmpty) {
-                        h = hslot(x, L);
-                        for (uint32_t probe = 0; probe < S; ++probe) {
-                            const uint32_t k = keys[h];
-                            if (k == x) {
-                                hit = single || (masks[h] & bits[j]);
-                                break;
-                            }
-                            if (k == kEmpty) break;
-                            h = (h + 1) & smask;
+                    const uint32_t xv[4] = {qv[j].x, qv[j].y, qv[j].z, qv[j].w};
+                    uint32_t h4 = 0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const uint32_t p = qb[j] + i;
+                        if (p < lo_[j] || p >= hi_[j]) continue;
+                        const uint32_t x = xv[i];
+                        bool hit;
+                        uint32_t h = 0;
+                        if (bitmap) {
+                            const uint32_t d = x - rlo;
+                            hit = (regA[d >> 5] >> (d & 31)) & 1u;
+                            if (PV && hit) h = table_find(keys, x, L);
+                        } else {
+                            h = table_find(keys, x, L);
+                            hit = h != kEmpty && (single || (masks[h] & bits[j]));
+                        }
+                        if (hit) {
+                            ++h4;
+                            if (PV) atomicAdd(&cnts[h], 1u);
                         }
                     }
-                    if (hit) {
-                        ++cnt;
-                        if (PV) atomicAdd(&cnts[h], 1u);
-                    }
+                    cnt += h4;
                     if (PV) {
-                        // one shared add per in-edge with hits in this round:
-                        // lanes of the same owner are grouped, the lowest adds
-                        const unsigned hm = __ballot_sync(kFullMask, hit);
-                        if (hm) {
-                            const unsigned grp = __match_any_sync(kFullMask, os[j]) & hm;
-                            if (hit && (int)(__ffs(grp) - 1) == lane) atomicAdd(&s_edge[warp][os[j]], __popc(grp));
+                        // per-in-edge tally: lanes of one owner are consecutive;
+                        // a segmented sum leaves each owner's total on its last
+                        // lane, which adds it to the owner's shared slot
+                        const unsigned same = __match_any_sync(kFullMask, own[j]);
+                        uint32_t acc = h4;
+                        const int first = __ffs(same) - 1;
+#pragma unroll
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const uint32_t y = __shfl_up_sync(kFullMask, acc, d);
+                            if (lane - d >= first) acc += y;
                         }
+                        if (lane == 31 - __clz(same) && acc) atomicAdd(&s_edge[warp][own[j]], acc);
                     }
                 }
             }
@@ -348,6 +422,15 @@ __global__ void __launch_bounds__(kHThreads, 4)
             }
             if (tid < I.nv && s_vcnt[tid]) atomicAdd(G.tv + I.v0 + tid, (unsigned long long)s_vcnt[tid]);
         }
+        // leave region A all zero for the next item
+        if (bitmap) {
+            for (uint32_t q = rb + tid; q < re; q += kHThreads) regA[(__ldg(G.col + q) - rlo) >> 5] = 0;
+        } else {
+            for (uint32_t i = tid; i < S; i += kHThreads) {
+                regA[i] = 0;
+                masks[i] = 0;
+            }
+        }
         __syncthreads();
     }
 #pragma unroll
@@ -364,7 +447,7 @@ __global__ void __launch_bounds__(kHThreads, 4)
 
 template <bool PV>
 size_t hash_smem() {
-    return (size_t)(PV ? 3 : 2) * kMaxSlots * sizeof(uint32_t);
+    return (size_t)(kRegionA + (PV ? 2 * kMaxSlots : 0)) * sizeof(uint32_t);
 }
 
 }  // namespace

@@ -12,6 +12,7 @@ struct HashGraph {
     const uint32_t* __restrict__ colptr;
     const unsigned long long* __restrict__ xr;
     unsigned long long* __restrict__ tv;  // per-vertex counts, rank space (may be null)
+    uint32_t n;                           // vertices
 };
 
 struct HashRunStats {

@@ -35,7 +35,10 @@ def load_golden(path):
 
 
 def golden_files():
-    return sorted(glob.glob(os.path.join(GOLDEN_DIR, "*.txt")))
+    """Small hand-derived fixtures (the oracle-written full-size files,
+    ``full_*.txt``, have their own loader)."""
+    return sorted(p for p in glob.glob(os.path.join(GOLDEN_DIR, "*.txt"))
+                  if not os.path.basename(p).startswith("full_"))
 
 
 def edges_to_arrays(edges):

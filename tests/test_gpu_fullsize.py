@@ -1,0 +1,61 @@
+"""Full-size parity: the CUDA path on the benchmark's own workloads.
+
+Expected values come from the oracle only, written by
+``tests/golden/make_golden.py`` into ``tests/golden/full_<name>.txt``: the
+exact triangle total and t[x] for a seeded vertex sample (the highest-degree
+vertices plus uniform draws).  The checks are bit-exact (tolerance 0):
+total, every sampled per-vertex count, and sum(t) = 3 T over all n vertices.
+
+R-MAT scale 20 (p = 16) runs in the plain one-launch-per-triple mode and in
+the persistent mode; R-MAT scale 24 (p = 32) runs in the launch
+configuration bench.py times (persistent, automatic variant, per-vertex).
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import graphgen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2209_04541_b300 import pgabb as P  # noqa: E402
+
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+import make_golden  # noqa: E402
+
+
+def run_full(name, scale, p, mode, variant=P.PGB_VAR_AUTO):
+    want = make_golden.load(name)
+    src, dst, n = graphgen.rmat(scale, 16, 1)
+    assert n == want["n"]
+    ds = torch.from_numpy(src).cuda()
+    dd = torch.from_numpy(dst).cuda()
+    del src, dst
+    g = P.pgb_graph_from_edges(ds, dd, n)
+    assert P.pgb_graph_info(g)[1] == want["m"]
+    b = P.pgb_partition(g, p)
+    g.free()
+    del ds, dd
+    tv = torch.zeros(n, dtype=torch.uint64, device="cuda")
+    r = P.pgb_tc_run(b, P.pgb_tc_opts_default(mode=mode, variant=variant))
+    T, _ = P.pgb_tc_result_get(r, per_vertex=tv)
+    assert T == want["T"]
+    t = tv.cpu().numpy()
+    assert np.array_equal(t[want["x"]], want["t"])
+    assert int(t.sum(dtype=np.uint64)) == 3 * T
+
+
+@pytest.mark.parametrize("mode", [P.PGB_MODE_PLAIN, P.PGB_MODE_PERSISTENT])
+def test_rmat20_p16_full_size(mode):
+    run_full("rmat20", 20, 16, mode)
+
+
+def test_rmat24_p32_full_size_bench_configuration():
+    run_full("rmat24", 24, 32, P.PGB_MODE_PERSISTENT)
+
+
+def test_rmat24_p32_full_size_bsearch_variant():
+    run_full("rmat24", 24, 32, P.PGB_MODE_PERSISTENT, P.PGB_VAR_BSEARCH)
