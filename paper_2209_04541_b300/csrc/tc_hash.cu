@@ -219,9 +219,12 @@ __global__ void __launch_bounds__(kHThreads, 3)
     extern __shared__ uint32_t hsm[];
     // Region A: the bitmap of a bitmap-mode item, or the keys and member
     // masks of a hash-mode item; all zero between items.  Region B (per-vertex
-    // counts only): keys and counters that index t[w] by table slot.
+    // counts only): in hash mode one counter per table slot; in bitmap mode a
+    // 16-bit running popcount per bitmap word, then one counter per key,
+    // indexed by the key's rank in v's sorted list.
     uint32_t* regA = hsm;
     uint32_t* regB = hsm + kRegionA;
+    __shared__ uint32_t s_wsum[kHWarps];
     __shared__ VItem s_it;
     __shared__ uint32_t s_item, s_vmask, s_next;
     __shared__ uint32_t s_edge[kHWarps][32];
@@ -256,13 +259,16 @@ __global__ void __launch_bounds__(kHThreads, 3)
         const uint32_t rhi = I.clip ? I.hi : G.n;
         const bool bitmap = single && rhi - rlo <= kBitmapBits;
         const uint32_t L = I.slots_log2, S = 1u << L;
-        uint32_t* keys = bitmap ? regB : regA;
+        uint32_t* keys = regA;
         uint32_t* masks = regA + kMaxSlots;
-        uint32_t* cnts = regB + kMaxSlots;
-        if (!bitmap || PV)
+        uint32_t* cnts = bitmap ? regB + kRegionA / 2 : regB;
+        uint16_t* pre = reinterpret_cast<uint16_t*>(regB);
+        if (!bitmap)
             for (uint32_t i = tid; i < S; i += kHThreads) keys[i] = kEmpty;
-        if (PV)
-            for (uint32_t i = tid; i < S; i += kHThreads) cnts[i] = 0;
+        if (PV) {
+            const uint32_t nc = bitmap ? kKeyCap : S;
+            for (uint32_t i = tid; i < nc; i += kHThreads) cnts[i] = 0;
+        }
         __syncthreads();
         // build: a singleton's list is inserted by the whole CTA (bitmap bits,
         // plus table keys for per-vertex counts); a group's members are
@@ -279,7 +285,7 @@ __global__ void __launch_bounds__(kHThreads, 3)
             for (uint32_t q = rb + tid; q < re; q += kHThreads) {
                 const uint32_t x = __ldg(G.col + q);
                 if (bitmap) atomicOr(&regA[(x - rlo) >> 5], 1u << ((x - rlo) & 31));
-                if (!bitmap || PV) table_insert(keys, masks, x, 0u, L);
+                else table_insert(keys, masks, x, 0u, L);
             }
         } else {
             for (uint32_t t = warp; t < I.nv; t += kHWarps) {
@@ -293,6 +299,29 @@ __global__ void __launch_bounds__(kHThreads, 3)
             }
         }
         __syncthreads();
+        if (PV && bitmap) {
+            // running popcount per bitmap word: thread t owns 32 consecutive
+            // words; a CTA scan of the per-thread sums gives each its base
+            const uint32_t nwords = (rhi - rlo + 31) >> 5;
+            const uint32_t w0 = tid * 32;
+            uint32_t own_sum = 0;
+            for (uint32_t w = w0; w < w0 + 32 && w < nwords; ++w) own_sum += __popc(regA[w]);
+            uint32_t inc = own_sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(kFullMask, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) s_wsum[warp] = inc;
+            __syncthreads();
+            uint32_t run = inc - own_sum;
+            for (int w = 0; w < warp; ++w) run += s_wsum[w];
+            for (uint32_t w = w0; w < w0 + 32 && w < nwords; ++w) {
+                pre[w] = (uint16_t)run;
+                run += __popc(regA[w]);
+            }
+            __syncthreads();
+        }
         if (tid == 0) {
             pending = atomicAdd(cursor, 1u);
             if (pending < nitems) pit = items[pending];
@@ -375,8 +404,10 @@ __global__ void __launch_bounds__(kHThreads, 3)
                         uint32_t h = 0;
                         if (bitmap) {
                             const uint32_t d = x - rlo;
-                            hit = (regA[d >> 5] >> (d & 31)) & 1u;
-                            if (PV && hit) h = table_find(keys, x, L);
+                            const uint32_t word = regA[d >> 5];
+                            hit = (word >> (d & 31)) & 1u;
+                            // counter index = rank of x in v's sorted list
+                            if (PV && hit) h = pre[d >> 5] + __popc(word & ((1u << (d & 31)) - 1u));
                         } else {
                             h = table_find(keys, x, L);
                             hit = h != kEmpty && (single || (masks[h] & bits[j]));
@@ -388,18 +419,12 @@ __global__ void __launch_bounds__(kHThreads, 3)
                     }
                     cnt += h4;
                     if (PV) {
-                        // per-in-edge tally: lanes of one owner are consecutive;
-                        // a segmented sum leaves each owner's total on its last
-                        // lane, which adds it to the owner's shared slot
+                        // per-in-edge tally: the lanes of one owner reduce
+                        // their hits together and the lowest adds the sum to
+                        // the owner's shared slot
                         const unsigned same = __match_any_sync(kFullMask, own[j]);
-                        uint32_t acc = h4;
-                        const int first = __ffs(same) - 1;
-#pragma unroll
-                        for (int d = 1; d < 32; d <<= 1) {
-                            const uint32_t y = __shfl_up_sync(kFullMask, acc, d);
-                            if (lane - d >= first) acc += y;
-                        }
-                        if (lane == 31 - __clz(same) && acc) atomicAdd(&s_edge[warp][own[j]], acc);
+                        const uint32_t acc = __reduce_add_sync(same, h4);
+                        if (lane == __ffs(same) - 1 && acc) atomicAdd(&s_edge[warp][own[j]], acc);
                     }
                 }
             }
@@ -416,9 +441,17 @@ __global__ void __launch_bounds__(kHThreads, 3)
         }
         __syncthreads();
         if (PV) {
-            for (uint32_t i = tid; i < S; i += kHThreads) {
-                const uint32_t c = cnts[i];
-                if (c) atomicAdd(G.tv + keys[i], (unsigned long long)c);
+            if (bitmap) {
+                // the key of rank i is the i-th entry of v's (clipped) list
+                for (uint32_t i = tid; i < re - rb; i += kHThreads) {
+                    const uint32_t c = cnts[i];
+                    if (c) atomicAdd(G.tv + __ldg(G.col + rb + i), (unsigned long long)c);
+                }
+            } else {
+                for (uint32_t i = tid; i < S; i += kHThreads) {
+                    const uint32_t c = cnts[i];
+                    if (c) atomicAdd(G.tv + keys[i], (unsigned long long)c);
+                }
             }
             if (tid < I.nv && s_vcnt[tid]) atomicAdd(G.tv + I.v0 + tid, (unsigned long long)s_vcnt[tid]);
         }
@@ -447,7 +480,9 @@ __global__ void __launch_bounds__(kHThreads, 3)
 
 template <bool PV>
 size_t hash_smem() {
-    return (size_t)(kRegionA + (PV ? 2 * kMaxSlots : 0)) * sizeof(uint32_t);
+    // region B: max(slot counters, 16-bit word prefix + per-key counters)
+    constexpr uint32_t kRegionB = (kRegionA / 2 + kKeyCap) > kMaxSlots ? (kRegionA / 2 + kKeyCap) : kMaxSlots;
+    return (size_t)(kRegionA + (PV ? kRegionB : 0)) * sizeof(uint32_t);
 }
 
 }  // namespace
