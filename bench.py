@@ -326,6 +326,12 @@ def main(argv=None):
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_note, "alg_bytes": info["alg_bytes"],
                 "kernel_ms": kernel_ms, "traffic": kernel_traffic(kname, args.workload)}
+    if kname == "k_tc_hash":
+        # bytes this variant must stream: every looked-up entry of the tails'
+        # rows, one 8-byte in-edge descriptor per edge, and each head's list
+        kb = 4 * info["probes"] + 12 * info["m"]
+        roofline.update({"kernel_alg_bytes": kb, "kernel_achieved": kb / (kernel_ms / 1e3) / 1e9,
+                         "kernel_frac": kb / (kernel_ms / 1e3) / 1e9 / peak})
 
     e2e = None
     if not args.no_e2e:
@@ -356,7 +362,7 @@ def main(argv=None):
                            "variant": args.variant, "kernel": kname,
                            "order": args.order, "per_vertex": bool(args.per_vertex), "n": n,
                            "raw_edges": mraw, "unique_edges": m_u, "triangles": T,
-                           "wedges": info["wedges"], "triples": info["triples"],
+                           "wedges": info["wedges"], "probes": info["probes"], "triples": info["triples"],
                            "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (raw edge list %.2f GB, oriented graph %.2f GB)"
                                  % (8 * mraw / 1e9, 8 * m_u / 1e9)},

@@ -162,6 +162,8 @@ typedef struct {
     uint64_t alg_bytes;    /* 4|E+| + 4 * wedges + 8 (n + 1) */
     uint32_t max_outdeg;
     uint32_t reserved;
+    uint64_t probes;       /* sum over edges (u, v) of the entries of u's row
+                              after v: the lookups of the middle-vertex variant */
 } pgb_blocks_stats;
 
 int pgb_blocks_info(const pgb_blocks* b, pgb_blocks_stats* out);

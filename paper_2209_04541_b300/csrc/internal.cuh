@@ -157,6 +157,7 @@ struct pgb_blocks {
     std::vector<uint64_t> block_off;    // p * p + 1 offsets into bedge
     std::vector<pgb_triple> triples;    // queue order
     uint64_t wedges = 0;
+    uint64_t probes = 0;  // sum over edges (u, v) of the entries of u's row after v
     uint32_t max_outdeg = 0;
 };
 

@@ -81,13 +81,19 @@ __global__ void k_offsets_from_sorted(const uint32_t* __restrict__ keys, uint64_
 // In-edge descriptors: for the edge u -> v at CSR position e, the range of
 // u's row after v, packed as (e + 1) | (rowptr[u + 1] << 32).
 __global__ void k_in_ranges(const uint32_t* __restrict__ eidx, uint64_t m, const uint32_t* __restrict__ rowidx,
-                            const uint32_t* __restrict__ rowptr, unsigned long long* __restrict__ xr) {
+                            const uint32_t* __restrict__ rowptr, unsigned long long* __restrict__ xr,
+                            unsigned long long* __restrict__ probes) {
+    unsigned long long acc = 0;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
         uint32_t e = eidx[i];
         uint32_t xe = rowptr[rowidx[e] + 1];
         xr[i] = (unsigned long long)(e + 1) | ((unsigned long long)xe << 32);
+        acc += xe - (e + 1);
     }
+    // sum of the range lengths: the entries the middle-vertex variant looks up
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(probes, acc);
 }
 
 __global__ void k_fill_u32(uint32_t* __restrict__ x, uint64_t n, uint32_t v) {
@@ -301,7 +307,8 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
     }
 
     // --- wedge statistics for B_alg and the autotuner
-    DevBuf<unsigned long long> wsum(1, s);
+    DevBuf<unsigned long long> wsum(1, s), wprobe(1, s);
+    PGB_CUDA(cudaMemsetAsync(wprobe.ptr, 0, 8, s));
     DevBuf<unsigned int> wmax(1, s);
     PGB_CUDA(cudaMemsetAsync(wsum.ptr, 0, 8, s));
     PGB_CUDA(cudaMemsetAsync(wmax.ptr, 0, 4, s));
@@ -354,14 +361,17 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
         sort_pairs(kc.ptr, kalt.ptr, vals.ptr, valt.ptr, m, num_bits(n > 0 ? n - 1 : 0), s, scratch, &ko, &vo);
         k_offsets_from_sorted<<<grid_for((uint64_t)n + 1), 256, 0, s>>>(ko, m, n, b->colptr.ptr);
         PGB_CHECK_LAUNCH("k_offsets_from_sorted");
-        k_in_ranges<<<grid_for(m), 256, 0, s>>>(vo, m, b->rowidx.ptr, b->rowptr.ptr, b->xr.ptr);
+        k_in_ranges<<<grid_for(m), 256, 0, s>>>(vo, m, b->rowidx.ptr, b->rowptr.ptr, b->xr.ptr, wprobe.ptr);
         PGB_CHECK_LAUNCH("k_in_ranges");
     } else {
         k_fill_u32<<<grid_for((uint64_t)n + 1), 256, 0, s>>>(b->colptr.ptr, (uint64_t)n + 1, 0);
         PGB_CHECK_LAUNCH("k_fill_u32");
     }
+    unsigned long long hp = 0;
+    PGB_CUDA(cudaMemcpyAsync(&hp, wprobe.ptr, 8, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaStreamSynchronize(s));
     b->wedges = hw;
+    b->probes = hp;
     b->max_outdeg = hm;
     b->block_off.assign(pp + 1, 0);
     for (size_t i = 0; i < pp; ++i) b->block_off[i + 1] = b->block_off[i] + b->block_edges[i];
@@ -402,6 +412,7 @@ int pgb_blocks_info(const pgb_blocks* b, pgb_blocks_stats* out) {
         out->wedges = b->wedges;
         out->alg_bytes = 4 * b->m + 4 * b->wedges + 8 * ((uint64_t)b->n + 1);
         out->max_outdeg = b->max_outdeg;
+        out->probes = b->probes;
     });
 }
 

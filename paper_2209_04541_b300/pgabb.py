@@ -77,7 +77,7 @@ class BlocksStats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint32), ("p", ctypes.c_uint32), ("m", ctypes.c_uint64),
                 ("nonempty_blocks", ctypes.c_uint64), ("triples", ctypes.c_uint64),
                 ("wedges", ctypes.c_uint64), ("alg_bytes", ctypes.c_uint64),
-                ("max_outdeg", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("max_outdeg", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("probes", ctypes.c_uint64)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

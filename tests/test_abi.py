@@ -57,7 +57,7 @@ def test_opts_default():
     assert o.per_vertex == 1 and o.per_triple == 0 and o.use_graph == 0
     assert o.device_budget == 0
     assert ctypes.sizeof(pgabb.TcOpts) == 64
-    assert ctypes.sizeof(pgabb.BlocksStats) == 56
+    assert ctypes.sizeof(pgabb.BlocksStats) == 64
     with pytest.raises(AttributeError):
         pgabb.pgb_tc_opts_default(bogus=1)
 
