@@ -65,7 +65,11 @@ __global__ void k_degrees(const uint64_t* __restrict__ keys, uint64_t m, uint32_
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         uint64_t k = keys[e];
-        atomicAdd(&deg[(uint32_t)(k >> B)], 1u);
+        const uint32_t a = (uint32_t)(k >> B);
+        // keys are sorted, so neighbouring lanes mostly share the first
+        // endpoint: one atomic per group of equal endpoints
+        const unsigned same = __match_any_sync(__activemask(), a);
+        if ((threadIdx.x & 31) == (unsigned)(__ffs(same) - 1)) atomicAdd(&deg[a], (unsigned)__popc(same));
         atomicAdd(&deg[(uint32_t)(k & mask)], 1u);
     }
 }

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -148,7 +149,11 @@ struct pgb_blocks {
     pgb::DevBuf<uint32_t> rowptr;  // n + 1 oriented offsets (m < 2^32)
     pgb::DevBuf<uint32_t> col;     // m oriented columns, rank space, rows sorted
     pgb::DevBuf<uint32_t> rowidx;  // m row of each oriented edge
-    pgb::DevBuf<uint32_t> bedge;   // m CSR edge positions grouped by block (i, j) row-major
+    // m CSR edge positions grouped by block (i, j) row-major; built on first
+    // use by ensure_block_edge_index (guarded by bedge_mu)
+    mutable pgb::DevBuf<uint32_t> bedge;
+    mutable bool bedge_ready = false;
+    mutable std::mutex bedge_mu;
     pgb::DevBuf<uint32_t> colptr;  // n + 1 first in-edge of each head v (in-edge index order)
     pgb::DevBuf<unsigned long long> xr;  // m in-edges grouped by head: tail-row range after v
     pgb::DevBuf<uint32_t> cuts_d;  // p + 1
@@ -166,6 +171,7 @@ namespace pgb {
 // Kernel-side stages (each enqueued on `s`; those that need sizes sync).
 void ingest_keys(pgb_graph* g, const uint32_t* src, const uint32_t* dst, uint64_t m, cudaStream_t s);
 void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, pgb_blocks* b);
+void ensure_block_edge_index(const pgb_blocks* b, cudaStream_t s);
 void copy_out(void* dst, const void* src_dev, size_t bytes, int mem, cudaStream_t s);
 
 }  // namespace pgb

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <memory>
+#include <mutex>
 #include <numeric>
 
 #include "internal.cuh"
@@ -78,20 +79,18 @@ __global__ void k_offsets_from_sorted(const uint32_t* __restrict__ keys, uint64_
     }
 }
 
-// In-edge descriptors: for the edge u -> v at CSR position e, the range of
-// u's row after v, packed as (e + 1) | (rowptr[u + 1] << 32).
-__global__ void k_in_ranges(const uint32_t* __restrict__ eidx, uint64_t m, const uint32_t* __restrict__ rowidx,
-                            const uint32_t* __restrict__ rowptr, unsigned long long* __restrict__ xr,
-                            unsigned long long* __restrict__ probes) {
+// Tail-row range of every edge in CSR order: for the edge u -> v at position
+// e, the entries of u's row after v, packed as (e + 1) | (rowptr[u + 1] << 32);
+// also sums the range lengths (the lookups of the middle-vertex variant).
+__global__ void k_row_ranges(uint64_t m, const uint32_t* __restrict__ rowidx, const uint32_t* __restrict__ rowptr,
+                             unsigned long long* __restrict__ xa, unsigned long long* __restrict__ probes) {
     unsigned long long acc = 0;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        uint32_t e = eidx[i];
-        uint32_t xe = rowptr[rowidx[e] + 1];
-        xr[i] = (unsigned long long)(e + 1) | ((unsigned long long)xe << 32);
-        acc += xe - (e + 1);
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const uint32_t xe = rowptr[rowidx[e] + 1];
+        xa[e] = (unsigned long long)(e + 1) | ((unsigned long long)xe << 32);
+        acc += xe - (uint32_t)(e + 1);
     }
-    // sum of the range lengths: the entries the middle-vertex variant looks up
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(probes, acc);
 }
@@ -134,8 +133,9 @@ __device__ __forceinline__ uint32_t part_of(const uint32_t* cuts, uint32_t p, ui
     return lo;
 }
 
-// Block id (i * p + j) of every oriented edge, and the p x p block edge
-// histogram (shared-memory counters when p*p fits, global otherwise).
+// Block id (i * p + j) of every oriented edge (when bid is not null) and the
+// p x p block edge histogram (when hist is not null; shared-memory counters
+// when p*p fits, global otherwise).
 __global__ void k_block_ids(const uint32_t* __restrict__ rowidx, const uint32_t* __restrict__ col, uint64_t m,
                             const uint32_t* __restrict__ cuts_g, uint32_t p, uint32_t* __restrict__ bid,
                             unsigned long long* __restrict__ hist) {
@@ -151,25 +151,19 @@ __global__ void k_block_ids(const uint32_t* __restrict__ rowidx, const uint32_t*
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         uint32_t b = part_of(cuts, p, rowidx[e]) * p + part_of(cuts, p, col[e]);
         if (bid) bid[e] = b;
+        if (!hist) continue;
         if (use_smem) atomicAdd(&h[b], 1u);
         else atomicAdd(&hist[b], 1ull);
     }
-    if (use_smem) {
+    if (use_smem && hist) {
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < p * p; i += blockDim.x)
             if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
     }
 }
 
-// In-degree histogram of the oriented graph.
-__global__ void k_indeg(const uint32_t* __restrict__ col, uint64_t m, uint32_t* __restrict__ indeg) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
-        atomicAdd(&indeg[col[e]], 1u);
-}
-
 // sum_v indeg(v) * outdeg(v) and max outdeg.
-__global__ void k_wedges(const uint32_t* __restrict__ indeg, const uint32_t* __restrict__ rowptr, uint32_t n,
+__global__ void k_wedges(const uint32_t* __restrict__ colptr, const uint32_t* __restrict__ rowptr, uint32_t n,
                          unsigned long long* __restrict__ out_sum, unsigned int* __restrict__ out_max) {
     __shared__ unsigned long long ssum[32];
     __shared__ unsigned int smax[32];
@@ -178,7 +172,7 @@ __global__ void k_wedges(const uint32_t* __restrict__ indeg, const uint32_t* __r
     uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         uint32_t od = rowptr[v + 1] - rowptr[v];
-        acc += (unsigned long long)indeg[v] * od;
+        acc += (unsigned long long)(colptr[v + 1] - colptr[v]) * od;
         mx = od > mx ? od : mx;
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -293,51 +287,88 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
     PGB_CHECK_LAUNCH("k_cuts");
     b->cuts.assign((size_t)p + 1, 0);
 
-    // --- block histogram and block ids
+    // --- block histogram (per-edge block ids are built on demand, for the
+    // runs that walk edges block by block)
     const size_t pp = (size_t)p * p;
     DevBuf<unsigned long long> hist(pp, s);
     PGB_CUDA(cudaMemsetAsync(hist.ptr, 0, pp * 8, s));
-    DevBuf<uint32_t> bid;
     if (m > 0) {
-        if (p > 1) bid.alloc(m, s);
         size_t smem = ((size_t)p + 1) * 4 + (pp <= 4096 ? pp * 4 : 0);
-        k_block_ids<<<grid_for(m), 256, smem, s>>>(b->rowidx.ptr, b->col.ptr, m, b->cuts_d.ptr, p,
-                                                   p > 1 ? bid.ptr : nullptr, hist.ptr);
+        k_block_ids<<<grid_for(m), 256, smem, s>>>(b->rowidx.ptr, b->col.ptr, m, b->cuts_d.ptr, p, nullptr,
+                                                   hist.ptr);
         PGB_CHECK_LAUNCH("k_block_ids");
     }
 
-    // --- wedge statistics for B_alg and the autotuner
+    // --- in-edge index for the middle-vertex variant: each edge's tail-row
+    // range after its head, made in CSR order, then carried into head order
+    // by a stable radix sort on the head (tails ascend within a head);
+    // colptr[v] = first in-edge of v.  Wedge statistics use in-degrees
+    // colptr[v + 1] - colptr[v].
+    b->colptr.alloc((size_t)n + 1, s);
+    b->xr.alloc(m, s);
     DevBuf<unsigned long long> wsum(1, s), wprobe(1, s);
-    PGB_CUDA(cudaMemsetAsync(wprobe.ptr, 0, 8, s));
     DevBuf<unsigned int> wmax(1, s);
     PGB_CUDA(cudaMemsetAsync(wsum.ptr, 0, 8, s));
+    PGB_CUDA(cudaMemsetAsync(wprobe.ptr, 0, 8, s));
     PGB_CUDA(cudaMemsetAsync(wmax.ptr, 0, 4, s));
     if (m > 0) {
-        DevBuf<uint32_t> indeg(n, s);
-        PGB_CUDA(cudaMemsetAsync(indeg.ptr, 0, (size_t)n * 4, s));
-        k_indeg<<<grid_for(m), 256, 0, s>>>(b->col.ptr, m, indeg.ptr);
-        PGB_CHECK_LAUNCH("k_indeg");
-        k_wedges<<<grid_for(n), 256, 0, s>>>(indeg.ptr, b->rowptr.ptr, n, wsum.ptr, wmax.ptr);
+        DevBuf<uint32_t> kc(m, s), kalt(m, s);
+        DevBuf<unsigned long long> xa(m, s);
+        PGB_CUDA(cudaMemcpyAsync(kc.ptr, b->col.ptr, m * 4, cudaMemcpyDeviceToDevice, s));
+        k_row_ranges<<<grid_for(m), 256, 0, s>>>(m, b->rowidx.ptr, b->rowptr.ptr, xa.ptr, wprobe.ptr);
+        PGB_CHECK_LAUNCH("k_row_ranges");
+        uint32_t* ko;
+        unsigned long long* vo;
+        sort_pairs(kc.ptr, kalt.ptr, xa.ptr, b->xr.ptr, m, num_bits(n > 0 ? n - 1 : 0), s, scratch, &ko, &vo);
+        if (vo != b->xr.ptr) PGB_CUDA(cudaMemcpyAsync(b->xr.ptr, vo, m * 8, cudaMemcpyDeviceToDevice, s));
+        k_offsets_from_sorted<<<grid_for((uint64_t)n + 1), 256, 0, s>>>(ko, m, n, b->colptr.ptr);
+        PGB_CHECK_LAUNCH("k_offsets_from_sorted");
+        k_wedges<<<grid_for(n), 256, 0, s>>>(b->colptr.ptr, b->rowptr.ptr, n, wsum.ptr, wmax.ptr);
         PGB_CHECK_LAUNCH("k_wedges");
+    } else {
+        k_fill_u32<<<grid_for((uint64_t)n + 1), 256, 0, s>>>(b->colptr.ptr, (uint64_t)n + 1, 0);
+        PGB_CHECK_LAUNCH("k_fill_u32");
     }
 
     // --- one sync: cuts, histogram, stats to the host
     b->block_edges.assign(pp, 0);
-    unsigned long long hw = 0;
+    unsigned long long hw = 0, hp = 0;
     unsigned int hm = 0;
     PGB_CUDA(cudaMemcpyAsync(b->cuts.data(), b->cuts_d.ptr, ((size_t)p + 1) * 4, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaMemcpyAsync(b->block_edges.data(), hist.ptr, pp * 8, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaMemcpyAsync(&hw, wsum.ptr, 8, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaMemcpyAsync(&hp, wprobe.ptr, 8, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaMemcpyAsync(&hm, wmax.ptr, 4, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaStreamSynchronize(s));
+    b->wedges = hw;
+    b->probes = hp;
+    b->max_outdeg = hm;
+    b->block_off.assign(pp + 1, 0);
+    for (size_t i = 0; i < pp; ++i) b->block_off[i + 1] = b->block_off[i] + b->block_edges[i];
+    b->triples = make_queue(p, b->block_edges);
+}
 
-    // --- group edges by block: stable radix sort of (block id, edge position)
+// Block-grouped edge index (positions of the edges of block (i, j), blocks in
+// row-major order, CSR order inside a block): a stable radix sort of
+// (block id, edge position).  Built once per partition, on first use.
+void ensure_block_edge_index(const pgb_blocks* b, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(b->bedge_mu);
+    if (b->bedge_ready) return;
+    const uint64_t m = b->m;
+    const uint32_t p = b->p;
     b->bedge.alloc(m, s);
     if (m > 0) {
         if (p == 1) {
             k_iota<<<grid_for(m), 256, 0, s>>>(b->bedge.ptr, m);
             PGB_CHECK_LAUNCH("k_iota");
         } else {
-            DevBuf<uint32_t> kalt(m, s), vals(m, s);
+            Scratch scratch;
+            const size_t pp = (size_t)p * p;
+            DevBuf<uint32_t> bid(m, s), kalt(m, s), vals(m, s);
+            size_t smem = ((size_t)p + 1) * 4 + (pp <= 4096 ? pp * 4 : 0);
+            k_block_ids<<<grid_for(m), 256, smem, s>>>(b->rowidx.ptr, b->col.ptr, m, b->cuts_d.ptr, p, bid.ptr,
+                                                       nullptr);
+            PGB_CHECK_LAUNCH("k_block_ids");
             k_iota<<<grid_for(m), 256, 0, s>>>(vals.ptr, m);
             PGB_CHECK_LAUNCH("k_iota");
             uint32_t *ko, *vo;
@@ -346,36 +377,7 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
                 PGB_CUDA(cudaMemcpyAsync(b->bedge.ptr, vo, m * 4, cudaMemcpyDeviceToDevice, s));
         }
     }
-
-    // --- in-edge index for the middle-vertex variant: edges grouped by head
-    // v (stable radix sort, so tails ascend within a head), colptr[v] = first
-    // in-edge of v, xr = the tail's row range after v
-    b->colptr.alloc((size_t)n + 1, s);
-    b->xr.alloc(m, s);
-    if (m > 0) {
-        DevBuf<uint32_t> kc(m, s), kalt(m, s), vals(m, s), valt(m, s);
-        PGB_CUDA(cudaMemcpyAsync(kc.ptr, b->col.ptr, m * 4, cudaMemcpyDeviceToDevice, s));
-        k_iota<<<grid_for(m), 256, 0, s>>>(vals.ptr, m);
-        PGB_CHECK_LAUNCH("k_iota");
-        uint32_t *ko, *vo;
-        sort_pairs(kc.ptr, kalt.ptr, vals.ptr, valt.ptr, m, num_bits(n > 0 ? n - 1 : 0), s, scratch, &ko, &vo);
-        k_offsets_from_sorted<<<grid_for((uint64_t)n + 1), 256, 0, s>>>(ko, m, n, b->colptr.ptr);
-        PGB_CHECK_LAUNCH("k_offsets_from_sorted");
-        k_in_ranges<<<grid_for(m), 256, 0, s>>>(vo, m, b->rowidx.ptr, b->rowptr.ptr, b->xr.ptr, wprobe.ptr);
-        PGB_CHECK_LAUNCH("k_in_ranges");
-    } else {
-        k_fill_u32<<<grid_for((uint64_t)n + 1), 256, 0, s>>>(b->colptr.ptr, (uint64_t)n + 1, 0);
-        PGB_CHECK_LAUNCH("k_fill_u32");
-    }
-    unsigned long long hp = 0;
-    PGB_CUDA(cudaMemcpyAsync(&hp, wprobe.ptr, 8, cudaMemcpyDeviceToHost, s));
-    PGB_CUDA(cudaStreamSynchronize(s));
-    b->wedges = hw;
-    b->probes = hp;
-    b->max_outdeg = hm;
-    b->block_off.assign(pp + 1, 0);
-    for (size_t i = 0; i < pp; ++i) b->block_off[i + 1] = b->block_off[i] + b->block_edges[i];
-    b->triples = make_queue(p, b->block_edges);
+    b->bedge_ready = true;
 }
 
 }  // namespace pgb

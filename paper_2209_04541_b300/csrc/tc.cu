@@ -305,6 +305,8 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o, cudaStream_t s, pgb_t
         tv.alloc(n, s);
         if (n) PGB_CUDA(cudaMemsetAsync(tv.ptr, 0, (size_t)n * 8, s));
     }
+    // the edge-wise (binary-search) kernels walk edges block by block
+    if (o.mode == PGB_MODE_PLAIN || o.variant == PGB_VAR_BSEARCH) ensure_block_edge_index(b, s);
     Graph G{b->bedge.ptr, b->rowidx.ptr, b->col.ptr, b->rowptr.ptr, tv.ptr};
 
     DevBuf<unsigned long long> partials;
@@ -345,7 +347,7 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o, cudaStream_t s, pgb_t
     } else if (o.variant != PGB_VAR_BSEARCH) {
         // middle-vertex hash variant (tc_hash.cu)
         HashGraph H{b->rowptr.ptr, b->col.ptr, b->rowidx.ptr, b->colptr.ptr, b->xr.ptr, tv.ptr, b->n};
-        run_hash(b, H, r->per_vertex, s, partials, npartials, r->ev0, r->ev1, nullptr);
+        run_hash(b, H, r->per_vertex, o.chunk_edges, s, partials, npartials, r->ev0, r->ev1, nullptr);
     } else {
         // tuples (A_ij, A_i[j..p-1], A_j[j..p-1]): one per non-empty block
         // pair on the queue, ordered by the summed weight of its triples

@@ -14,9 +14,9 @@
 // Work items (built on the device, heaviest middle vertices first):
 //   group item:     up to 32 consecutive ranks whose partial lists hold at
 //                   most kKeyCap entries in total and whose in-edges number
-//                   at most kInChunk; table entries carry a 32-bit mask of
+//                   at most in_chunk; table entries carry a 32-bit mask of
 //                   the group members that own the key;
-//   singleton item: one middle vertex, a run of at most kInChunk of its
+//   singleton item: one middle vertex, a run of at most in_chunk of its
 //                   in-edges, and a slice of at most kKeyCap entries of its
 //                   list (the slice is a third-vertex rank range [lo, hi),
 //                   i.e. a narrower column-block run; both lists are clipped).
@@ -37,7 +37,7 @@ namespace {
 constexpr int kHThreads = 256;
 constexpr int kHWarps = kHThreads / 32;
 constexpr uint32_t kKeyCap = 2048;     // table keys per item (load factor <= 1/2)
-constexpr uint32_t kInChunk = 1024;    // in-edges per item
+constexpr uint32_t kInChunkDefault = 4096;  // in-edges per item unless the caller sets one
 constexpr int kMaxSlotsLog2 = 12;      // 4096 slots
 constexpr uint32_t kMaxSlots = 1u << kMaxSlotsLog2;
 constexpr uint32_t kEmpty = 0xffffffffu;
@@ -125,7 +125,7 @@ struct WindowInfo {
 
 __device__ __forceinline__ WindowInfo window_info(const uint32_t* __restrict__ rowptr,
                                                   const uint32_t* __restrict__ colptr, uint32_t n, uint32_t w,
-                                                  int lane) {
+                                                  uint32_t in_chunk, int lane) {
     WindowInfo W;
     W.v = w * 32 + lane;
     W.dp = W.dm = 0;
@@ -136,30 +136,30 @@ __device__ __forceinline__ WindowInfo window_info(const uint32_t* __restrict__ r
     W.act = W.dp > 0 && W.dm > 0;
     W.keys = warp_sum(W.act ? W.dp : 0);
     W.ins = warp_sum(W.act ? W.dm : 0);
-    W.group = W.keys > 0 && W.keys <= kKeyCap && W.ins <= kInChunk;
-    W.mine = (W.act && !W.group) ? ((W.dm + kInChunk - 1) / kInChunk) * ((W.dp + kKeyCap - 1) / kKeyCap) : 0;
+    W.group = W.keys > 0 && W.keys <= kKeyCap && W.ins <= in_chunk;
+    W.mine = (W.act && !W.group) ? ((W.dm + in_chunk - 1) / in_chunk) * ((W.dp + kKeyCap - 1) / kKeyCap) : 0;
     return W;
 }
 
 // counts[nwin - 1 - w] = items of window w (windows of high ranks first).
 __global__ void k_items_count(const uint32_t* __restrict__ rowptr, const uint32_t* __restrict__ colptr, uint32_t n,
-                              uint32_t nwin, uint32_t* __restrict__ counts) {
+                              uint32_t nwin, uint32_t in_chunk, uint32_t* __restrict__ counts) {
     const int lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwin; w += nw) {
-        WindowInfo W = window_info(rowptr, colptr, n, w, lane);
+        WindowInfo W = window_info(rowptr, colptr, n, w, in_chunk, lane);
         uint32_t c = W.keys == 0 ? 0 : (W.group ? 1 : warp_sum(W.mine));
         if (lane == 0) counts[nwin - 1 - w] = c;
     }
 }
 
 __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t* __restrict__ colptr,
-                             const uint32_t* __restrict__ col, uint32_t n, uint32_t nwin,
+                             const uint32_t* __restrict__ col, uint32_t n, uint32_t nwin, uint32_t in_chunk,
                              const uint32_t* __restrict__ offs, VItem* __restrict__ items) {
     const int lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwin; w += nw) {
-        WindowInfo W = window_info(rowptr, colptr, n, w, lane);
+        WindowInfo W = window_info(rowptr, colptr, n, w, in_chunk, lane);
         if (W.keys == 0) continue;
         const uint32_t base = offs[nwin - 1 - w];
         if (W.group) {
@@ -185,7 +185,7 @@ __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t
         }
         excl -= W.mine;
         if (!W.mine) continue;
-        const uint32_t na = (W.dm + kInChunk - 1) / kInChunk;
+        const uint32_t na = (W.dm + in_chunk - 1) / in_chunk;
         const uint32_t nk = (W.dp + kKeyCap - 1) / kKeyCap;
         const uint32_t rb = rowptr[W.v], cb = colptr[W.v];
         uint32_t out = base + excl;
@@ -194,8 +194,8 @@ __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t
                 VItem it;
                 it.v0 = W.v;
                 it.nv = 1;
-                it.in_begin = cb + a * kInChunk;
-                it.in_end = min(it.in_begin + kInChunk, cb + W.dm);
+                it.in_begin = cb + a * in_chunk;
+                it.in_end = min(it.in_begin + in_chunk, cb + W.dm);
                 if (nk > 1) {
                     it.lo = col[rb + kk * kKeyCap];
                     it.hi = (kk + 1 < nk) ? col[rb + (kk + 1) * kKeyCap] : n;
@@ -487,8 +487,10 @@ size_t hash_smem() {
 
 }  // namespace
 
-void run_hash(const pgb_blocks* b, const HashGraph& G, bool pv, cudaStream_t s, DevBuf<unsigned long long>& partials,
-              uint64_t& npartials, cudaEvent_t ev0, cudaEvent_t ev1, HashRunStats* stats) {
+void run_hash(const pgb_blocks* b, const HashGraph& G, bool pv, uint32_t in_chunk, cudaStream_t s,
+              DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0, cudaEvent_t ev1,
+              HashRunStats* stats) {
+    if (in_chunk == 0) in_chunk = kInChunkDefault;
     const uint32_t n = b->n;
     const uint32_t nwin = (n + 31) / 32;
     npartials = 0;
@@ -500,7 +502,7 @@ void run_hash(const pgb_blocks* b, const HashGraph& G, bool pv, cudaStream_t s, 
     DevBuf<uint32_t> counts((size_t)nwin + 1, s), offs((size_t)nwin + 1, s);
     PGB_CUDA(cudaMemsetAsync(counts.ptr + nwin, 0, 4, s));
     const int wgrid = (int)std::min<uint64_t>(((uint64_t)nwin * 32 + 255) / 256, 148ull * 64);
-    k_items_count<<<wgrid, 256, 0, s>>>(b->rowptr.ptr, b->colptr.ptr, n, nwin, counts.ptr);
+    k_items_count<<<wgrid, 256, 0, s>>>(b->rowptr.ptr, b->colptr.ptr, n, nwin, in_chunk, counts.ptr);
     PGB_CHECK_LAUNCH("k_items_count");
     Scratch scratch;
     size_t tmp = 0;
@@ -512,7 +514,8 @@ void run_hash(const pgb_blocks* b, const HashGraph& G, bool pv, cudaStream_t s, 
     PGB_CUDA(cudaStreamSynchronize(s));
     DevBuf<VItem> items(std::max<uint32_t>(nitems, 1), s);
     if (nitems) {
-        k_items_emit<<<wgrid, 256, 0, s>>>(b->rowptr.ptr, b->colptr.ptr, b->col.ptr, n, nwin, offs.ptr, items.ptr);
+        k_items_emit<<<wgrid, 256, 0, s>>>(b->rowptr.ptr, b->colptr.ptr, b->col.ptr, n, nwin, in_chunk, offs.ptr,
+                                           items.ptr);
         PGB_CHECK_LAUNCH("k_items_emit");
     }
     DevBuf<unsigned int> cursor(1, s);

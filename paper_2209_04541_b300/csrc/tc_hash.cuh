@@ -22,7 +22,9 @@ struct HashRunStats {
 
 // Builds the work items and launches the persistent hash kernel on `s`
 // between events ev0 and ev1; per-CTA totals land in `partials`.
-void run_hash(const pgb_blocks* b, const HashGraph& G, bool pv, cudaStream_t s, DevBuf<unsigned long long>& partials,
-              uint64_t& npartials, cudaEvent_t ev0, cudaEvent_t ev1, HashRunStats* stats);
+// in_chunk: in-edges per work item (0 = default).
+void run_hash(const pgb_blocks* b, const HashGraph& G, bool pv, uint32_t in_chunk, cudaStream_t s,
+              DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0, cudaEvent_t ev1,
+              HashRunStats* stats);
 
 }  // namespace pgb
