@@ -42,7 +42,8 @@ constexpr int kMaxSlotsLog2 = 12;      // 4096 slots
 constexpr uint32_t kMaxSlots = 1u << kMaxSlotsLog2;
 constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr unsigned kFullMask = 0xffffffffu;
-constexpr int kUnroll = 4;             // 16-byte quad loads per lane issued together
+constexpr int kUnrollPV = 4;           // 16-byte quad loads per lane issued together (per-vertex run)
+constexpr int kUnrollGlobal = 4;       // the same for a global-count run
 constexpr uint32_t kRegionA = 2 * kMaxSlots;        // words: hash keys + masks, or a bitmap
 constexpr uint32_t kBitmapBits = 32 * kRegionA;    // widest third-vertex range held as a bitmap
 
@@ -213,14 +214,14 @@ __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t
 }
 
 template <bool PV>
-__global__ void __launch_bounds__(kHThreads, 3)
+__global__ void __launch_bounds__(kHThreads, 4)
     k_tc_hash(HashGraph G, const VItem* __restrict__ items, uint32_t nitems, unsigned int* __restrict__ cursor,
               unsigned long long* __restrict__ partials) {
     extern __shared__ uint32_t hsm[];
     // Region A: the bitmap of a bitmap-mode item, or the keys and member
     // masks of a hash-mode item; all zero between items.  Region B (per-vertex
     // counts only): in hash mode one counter per table slot; in bitmap mode a
-    // 16-bit running popcount per bitmap word, then one counter per key,
+    // 16-bit running popcount per pair of bitmap words, then one counter per key,
     // indexed by the key's rank in v's sorted list.
     uint32_t* regA = hsm;
     uint32_t* regB = hsm + kRegionA;
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(kHThreads, 3)
         const uint32_t L = I.slots_log2, S = 1u << L;
         uint32_t* keys = regA;
         uint32_t* masks = regA + kMaxSlots;
-        uint32_t* cnts = bitmap ? regB + kRegionA / 2 : regB;
+        uint32_t* cnts = bitmap ? regB + kRegionA / 4 : regB;
         uint16_t* pre = reinterpret_cast<uint16_t*>(regB);
         if (!bitmap)
             for (uint32_t i = tid; i < S; i += kHThreads) keys[i] = kEmpty;
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(kHThreads, 3)
             uint32_t run = inc - own_sum;
             for (int w = 0; w < warp; ++w) run += s_wsum[w];
             for (uint32_t w = w0; w < w0 + 32 && w < nwords; ++w) {
-                pre[w] = (uint16_t)run;
+                if ((w & 1) == 0) pre[w >> 1] = (uint16_t)run;
                 run += __popc(regA[w]);
             }
             __syncthreads();
@@ -369,11 +370,12 @@ __global__ void __launch_bounds__(kHThreads, 3)
             const uint32_t total = __shfl_sync(kFullMask, incl, 31);
             const uint32_t excl = incl - nq;
             const uint32_t send = sb + sl;
-            for (uint32_t r0 = 0; r0 < total; r0 += 32 * kUnroll) {
-                uint4 qv[kUnroll];
-                uint32_t qb[kUnroll], lo_[kUnroll], hi_[kUnroll], bits[kUnroll], own[kUnroll];
+            constexpr int U = PV ? kUnrollPV : kUnrollGlobal;
+            for (uint32_t r0 = 0; r0 < total; r0 += 32 * U) {
+                uint4 qv[U];
+                uint32_t qb[U], lo_[U], hi_[U], bits[U], own[U];
 #pragma unroll
-                for (int j = 0; j < kUnroll; ++j) {
+                for (int j = 0; j < U; ++j) {
                     const uint32_t f = r0 + 32 * j + lane;
                     int o = 0;
 #pragma unroll
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(kHThreads, 3)
                     if (f >= total) hi_[j] = 0;
                 }
 #pragma unroll
-                for (int j = 0; j < kUnroll; ++j) {
+                for (int j = 0; j < U; ++j) {
                     const uint32_t xv[4] = {qv[j].x, qv[j].y, qv[j].z, qv[j].w};
                     uint32_t h4 = 0;
 #pragma unroll
@@ -407,7 +409,11 @@ __global__ void __launch_bounds__(kHThreads, 3)
                             const uint32_t word = regA[d >> 5];
                             hit = (word >> (d & 31)) & 1u;
                             // counter index = rank of x in v's sorted list
-                            if (PV && hit) h = pre[d >> 5] + __popc(word & ((1u << (d & 31)) - 1u));
+                            if (PV && hit) {
+                                const uint32_t w = d >> 5;
+                                h = pre[w >> 1] + ((w & 1) ? __popc(regA[w - 1]) : 0) +
+                                    __popc(word & ((1u << (d & 31)) - 1u));
+                            }
                         } else {
                             h = table_find(keys, x, L);
                             hit = h != kEmpty && (single || (masks[h] & bits[j]));
@@ -481,7 +487,7 @@ __global__ void __launch_bounds__(kHThreads, 3)
 template <bool PV>
 size_t hash_smem() {
     // region B: max(slot counters, 16-bit word prefix + per-key counters)
-    constexpr uint32_t kRegionB = (kRegionA / 2 + kKeyCap) > kMaxSlots ? (kRegionA / 2 + kKeyCap) : kMaxSlots;
+    constexpr uint32_t kRegionB = (kRegionA / 4 + kKeyCap) > kMaxSlots ? (kRegionA / 4 + kKeyCap) : kMaxSlots;
     return (size_t)(kRegionA + (PV ? kRegionB : 0)) * sizeof(uint32_t);
 }
 
