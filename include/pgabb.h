@@ -87,8 +87,14 @@ extern "C" {
  * PGB_VAR_BSEARCH: each element of the shorter list is binary-searched in
  *                  the longer one; work is flattened across a warp.
  * PGB_VAR_MERGE:   warp-cooperative merge of 32-element chunks.
- * PGB_VAR_HASH:    the first endpoint's partial list is put in a
- *                  shared-memory hash table and probed. */
+ * PGB_VAR_HASH:    middle-vertex form: the partial list of each middle
+ *                  vertex v is held in shared memory (a bitmap over its
+ *                  third-vertex rank range when that range is at most
+ *                  262,144 ranks, else a hash table) and the lists of v's
+ *                  in-neighbours after v are streamed through it.
+ * PGB_VAR_AUTO runs PGB_VAR_HASH in PERSISTENT mode and PGB_VAR_BSEARCH in
+ * PLAIN mode; within the hash form the bitmap or table is chosen per work
+ * item from the width of its rank range. */
 #define PGB_VAR_AUTO    0
 #define PGB_VAR_BSEARCH 1
 #define PGB_VAR_MERGE   2
@@ -196,7 +202,9 @@ typedef struct {
     int32_t use_graph;     /* capture the launches in a CUDA graph (default 0) */
     int32_t order;         /* PGB_ORDER_* (default PGB_ORDER_WEIGHT) */
     uint64_t device_budget;/* bytes for resident blocks; 0 = no limit */
-    uint32_t chunk_edges;  /* PERSISTENT: edges per dequeued chunk (0 = auto) */
+    uint32_t chunk_edges;  /* PERSISTENT: binary-search variant: edges per
+                              dequeued chunk; hash variant: in-edges per work
+                              item (0 = default) */
     uint32_t reserved[7];
 } pgb_tc_opts;
 
