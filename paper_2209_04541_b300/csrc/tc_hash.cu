@@ -47,16 +47,6 @@ constexpr int kUnrollGlobal = 4;       // the same for a global-count run
 constexpr uint32_t kRegionA = 2 * kMaxSlots;        // words: hash keys + masks, or a bitmap
 constexpr uint32_t kBitmapBits = 32 * kRegionA;    // widest third-vertex range held as a bitmap
 
-struct VItem {
-    uint32_t v0;        // first middle vertex (rank)
-    uint32_t nv;        // consecutive middle vertices in the item (<= 32)
-    uint32_t in_begin;  // in-edge range [in_begin, in_end) of the in-edge index
-    uint32_t in_end;
-    uint32_t lo, hi;    // third-vertex rank range
-    uint32_t slots_log2;
-    uint32_t clip;      // 1 when lists are clipped to [lo, hi)
-};
-
 __device__ __forceinline__ uint32_t hslot(uint32_t x, uint32_t log2s) { return (x * 0x9E3779B1u) >> (32 - log2s); }
 
 __device__ __forceinline__ uint32_t ceil_log2(uint32_t x) { return x <= 1 ? 0 : 32 - __clz(x - 1); }
@@ -156,7 +146,7 @@ __global__ void k_items_count(const uint32_t* __restrict__ rowptr, const uint32_
 
 __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t* __restrict__ colptr,
                              const uint32_t* __restrict__ col, uint32_t n, uint32_t nwin, uint32_t in_chunk,
-                             const uint32_t* __restrict__ offs, VItem* __restrict__ items) {
+                             uint32_t job, const uint32_t* __restrict__ offs, VItem* __restrict__ items) {
     const int lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwin; w += nw) {
@@ -172,8 +162,9 @@ __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t
                 it.in_end = colptr[it.v0 + it.nv];
                 it.lo = 0;
                 it.hi = n;
-                it.slots_log2 = slots_for(W.keys);
+                it.slots_log2 = (uint16_t)slots_for(W.keys);
                 it.clip = 0;
+                it.job = job;
                 items[base] = it;
             }
             continue;
@@ -206,7 +197,8 @@ __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t
                     it.hi = n;
                     it.clip = 0;
                 }
-                it.slots_log2 = slots_for(min(kKeyCap, W.dp - kk * kKeyCap));
+                it.slots_log2 = (uint16_t)slots_for(min(kKeyCap, W.dp - kk * kKeyCap));
+                it.job = job;
                 items[out++] = it;
             }
         }
@@ -215,8 +207,8 @@ __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t
 
 template <bool PV>
 __global__ void __launch_bounds__(kHThreads, 4)
-    k_tc_hash(HashGraph G, const VItem* __restrict__ items, uint32_t nitems, unsigned int* __restrict__ cursor,
-              unsigned long long* __restrict__ partials) {
+    k_tc_hash(const HashGraph* __restrict__ graphs, uint32_t njobs, const VItem* __restrict__ items,
+              uint32_t nitems, unsigned int* __restrict__ cursor, unsigned long long* __restrict__ partials) {
     extern __shared__ uint32_t hsm[];
     // Region A: the bitmap of a bitmap-mode item, or the keys and member
     // masks of a hash-mode item; all zero between items.  Region B (per-vertex
@@ -226,26 +218,31 @@ __global__ void __launch_bounds__(kHThreads, 4)
     uint32_t* regA = hsm;
     uint32_t* regB = hsm + kRegionA;
     __shared__ uint32_t s_wsum[kHWarps];
-    __shared__ VItem s_it;
-    __shared__ uint32_t s_item, s_vmask, s_next;
+    __shared__ VItem s_it, s_itn;      // current item and the next one (prefetched)
+    __shared__ HashGraph s_g, s_gn;
+    __shared__ unsigned long long s_jobcnt[kMaxBatchJobs];
+    __shared__ uint32_t s_item, s_itemn, s_vmask, s_next;
     __shared__ uint32_t s_edge[kHWarps][32];
     __shared__ uint32_t s_vcnt[32];
-    __shared__ unsigned long long s_red[kHWarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (uint32_t i = tid; i < kRegionA; i += kHThreads) regA[i] = 0;
+    for (uint32_t j = tid; j < njobs; j += kHThreads) s_jobcnt[j] = 0;
     if (PV) s_edge[warp][lane] = 0;
-    // thread 0 keeps the next item (index and descriptor) fetched ahead
-    uint32_t pending = 0;
-    VItem pit{};
+    // thread 0 fetches the next item (index, descriptor, graph) ahead into
+    // the second shared slot
     if (tid == 0) {
-        pending = atomicAdd(cursor, 1u);
-        if (pending < nitems) pit = items[pending];
+        s_itemn = atomicAdd(cursor, 1u);
+        if (s_itemn < nitems) {
+            s_itn = items[s_itemn];
+            s_gn = graphs[s_itn.job];
+        }
     }
     unsigned long long cnt = 0;
     for (;;) {
         if (tid == 0) {
-            s_item = pending;
-            s_it = pit;
+            s_item = s_itemn;
+            s_it = s_itn;
+            s_g = s_gn;
             s_vmask = 0;
             s_next = 0;
         }
@@ -253,6 +250,7 @@ __global__ void __launch_bounds__(kHThreads, 4)
         __syncthreads();
         if (s_item >= nitems) break;
         const VItem I = s_it;
+        const HashGraph& G = s_g;
         const bool single = I.nv == 1;
         // third-vertex range of the item: a singleton's partner entries all
         // exceed v, so its range starts at v + 1
@@ -324,8 +322,11 @@ __global__ void __launch_bounds__(kHThreads, 4)
             __syncthreads();
         }
         if (tid == 0) {
-            pending = atomicAdd(cursor, 1u);
-            if (pending < nitems) pit = items[pending];
+            s_itemn = atomicAdd(cursor, 1u);
+            if (s_itemn < nitems) {
+                s_itn = items[s_itemn];
+                s_gn = graphs[s_itn.job];
+            }
         }
         const uint32_t vmask = s_vmask;
         // probe: warps take batches of 32 in-edges from a shared counter (so a
@@ -445,6 +446,11 @@ __global__ void __launch_bounds__(kHThreads, 4)
                 __syncwarp();
             }
         }
+        // the item's count goes to its job's shared accumulator
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFullMask, cnt, o);
+        if (lane == 0 && cnt) atomicAdd(&s_jobcnt[I.job], cnt);
+        cnt = 0;
         __syncthreads();
         if (PV) {
             if (bitmap) {
@@ -472,16 +478,9 @@ __global__ void __launch_bounds__(kHThreads, 4)
         }
         __syncthreads();
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFullMask, cnt, o);
-    if (lane == 0) s_red[warp] = cnt;
+    // per-job CTA totals: partials[job * gridDim.x + blockIdx.x]
     __syncthreads();
-    if (warp == 0) {
-        cnt = lane < kHWarps ? s_red[lane] : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFullMask, cnt, o);
-        if (lane == 0) partials[blockIdx.x] = cnt;
-    }
+    for (uint32_t j = tid; j < njobs; j += kHThreads) partials[(size_t)j * gridDim.x + blockIdx.x] = s_jobcnt[j];
 }
 
 template <bool PV>
@@ -493,17 +492,14 @@ size_t hash_smem() {
 
 }  // namespace
 
-void run_hash(const pgb_blocks* b, const HashGraph& G, bool pv, uint32_t in_chunk, cudaStream_t s,
-              DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0, cudaEvent_t ev1,
-              HashRunStats* stats) {
+uint32_t build_hash_items(const pgb_blocks* b, uint32_t job, uint32_t in_chunk, cudaStream_t s,
+                          DevBuf<VItem>& items) {
     if (in_chunk == 0) in_chunk = kInChunkDefault;
     const uint32_t n = b->n;
     const uint32_t nwin = (n + 31) / 32;
-    npartials = 0;
     if (b->m == 0 || nwin == 0) {
-        PGB_CUDA(cudaEventRecord(ev0, s));
-        PGB_CUDA(cudaEventRecord(ev1, s));
-        return;
+        items.alloc(1, s);
+        return 0;
     }
     DevBuf<uint32_t> counts((size_t)nwin + 1, s), offs((size_t)nwin + 1, s);
     PGB_CUDA(cudaMemsetAsync(counts.ptr + nwin, 0, 4, s));
@@ -518,14 +514,16 @@ void run_hash(const pgb_blocks* b, const HashGraph& G, bool pv, uint32_t in_chun
     uint32_t nitems = 0;
     PGB_CUDA(cudaMemcpyAsync(&nitems, offs.ptr + nwin, 4, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaStreamSynchronize(s));
-    DevBuf<VItem> items(std::max<uint32_t>(nitems, 1), s);
+    items.alloc(std::max<uint32_t>(nitems, 1), s);
     if (nitems) {
-        k_items_emit<<<wgrid, 256, 0, s>>>(b->rowptr.ptr, b->colptr.ptr, b->col.ptr, n, nwin, in_chunk, offs.ptr,
+        k_items_emit<<<wgrid, 256, 0, s>>>(b->rowptr.ptr, b->colptr.ptr, b->col.ptr, n, nwin, in_chunk, job, offs.ptr,
                                            items.ptr);
         PGB_CHECK_LAUNCH("k_items_emit");
     }
-    DevBuf<unsigned int> cursor(1, s);
-    PGB_CUDA(cudaMemsetAsync(cursor.ptr, 0, 4, s));
+    return nitems;
+}
+
+int hash_grid(bool pv) {
     int dev = 0, sms = 0, per_sm = 0;
     PGB_CUDA(cudaGetDevice(&dev));
     PGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -537,16 +535,42 @@ void run_hash(const pgb_blocks* b, const HashGraph& G, bool pv, uint32_t in_chun
         PGB_CUDA(cudaFuncSetAttribute(k_tc_hash<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         PGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_hash<false>, kHThreads, smem));
     }
-    const int grid = std::max(1, per_sm) * sms;
+    return std::max(1, per_sm) * sms;
+}
+
+void launch_hash(const HashGraph* d_graphs, uint32_t njobs, const VItem* items, uint32_t nitems, bool pv,
+                 cudaStream_t s, unsigned int* cursor, unsigned long long* partials, int grid) {
+    if (njobs == 0 || njobs > kMaxBatchJobs) fail(PGB_E_INVAL, "jobs per launch must be in [1, 256]");
+    const size_t smem = pv ? hash_smem<true>() : hash_smem<false>();
+    PGB_CUDA(cudaMemsetAsync(cursor, 0, 4, s));
+    if (pv)
+        k_tc_hash<true><<<grid, kHThreads, smem, s>>>(d_graphs, njobs, items, nitems, cursor, partials);
+    else
+        k_tc_hash<false><<<grid, kHThreads, smem, s>>>(d_graphs, njobs, items, nitems, cursor, partials);
+    PGB_CHECK_LAUNCH("k_tc_hash");
+}
+
+void run_hash(const pgb_blocks* b, const HashGraph& G, bool pv, uint32_t in_chunk, cudaStream_t s,
+              DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0, cudaEvent_t ev1,
+              HashRunStats* stats) {
+    npartials = 0;
+    DevBuf<VItem> items;
+    const uint32_t nitems = build_hash_items(b, 0, in_chunk, s, items);
+    if (nitems == 0) {
+        PGB_CUDA(cudaEventRecord(ev0, s));
+        PGB_CUDA(cudaEventRecord(ev1, s));
+        return;
+    }
+    DevBuf<HashGraph> dg(1, s);
+    PGB_CUDA(cudaMemcpyAsync(dg.ptr, &G, sizeof(HashGraph), cudaMemcpyHostToDevice, s));
+    DevBuf<unsigned int> cursor(1, s);
+    const int grid = hash_grid(pv);
     npartials = (uint64_t)grid;
     partials.alloc(npartials, s);
     PGB_CUDA(cudaEventRecord(ev0, s));
-    if (pv)
-        k_tc_hash<true><<<grid, kHThreads, smem, s>>>(G, items.ptr, nitems, cursor.ptr, partials.ptr);
-    else
-        k_tc_hash<false><<<grid, kHThreads, smem, s>>>(G, items.ptr, nitems, cursor.ptr, partials.ptr);
-    PGB_CHECK_LAUNCH("k_tc_hash");
+    launch_hash(dg.ptr, 1, items.ptr, nitems, pv, s, cursor.ptr, partials.ptr, grid);
     PGB_CUDA(cudaEventRecord(ev1, s));
+    // the host copy of G above is pageable, so the copy is staged before return
     if (stats) {
         stats->items = nitems;
         stats->grid = grid;
