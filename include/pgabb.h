@@ -235,6 +235,90 @@ int pgb_tc_count_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, uin
                        int cut_rule, const pgb_tc_opts* opts, int mem, void* stream, uint64_t* total,
                        uint64_t* per_vertex);
 
+/* ---------------------------------------------------------------- serve */
+/* A serve loop for triangle-count jobs on graphs of mixed sizes (the paper
+ * runs one computation at a time, Section 4.1; serving is this library's
+ * extension of the same path).  Jobs are raw edge lists.  The server admits
+ * queued jobs in arrival order while the estimated device bytes of admitted
+ * jobs stay within budget_bytes; admitted jobs are ingested, ordered and
+ * partitioned concurrently on their own streams.
+ *   PGB_SERVE_BATCHED: continuous batching.  Every staged job (up to
+ *     max_batch_jobs) is counted in ONE persistent launch whose work items
+ *     interleave the jobs' block tuples; jobs staged during that launch go
+ *     into the next one.
+ *   PGB_SERVE_SERIAL: one job at a time, staged and counted alone (the
+ *     baseline).
+ * Results are bit-identical to pgb_tc_run on each graph alone.  The server
+ * keeps its own CUDA streams and threads on the device current at create;
+ * its threads take device memory from the CUDA stream-ordered allocator
+ * (cudaMallocAsync), not from hooks set with pgb_set_allocator. */
+typedef struct pgb_server pgb_server;
+
+#define PGB_SERVE_BATCHED 0
+#define PGB_SERVE_SERIAL  1
+
+#define PGB_JOB_QUEUED    0
+#define PGB_JOB_RUNNING   1
+#define PGB_JOB_DONE      2
+#define PGB_JOB_FAILED    3
+#define PGB_JOB_CANCELLED 4
+
+typedef struct {
+    uint64_t budget_bytes;    /* HBM admission budget (0 = 64 GiB) */
+    uint32_t max_inflight;    /* jobs staged at once (0 = 8; SERIAL uses 1) */
+    uint32_t p;               /* parts per dimension for each job (0 = 8, capped at n) */
+    int32_t mode;             /* PGB_SERVE_* */
+    int32_t per_vertex;       /* also return per-vertex counts */
+    uint32_t max_batch_jobs;  /* jobs per counting launch (0 = 64, at most 256) */
+    uint32_t reserved[9];
+} pgb_server_opts;
+
+typedef struct {
+    uint64_t submitted, done, failed, cancelled, queued;
+    uint64_t batches;          /* counting launches (BATCHED mode) */
+    uint64_t jobs_in_batches;  /* jobs counted by those launches */
+    uint64_t bytes_in_use;     /* estimated device bytes of admitted jobs */
+} pgb_server_info;
+
+void pgb_server_opts_default(pgb_server_opts* o);
+
+/* The admission estimate of one job's device bytes (m raw edges, n vertices). */
+uint64_t pgb_server_job_bytes(uint64_t m, uint32_t n);
+
+/* Start a server.  Errors: PGB_E_INVAL (bad opts), PGB_E_CUDA. */
+int pgb_server_create(const pgb_server_opts* opts, pgb_server** out);
+
+/* Queue one job; src/dst (m raw pairs, IDs < n) are copied before return.
+ * Errors: PGB_E_BUDGET (the job can never fit the budget), PGB_E_INVAL,
+ * PGB_E_STATE (server shutting down).  Vertex IDs >= n make the job fail. */
+int pgb_server_submit(pgb_server* s, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, int mem,
+                      uint64_t* job_id);
+
+/* Hold (paused != 0) or resume admission: while held, queued jobs stay
+ * queued; jobs already admitted continue. */
+int pgb_server_pause(pgb_server* s, int paused);
+
+/* State of a job (PGB_JOB_*). */
+int pgb_server_poll(pgb_server* s, uint64_t job_id, int* state);
+
+/* Wait (timeout_s < 0: without limit) and fetch: total, per-vertex counts
+ * by original ID into a host array of n (may be NULL), seconds from submit
+ * to completion (may be NULL).  A job that ended is forgotten after this
+ * call.  Errors: PGB_E_TIMEOUT (not finished; the job stays), PGB_E_CANCELLED,
+ * the job's own error if it failed. */
+int pgb_server_wait(pgb_server* s, uint64_t job_id, double timeout_s, uint64_t* total, uint64_t* per_vertex,
+                    double* latency_s);
+
+/* Cancel: a queued job is dropped at once; a job already on the device runs
+ * to its end and its result is dropped (wait returns PGB_E_CANCELLED). */
+int pgb_server_cancel(pgb_server* s, uint64_t job_id);
+
+int pgb_server_stats(pgb_server* s, pgb_server_info* out);
+
+/* Stop: queued jobs are cancelled, jobs on the device finish, threads and
+ * streams are released. */
+void pgb_server_destroy(pgb_server* s);
+
 /* ------------------------------------------------- no-allocation count */
 /* The paper has no counterpart to this call.  It is for callers that must
  * not allocate device memory while they run: code whose host framework

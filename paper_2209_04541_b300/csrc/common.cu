@@ -23,14 +23,20 @@ void note_launches(uint64_t k) { g_launches += k; }
 
 void live_handles_add(int d) { g_live += d; }
 
-void* dev_alloc(size_t bytes, cudaStream_t s) {
+static thread_local bool t_native_only = false;
+
+void use_native_allocator_in_this_thread() { t_native_only = true; }
+
+void* dev_alloc(size_t bytes, cudaStream_t s, bool* native) {
     if (bytes == 0) return nullptr;
     void* p = nullptr;
-    if (g_alloc) {
+    if (g_alloc && !t_native_only) {
+        *native = false;
         p = g_alloc(bytes, s, g_ctx);
         if (!p) fail(PGB_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
         return p;
     }
+    *native = true;
     cudaError_t e = cudaMallocAsync(&p, bytes, s);
     if (e != cudaSuccess || !p) {
         cudaGetLastError();
@@ -40,9 +46,9 @@ void* dev_alloc(size_t bytes, cudaStream_t s) {
     return p;
 }
 
-void dev_free(void* p, size_t bytes, cudaStream_t s) {
+void dev_free(void* p, size_t bytes, cudaStream_t s, bool native) {
     if (!p) return;
-    if (g_free) {
+    if (!native && g_free) {
         g_free(p, bytes, s, g_ctx);
         return;
     }

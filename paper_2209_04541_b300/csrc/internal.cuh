@@ -67,8 +67,15 @@ int guard(F&& f) {
 
 // --------------------------------------------------------------- allocator
 
-void* dev_alloc(size_t bytes, cudaStream_t s);
-void dev_free(void* p, size_t bytes, cudaStream_t s);
+// dev_alloc reports in *native whether the memory came from the CUDA
+// stream-ordered allocator (true) or from the registered hooks (false); the
+// matching dev_free needs that flag.
+void* dev_alloc(size_t bytes, cudaStream_t s, bool* native);
+void dev_free(void* p, size_t bytes, cudaStream_t s, bool native);
+// Make the calling thread use the CUDA stream-ordered allocator even when
+// hooks are registered (for the library's own threads, which must not call
+// back into the host program).
+void use_native_allocator_in_this_thread();
 void live_handles_add(int d);
 
 // Owning device buffer that returns its memory to the library allocator on
@@ -78,6 +85,7 @@ struct DevBuf {
     T* ptr = nullptr;
     size_t count = 0;
     cudaStream_t stream = nullptr;
+    bool native = false;
 
     DevBuf() = default;
     DevBuf(size_t n, cudaStream_t s) { alloc(n, s); }
@@ -97,15 +105,16 @@ struct DevBuf {
         std::swap(ptr, o.ptr);
         std::swap(count, o.count);
         std::swap(stream, o.stream);
+        std::swap(native, o.native);
     }
     void alloc(size_t n, cudaStream_t s) {
         release();
         stream = s;
         count = n;
-        ptr = n ? static_cast<T*>(dev_alloc(n * sizeof(T), s)) : nullptr;
+        ptr = n ? static_cast<T*>(dev_alloc(n * sizeof(T), s, &native)) : nullptr;
     }
     void release() {
-        if (ptr) dev_free(ptr, count * sizeof(T), stream);
+        if (ptr) dev_free(ptr, count * sizeof(T), stream, native);
         ptr = nullptr;
         count = 0;
     }

@@ -114,6 +114,18 @@ _SIGS = {
     "pgb_kernel_launches": (ctypes.c_uint64, []),
     "pgb_tc_count_oriented_noalloc": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, _VP, _VP, _VP, _VP, _VP,
                                                      _VP]),
+    "pgb_server_opts_default": (None, [_VP]),
+    "pgb_server_job_bytes": (ctypes.c_uint64, [ctypes.c_uint64, ctypes.c_uint32]),
+    "pgb_server_create": (ctypes.c_int, [_VP, ctypes.POINTER(_VP)]),
+    "pgb_server_submit": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+    "pgb_server_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+    "pgb_server_pause": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "pgb_server_wait": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64), _VP,
+                                       ctypes.POINTER(ctypes.c_double)]),
+    "pgb_server_cancel": (ctypes.c_int, [_VP, ctypes.c_uint64]),
+    "pgb_server_stats": (ctypes.c_int, [_VP, _VP]),
+    "pgb_server_destroy": (None, [_VP]),
 }
 
 PGB_NOALLOC_MAX_VERTICES = 1 << 20
@@ -452,3 +464,103 @@ def pgb_tc_count_oriented_noalloc(n: int, m: int, rowptr, col, perm, total, per_
             raise ValueError("pgb_tc_count_oriented_noalloc takes device tensors only")
         args.append(ptr)
     _check(load().pgb_tc_count_oriented_noalloc(n, m, *args, _stream(stream)), "pgb_tc_count_oriented_noalloc")
+
+
+# ------------------------------------------------------------------ serve
+
+PGB_SERVE_BATCHED = 0
+PGB_SERVE_SERIAL = 1
+PGB_JOB_QUEUED, PGB_JOB_RUNNING, PGB_JOB_DONE, PGB_JOB_FAILED, PGB_JOB_CANCELLED = range(5)
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32), ("p", ctypes.c_uint32),
+                ("mode", ctypes.c_int32), ("per_vertex", ctypes.c_int32), ("max_batch_jobs", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 9)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "done", "failed", "cancelled", "queued", "batches",
+                                              "jobs_in_batches", "bytes_in_use")]
+
+
+class Server(_Handle):
+    _free_name = "pgb_server_destroy"
+
+    def __init__(self, ptr, per_vertex):
+        super().__init__(ptr, None)
+        self.per_vertex = per_vertex
+        self.n_of = {}
+
+
+def pgb_server_opts_default(**kw) -> ServerOpts:
+    o = ServerOpts()
+    load().pgb_server_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def pgb_server_job_bytes(m: int, n: int) -> int:
+    return int(load().pgb_server_job_bytes(m, n))
+
+
+def pgb_server_create(opts: ServerOpts | None = None) -> Server:
+    opts = opts or pgb_server_opts_default()
+    out = ctypes.c_void_p()
+    _check(load().pgb_server_create(ctypes.byref(opts), ctypes.byref(out)), "pgb_server_create")
+    return Server(out.value, bool(opts.per_vertex))
+
+
+def pgb_server_submit(srv: Server, src, dst, n: int) -> int:
+    ps, ms, ks = _arr(src, np.uint32)
+    pd, md, kd = _arr(dst, np.uint32)
+    if ms != md:
+        raise ValueError("src and dst must live in the same memory")
+    m = 0 if ks is None else int(ks.numel() if hasattr(ks, "numel") else ks.size)
+    jid = ctypes.c_uint64()
+    _check(load().pgb_server_submit(srv, ps, pd, m, n, ms, ctypes.byref(jid)), "pgb_server_submit")
+    srv.n_of[int(jid.value)] = n
+    return int(jid.value)
+
+
+def pgb_server_pause(srv: Server, paused: bool = True):
+    _check(load().pgb_server_pause(srv, int(paused)), "pgb_server_pause")
+
+
+def pgb_server_poll(srv: Server, job: int) -> int:
+    st = ctypes.c_int()
+    _check(load().pgb_server_poll(srv, job, ctypes.byref(st)), "pgb_server_poll")
+    return int(st.value)
+
+
+def pgb_server_wait(srv: Server, job: int, timeout_s: float = -1.0, per_vertex: bool = False):
+    """(total, per-vertex numpy array or None, latency seconds)."""
+    tot = ctypes.c_uint64()
+    lat = ctypes.c_double()
+    pv = None
+    ptr = None
+    if per_vertex:
+        pv = np.zeros(srv.n_of.get(job, 0), np.uint64)
+        ptr = pv.ctypes.data if pv.size else None
+    rc = load().pgb_server_wait(srv, job, timeout_s, ctypes.byref(tot), ptr, ctypes.byref(lat))
+    if rc != PGB_E_TIMEOUT:
+        srv.n_of.pop(job, None)
+    _check(rc, "pgb_server_wait")
+    return int(tot.value), pv, float(lat.value)
+
+
+def pgb_server_cancel(srv: Server, job: int):
+    _check(load().pgb_server_cancel(srv, job), "pgb_server_cancel")
+
+
+def pgb_server_stats(srv: Server) -> dict:
+    info = ServerInfo()
+    _check(load().pgb_server_stats(srv, ctypes.byref(info)), "pgb_server_stats")
+    return {k: int(getattr(info, k)) for k, _ in ServerInfo._fields_}
+
+
+def pgb_server_destroy(srv: Server):
+    srv.free()

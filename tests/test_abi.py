@@ -67,3 +67,22 @@ def test_allocator_pairing_checked():
     fa = pgabb._ALLOC_FN(lambda size, stream, ctx: None)
     ff = ctypes.cast(None, pgabb._FREE_FN)
     assert lib.pgb_set_allocator(fa, ff, None) == pgabb.PGB_E_INVAL
+
+
+def test_server_opts_and_admission_estimate():
+    lib = pgabb.load(register_torch_allocator=False)
+    o = pgabb.pgb_server_opts_default()
+    assert o.mode == pgabb.PGB_SERVE_BATCHED and o.budget_bytes == 64 << 30
+    assert o.max_inflight == 8 and o.per_vertex == 1 and o.max_batch_jobs == 64 and o.p == 8
+    assert ctypes.sizeof(pgabb.ServerOpts) == 64 and ctypes.sizeof(pgabb.ServerInfo) == 64
+    est = pgabb.pgb_server_job_bytes
+    assert 0 < est(0, 0) < est(10, 10) < est(1000, 10) < est(1000, 100000)
+    # bad arguments are refused before any device work
+    bad = pgabb.pgb_server_opts_default(mode=7)
+    out = ctypes.c_void_p()
+    assert lib.pgb_server_create(ctypes.byref(bad), ctypes.byref(out)) == pgabb.PGB_E_INVAL
+    jid = ctypes.c_uint64()
+    assert lib.pgb_server_submit(None, None, None, 0, 0, 0, ctypes.byref(jid)) == pgabb.PGB_E_INVAL
+    st = ctypes.c_int()
+    assert lib.pgb_server_poll(None, 1, ctypes.byref(st)) == pgabb.PGB_E_INVAL
+    lib.pgb_server_destroy(None)

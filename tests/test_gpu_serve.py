@@ -1,0 +1,133 @@
+"""Serve loop on the GPU: each job's counts are exact (bit-identical to the
+oracle) whether it runs alone (SERIAL, one job at a time) or interleaved with
+other jobs in shared persistent launches (BATCHED, continuous batching), and
+the admission, cancel and timeout paths behave as the header states."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from _graphs import messy_random
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2209_04541_b300 import pgabb as P  # noqa: E402
+
+
+def job_mix(seed=0):
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for s in (6, 8, 10, 12, 13):
+        jobs.append(graphgen.rmat(s, int(rng.integers(8, 33)), int(rng.integers(1, 1000))))
+    for n in (50, 1000, 5000):
+        m = int(n * rng.integers(2, 33) // 2)
+        jobs.append(graphgen.er_pairs(n, m, int(rng.integers(1, 1000))))
+    jobs.append(graphgen.rgg(20000, None, 3))
+    jobs.append(graphgen.grid_plus_percent(64, 1.0, 2))
+    src, dst = messy_random(300, 4000, rng)
+    jobs.append((src, dst, 300))
+    e = np.zeros(0, np.uint32)
+    jobs.append((e, e, 0))           # empty graph
+    jobs.append((e, e, 17))          # isolated vertices only
+    loops = np.arange(9, dtype=np.uint32)
+    jobs.append((loops, loops, 9))   # self-loops only
+    return jobs
+
+
+def expected(jobs):
+    out = []
+    for src, dst, n in jobs:
+        g = oracle.clean(src, dst, n)
+        out.append(oracle.tc_node_iterator(g))
+    return out
+
+
+def run_server(jobs, mode, **kw):
+    srv = P.pgb_server_create(P.pgb_server_opts_default(mode=mode, **kw))
+    try:
+        ids = [P.pgb_server_submit(srv, s, d, n) for s, d, n in jobs]
+        res = [P.pgb_server_wait(srv, j, 120.0, per_vertex=True) for j in ids]
+        stats = P.pgb_server_stats(srv)
+    finally:
+        P.pgb_server_destroy(srv)
+    return res, stats
+
+
+def test_serve_alone_and_mixed_match_oracle():
+    jobs = job_mix()
+    want = expected(jobs)
+    batched, st_b = run_server(jobs, P.PGB_SERVE_BATCHED, max_inflight=4, max_batch_jobs=64)
+    serial, st_s = run_server(jobs, P.PGB_SERVE_SERIAL)
+    assert st_b["done"] == len(jobs) and st_s["done"] == len(jobs)
+    assert st_b["jobs_in_batches"] == len(jobs)
+    for (T, t), (bT, bt, blat), (sT, st, slat) in zip(want, batched, serial):
+        assert bT == T and sT == T
+        assert np.array_equal(bt, t) and np.array_equal(st, t)
+        assert blat > 0 and slat > 0
+    # a single job submitted alone gives the same answer as in the mix
+    alone, _ = run_server(jobs[4:5], P.PGB_SERVE_BATCHED)
+    assert alone[0][0] == want[4][0] and np.array_equal(alone[0][1], want[4][1])
+
+
+def test_serve_mixed_batches_share_launches():
+    jobs = [graphgen.rmat(10, 16, s) for s in range(24)]
+    want = expected(jobs)
+    res, st = run_server(jobs, P.PGB_SERVE_BATCHED, max_inflight=8, max_batch_jobs=16)
+    assert st["done"] == len(jobs)
+    assert st["batches"] < len(jobs), "batching should count several jobs per launch"
+    for (T, t), (bT, bt, _) in zip(want, res):
+        assert bT == T and np.array_equal(bt, t)
+
+
+def test_serve_budget_cancel_timeout_and_failures():
+    big = graphgen.rmat(17, 16, 5)
+    small = graphgen.rmat(8, 8, 6)
+    est_big = P.pgb_server_job_bytes(len(big[0]), big[2])
+    srv = P.pgb_server_create(P.pgb_server_opts_default(budget_bytes=est_big + (1 << 20), max_inflight=2))
+    try:
+        # a job that can never fit the budget is refused at submit
+        with pytest.raises(P.PgbError) as ei:
+            P.pgb_server_submit(srv, *graphgen.rmat(19, 16, 1)[:2], 1 << 19)
+        assert ei.value.code == P.PGB_E_BUDGET
+        # with admission held, jobs stay queued: a bounded wait times out and
+        # a queued job can be cancelled
+        P.pgb_server_pause(srv, True)
+        j1 = P.pgb_server_submit(srv, big[0], big[1], big[2])
+        j2 = P.pgb_server_submit(srv, big[0], big[1], big[2])
+        assert P.pgb_server_poll(srv, j1) == P.PGB_JOB_QUEUED
+        with pytest.raises(P.PgbError) as ei:
+            P.pgb_server_wait(srv, j1, 0.05)
+        assert ei.value.code == P.PGB_E_TIMEOUT
+        P.pgb_server_cancel(srv, j2)
+        with pytest.raises(P.PgbError) as ei:
+            P.pgb_server_wait(srv, j2, 60.0)
+        assert ei.value.code == P.PGB_E_CANCELLED
+        P.pgb_server_pause(srv, False)
+        T1, _, _ = P.pgb_server_wait(srv, j1, 120.0)
+        assert T1 == oracle.tc_node_iterator(oracle.clean(*big), per_vertex=False)[0]
+        # a job with a vertex ID >= n fails; the server keeps serving
+        bad = P.pgb_server_submit(srv, np.array([0, 7], np.uint32), np.array([1, 2], np.uint32), 5)
+        with pytest.raises(P.PgbError) as ei:
+            P.pgb_server_wait(srv, bad, 60.0)
+        assert ei.value.code == P.PGB_E_INVAL
+        ok = P.pgb_server_submit(srv, *small)
+        assert P.pgb_server_wait(srv, ok, 60.0)[0] == oracle.tc_node_iterator(oracle.clean(*small), False)[0]
+        st = P.pgb_server_stats(srv)
+        assert st["cancelled"] == 1 and st["failed"] == 1 and st["bytes_in_use"] == 0
+    finally:
+        P.pgb_server_destroy(srv)
+
+
+def test_serve_without_per_vertex():
+    srv = P.pgb_server_create(P.pgb_server_opts_default(per_vertex=0))
+    try:
+        g = graphgen.rmat(9, 8, 3)
+        j = P.pgb_server_submit(srv, *g)
+        with pytest.raises(P.PgbError) as ei:
+            P.pgb_server_wait(srv, j, 60.0, per_vertex=True)
+        assert ei.value.code == P.PGB_E_STATE
+        j = P.pgb_server_submit(srv, *g)
+        assert P.pgb_server_wait(srv, j, 60.0)[0] == oracle.tc_node_iterator(oracle.clean(*g), False)[0]
+    finally:
+        P.pgb_server_destroy(srv)
