@@ -53,6 +53,10 @@ WORKLOADS = {
                      desc="4096x4096 4-neighbour grid + 1% uniform random extra edges; p=32"),
     "er4096": dict(kind="er", n=4096, m=65536, p=4, seed=1,
                    desc="Erdos-Renyi G(n=4096, m=65536) distinct pairs; p=4"),
+    "rgg22": dict(kind="rgg", n=1 << 22, p=32, seed=1,
+                  desc="random geometric graph, n=2^22, average degree about 6; p=32"),
+    "er22": dict(kind="erp", n=1 << 22, m=32 << 22, p=32, seed=1,
+                 desc="Erdos-Renyi, n=2^22, 2^27 uniform pairs (average degree about 64); p=32"),
 }
 
 # CPU-baseline sample: the oracle's whole pipeline on the same generator
@@ -68,6 +72,10 @@ def generate(w, out=None):
         return graphgen.grid_plus_percent(w["side"], w["pct"], w["seed"])
     if w["kind"] == "er":
         return graphgen.er_distinct(w["n"], w["m"], w["seed"])
+    if w["kind"] == "erp":
+        return graphgen.er_pairs(w["n"], w["m"], w["seed"])
+    if w["kind"] == "rgg":
+        return graphgen.rgg(w["n"], None, w["seed"])
     raise ValueError(w)
 
 
@@ -355,6 +363,7 @@ def main(argv=None):
         kms = P.pgb_tc_result_kernel_ms(r)
         if not info:
             info.update(P.pgb_blocks_info(b))
+            info["variant_used"] = P.pgb_tc_result_variant(r)
         r.free()
         b.free()
         return T, kms
@@ -397,7 +406,7 @@ def main(argv=None):
     if mode == P.PGB_MODE_PLAIN:
         kname = "k_tc_tuple"
     else:
-        kname = "k_tc_persistent" if variant == P.PGB_VAR_BSEARCH else "k_tc_hash"
+        kname = "k_tc_persistent" if info["variant_used"] == P.PGB_VAR_BSEARCH else "k_tc_hash"
     achieved = info["alg_bytes"] / (kernel_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_note, "alg_bytes": info["alg_bytes"],

@@ -82,8 +82,7 @@ extern "C" {
 /* ------------------------------------------------- intersection variants */
 /* Section 3.6: "list or hashmap-based" intersection.  Every variant returns
  * the same integers; the choice only changes speed.
- * PGB_VAR_AUTO:    chosen per tuple by the autotuner from block density and
- *                  degree skew.
+ * PGB_VAR_AUTO:    chosen by the autotuner (below).
  * PGB_VAR_BSEARCH: each element of the shorter list is binary-searched in
  *                  the longer one; work is flattened across a warp.
  * PGB_VAR_MERGE:   warp-cooperative merge of 32-element chunks.
@@ -92,9 +91,13 @@ extern "C" {
  *                  third-vertex rank range when that range is at most
  *                  262,144 ranks, else a hash table) and the lists of v's
  *                  in-neighbours after v are streamed through it.
- * PGB_VAR_AUTO runs PGB_VAR_HASH in PERSISTENT mode and PGB_VAR_BSEARCH in
- * PLAIN mode; within the hash form the bitmap or table is chosen per work
- * item from the width of its rank range. */
+ * Autotuner (PGB_VAR_AUTO): PLAIN mode runs PGB_VAR_BSEARCH.  PERSISTENT
+ * mode runs PGB_VAR_HASH when the graph averages at least 32 lookups per
+ * oriented edge (probes >= 32 |E+|, see pgb_blocks_stats: long lists, skewed
+ * degrees) and PGB_VAR_BSEARCH otherwise (flat graphs with short lists).
+ * Within the hash form the bitmap or table, and the split of heavy middle
+ * vertices into in-edge chunks and key-range slices, are chosen per work
+ * item from its rank range, list length and in-degree. */
 #define PGB_VAR_AUTO    0
 #define PGB_VAR_BSEARCH 1
 #define PGB_VAR_MERGE   2
@@ -223,6 +226,9 @@ int pgb_tc_result_get(pgb_tc_result* r, uint64_t* total, uint64_t* per_vertex, i
 
 /* PLAIN mode with per_triple = 1: counts[t] for queue entry t (T entries). */
 int pgb_tc_result_triples(pgb_tc_result* r, uint64_t* counts, int mem);
+
+/* The variant that ran (PGB_VAR_BSEARCH or PGB_VAR_HASH). */
+int pgb_tc_result_variant(pgb_tc_result* r, int* variant);
 
 /* Device time of the counting kernels of this run in milliseconds (CUDA
  * events around the launches on the run's stream); valid after get. */

@@ -264,6 +264,7 @@ struct pgb_tc_result {
     bool per_vertex = false;
     bool per_triple = false;
     uint64_t ntriples = 0;
+    int variant = PGB_VAR_BSEARCH;  // the variant that ran
     pgb::DevBuf<unsigned long long> total;
     pgb::DevBuf<unsigned long long> tv_orig;
     pgb::DevBuf<unsigned long long> triple_counts;
@@ -289,7 +290,25 @@ static Tuple make_tuple(const pgb_blocks* b, uint32_t i, uint32_t j, uint32_t k0
     return t;
 }
 
-static void run(const pgb_blocks* b, const pgb_tc_opts& o, cudaStream_t s, pgb_tc_result* r) {
+// Autotuner (run level).  The middle-vertex hash kernel pays a fixed cost
+// per work item and wins when lists are long; the edge-wise binary-search
+// kernel wins on flat graphs with short lists.  The graph statistic that
+// separates them is the average number of lookups per oriented edge (the
+// entries of the tail's row after the head): measured on one B300 the hash
+// kernel is 5-10x faster on R-MAT (78-160 lookups per edge) and 1.6-18x
+// slower on Erdos-Renyi (19), random geometric (1.5) and grid (0.55) graphs.
+constexpr uint64_t kHashMinLookupsPerEdge = 32;
+
+static int choose_variant(const pgb_blocks* b, const pgb_tc_opts& o) {
+    if (o.mode == PGB_MODE_PLAIN) return PGB_VAR_BSEARCH;
+    if (o.variant != PGB_VAR_AUTO) return o.variant;
+    return b->probes >= kHashMinLookupsPerEdge * b->m ? PGB_VAR_HASH : PGB_VAR_BSEARCH;
+}
+
+static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pgb_tc_result* r) {
+    pgb_tc_opts o = o_in;
+    o.variant = choose_variant(b, o_in);
+    r->variant = o.variant;
     const uint32_t n = b->n;
     r->stream = s;
     r->n = n;
@@ -344,7 +363,7 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o, cudaStream_t s, pgb_t
             k_reduce_segments<<<(unsigned)T, 256, 0, s>>>(partials.ptr, dseg.ptr, r->triple_counts.ptr);
             PGB_CHECK_LAUNCH("k_reduce_segments");
         }
-    } else if (o.variant != PGB_VAR_BSEARCH) {
+    } else if (o.variant == PGB_VAR_HASH) {
         // middle-vertex hash variant (tc_hash.cu)
         HashGraph H{b->rowptr.ptr, b->col.ptr, b->rowidx.ptr, b->colptr.ptr, b->xr.ptr, tv.ptr, b->n};
         run_hash(b, H, r->per_vertex, o.chunk_edges, s, partials, npartials, r->ev0, r->ev1, nullptr);
@@ -468,6 +487,13 @@ int pgb_tc_result_triples(pgb_tc_result* r, uint64_t* counts, int mem) {
         if (!r->per_triple) fail(PGB_E_STATE, "run was not PLAIN with per_triple = 1");
         copy_out(counts, r->triple_counts.ptr, r->ntriples * 8, mem, r->stream);
         PGB_CUDA(cudaStreamSynchronize(r->stream));
+    });
+}
+
+int pgb_tc_result_variant(pgb_tc_result* r, int* variant) {
+    return guard([&] {
+        if (!r || !variant) fail(PGB_E_INVAL, "NULL argument");
+        *variant = r->variant;
     });
 }
 

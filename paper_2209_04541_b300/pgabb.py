@@ -105,6 +105,7 @@ _SIGS = {
     "pgb_tc_result_get": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), _VP, ctypes.c_int]),
     "pgb_tc_result_triples": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "pgb_tc_result_kernel_ms": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "pgb_tc_result_variant": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "pgb_tc_result_free": (None, [_VP]),
     "pgb_tc_count_edges": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                           ctypes.c_int, ctypes.POINTER(TcOpts), ctypes.c_int, _VP,
@@ -413,6 +414,12 @@ def pgb_tc_result_kernel_ms(r: Result) -> float:
     ms = ctypes.c_float()
     _check(load().pgb_tc_result_kernel_ms(r, ctypes.byref(ms)), "pgb_tc_result_kernel_ms")
     return float(ms.value)
+
+
+def pgb_tc_result_variant(r: Result) -> int:
+    v = ctypes.c_int()
+    _check(load().pgb_tc_result_variant(r, ctypes.byref(v)), "pgb_tc_result_variant")
+    return int(v.value)
 
 
 def pgb_tc_result_free(r: Result):
