@@ -196,6 +196,29 @@ int pgb_blocks_export(const pgb_blocks* b, int what, void* dst, int mem, void* s
 
 void pgb_blocks_free(pgb_blocks* b);
 
+/* Streaming tier (Section 4.4: the scheduler copies a task's blocks to the
+ * device asynchronously while other tasks compute; Section 1: graphs that fit
+ * in host DRAM but not in device memory).  Moves the in-edge index -- for
+ * every oriented edge, grouped by head v, the range of the tail's row after
+ * v (8 bytes) and the tail (4 bytes), 12 bytes per edge -- into pinned host
+ * memory owned by `b`, and frees it and the edge-wise kernels' arrays (row
+ * index, block edge index) on the device.  What stays resident is what the
+ * counting kernel reads at random: row offsets, columns, in-edge offsets and
+ * the rank permutation (about 4|E+| + 12n bytes).  Later runs on `b` stream
+ * the index in chunks (see device_budget) and must use PGB_MODE_PERSISTENT
+ * with PGB_VAR_AUTO or PGB_VAR_HASH (else PGB_E_STATE).  Synchronises
+ * `stream`.  Calling it twice is a no-op.  Errors: PGB_E_INVAL (NULL),
+ * PGB_E_NOMEM (pinned allocation), PGB_E_CUDA. */
+int pgb_blocks_offload(pgb_blocks* b, void* stream);
+
+/* The device bytes a streamed run on `b` holds besides its two stream slots:
+ * 4(n+1) + 4(m+4) + 4(n+1) + 4n + 4(p+1) for the resident arrays, 16n for the
+ * per-vertex counters when per_vertex != 0, and 16 MiB for the launches'
+ * partial sums.  A device_budget must exceed it; the rest is split into two
+ * slots of 44 bytes per in-edge (index entry plus one work item bound).
+ * Errors: PGB_E_INVAL (NULL). */
+int pgb_blocks_resident_bytes(const pgb_blocks* b, int per_vertex, uint64_t* bytes);
+
 /* ------------------------------------------------------------------ run */
 typedef struct {
     int32_t mode;          /* PGB_MODE_* (default PGB_MODE_PERSISTENT) */
@@ -204,7 +227,12 @@ typedef struct {
     int32_t per_triple;    /* PLAIN mode: keep one count per queued triple */
     int32_t use_graph;     /* capture the launches in a CUDA graph (default 0) */
     int32_t order;         /* PGB_ORDER_* (default PGB_ORDER_WEIGHT) */
-    uint64_t device_budget;/* bytes for resident blocks; 0 = no limit */
+    uint64_t device_budget;/* offloaded blocks only: device bytes the run may
+                              hold (resident arrays, counters, and two stream
+                              slots that get the rest); 0 = 1 GiB slots.  A
+                              budget below the resident arrays, or one whose
+                              slots cannot hold the largest work item, gives
+                              PGB_E_BUDGET.  Ignored for resident blocks. */
     uint32_t chunk_edges;  /* PERSISTENT: binary-search variant: edges per
                               dequeued chunk; hash variant: in-edges per work
                               item (0 = default) */
@@ -230,8 +258,13 @@ int pgb_tc_result_triples(pgb_tc_result* r, uint64_t* counts, int mem);
 /* The variant that ran (PGB_VAR_BSEARCH or PGB_VAR_HASH). */
 int pgb_tc_result_variant(pgb_tc_result* r, int* variant);
 
+/* Streamed runs: host-to-device bytes copied (in-edge index slices and work
+ * items) and the number of chunks; both 0 for a run on resident blocks. */
+int pgb_tc_result_stream(pgb_tc_result* r, uint64_t* bytes, uint32_t* chunks);
+
 /* Device time of the counting kernels of this run in milliseconds (CUDA
- * events around the launches on the run's stream); valid after get. */
+ * events around the launches on the run's stream; for a streamed run this
+ * includes the copies it waits for); valid after get. */
 int pgb_tc_result_kernel_ms(pgb_tc_result* r, float* ms);
 
 void pgb_tc_result_free(pgb_tc_result* r);

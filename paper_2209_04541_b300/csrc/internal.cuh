@@ -154,6 +154,15 @@ struct pgb_blocks {
     uint32_t n = 0, p = 0;
     uint64_t m = 0;
     cudaStream_t stream = nullptr;
+    // offloaded in-edge index (pgb_blocks_offload): per in-edge the tail-row
+    // range after the head (xr) and the tail, in pinned host memory
+    bool offloaded = false;
+    unsigned long long* h_xr = nullptr;
+    uint32_t* h_itail = nullptr;
+    ~pgb_blocks() {
+        if (h_xr) cudaFreeHost(h_xr);
+        if (h_itail) cudaFreeHost(h_itail);
+    }
     pgb::DevBuf<uint32_t> perm;    // rank -> original ID
     pgb::DevBuf<uint32_t> rowptr;  // n + 1 oriented offsets (m < 2^32)
     pgb::DevBuf<uint32_t> col;     // m oriented columns, rank space, rows sorted

@@ -265,6 +265,8 @@ struct pgb_tc_result {
     bool per_triple = false;
     uint64_t ntriples = 0;
     int variant = PGB_VAR_BSEARCH;  // the variant that ran
+    uint64_t streamed = 0;          // host-to-device bytes of a streamed run
+    uint32_t chunks = 0;            // stream chunks of a streamed run (0 = resident)
     pgb::DevBuf<unsigned long long> total;
     pgb::DevBuf<unsigned long long> tv_orig;
     pgb::DevBuf<unsigned long long> triple_counts;
@@ -301,6 +303,7 @@ constexpr uint64_t kHashMinLookupsPerEdge = 32;
 
 static int choose_variant(const pgb_blocks* b, const pgb_tc_opts& o) {
     if (o.mode == PGB_MODE_PLAIN) return PGB_VAR_BSEARCH;
+    if (b->offloaded) return PGB_VAR_HASH;  // only the hash kernel reads a streamed index
     if (o.variant != PGB_VAR_AUTO) return o.variant;
     return b->probes >= kHashMinLookupsPerEdge * b->m ? PGB_VAR_HASH : PGB_VAR_BSEARCH;
 }
@@ -325,7 +328,7 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
         if (n) PGB_CUDA(cudaMemsetAsync(tv.ptr, 0, (size_t)n * 8, s));
     }
     // the edge-wise (binary-search) kernels walk edges block by block
-    if (o.mode == PGB_MODE_PLAIN || o.variant == PGB_VAR_BSEARCH) ensure_block_edge_index(b, s);
+    if (!b->offloaded && (o.mode == PGB_MODE_PLAIN || o.variant == PGB_VAR_BSEARCH)) ensure_block_edge_index(b, s);
     Graph G{b->bedge.ptr, b->rowidx.ptr, b->col.ptr, b->rowptr.ptr, tv.ptr};
 
     DevBuf<unsigned long long> partials;
@@ -363,6 +366,10 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
             k_reduce_segments<<<(unsigned)T, 256, 0, s>>>(partials.ptr, dseg.ptr, r->triple_counts.ptr);
             PGB_CHECK_LAUNCH("k_reduce_segments");
         }
+    } else if (b->offloaded) {
+        // in-edge index in pinned host memory, streamed in chunks (stream.cu)
+        run_streaming(b, o.chunk_edges, r->per_vertex, tv.ptr, o.device_budget, s, partials, npartials, r->ev0,
+                      r->ev1, &r->streamed, &r->chunks);
     } else if (o.variant == PGB_VAR_HASH) {
         // middle-vertex hash variant (tc_hash.cu)
         HashGraph H{b->rowptr.ptr, b->col.ptr, b->rowidx.ptr, b->colptr.ptr, b->xr.ptr, tv.ptr, b->n};
@@ -456,6 +463,8 @@ int pgb_tc_run(const pgb_blocks* b, const pgb_tc_opts* opts, void* stream, pgb_t
         if (o.mode == PGB_MODE_PLAIN && o.variant == PGB_VAR_HASH)
             fail(PGB_E_INVAL, "PLAIN mode runs the binary-search variant only");
         if (o.order != PGB_ORDER_WEIGHT && o.order != PGB_ORDER_LOCALITY) fail(PGB_E_INVAL, "bad order");
+        if (b->offloaded && (o.mode != PGB_MODE_PERSISTENT || o.variant == PGB_VAR_BSEARCH))
+            fail(PGB_E_STATE, "offloaded blocks run in PERSISTENT mode with the hash variant only");
         std::unique_ptr<pgb_tc_result> r(new pgb_tc_result());
         run(b, o, (cudaStream_t)stream, r.get());
         live_handles_add(1);
@@ -494,6 +503,14 @@ int pgb_tc_result_variant(pgb_tc_result* r, int* variant) {
     return guard([&] {
         if (!r || !variant) fail(PGB_E_INVAL, "NULL argument");
         *variant = r->variant;
+    });
+}
+
+int pgb_tc_result_stream(pgb_tc_result* r, uint64_t* bytes, uint32_t* chunks) {
+    return guard([&] {
+        if (!r || !bytes || !chunks) fail(PGB_E_INVAL, "NULL argument");
+        *bytes = r->streamed;
+        *chunks = r->chunks;
     });
 }
 

@@ -440,7 +440,10 @@ __global__ void __launch_bounds__(kHThreads, 4)
                 const uint32_t c = s_edge[warp][lane];
                 if (c) {
                     s_edge[warp][lane] = 0;
-                    atomicAdd(G.tv + __ldg(G.rowidx + e), (unsigned long long)c);
+                    // the tail u: from the streamed per-in-edge tails when the
+                    // row index is not resident, else from the row index
+                    const uint32_t u = G.itail ? __ldg(G.itail + idx) : __ldg(G.rowidx + e);
+                    atomicAdd(G.tv + u, (unsigned long long)c);
                     atomicAdd(&s_vcnt[31 - __clz(vbit)], c);
                 }
                 __syncwarp();

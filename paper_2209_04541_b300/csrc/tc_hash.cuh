@@ -13,6 +13,7 @@ struct HashGraph {
     const unsigned long long* __restrict__ xr;
     unsigned long long* __restrict__ tv;  // per-vertex counts, rank space (may be null)
     uint32_t n;                           // vertices
+    const uint32_t* __restrict__ itail = nullptr;  // tail of each in-edge (streamed runs), else null
 };
 
 // One work item of the middle-vertex kernel (built on the device).
@@ -53,5 +54,13 @@ void launch_hash(const HashGraph* d_graphs, uint32_t njobs, const VItem* items, 
 void run_hash(const pgb_blocks* b, const HashGraph& G, bool pv, uint32_t in_chunk, cudaStream_t s,
               DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0, cudaEvent_t ev1,
               HashRunStats* stats);
+
+// Streamed run over blocks whose in-edge index is in pinned host memory:
+// chunks of work items whose in-edges fit two device slots within `budget`
+// bytes (0 = 1 GiB slots), copied on a side stream while the previous chunk
+// counts on `s`.  Returns after the work completes.
+void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, unsigned long long* tv, uint64_t budget,
+                   cudaStream_t s, DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
+                   cudaEvent_t ev1, uint64_t* streamed, uint32_t* nchunks);
 
 }  // namespace pgb

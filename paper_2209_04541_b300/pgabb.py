@@ -100,12 +100,15 @@ _SIGS = {
     "pgb_blocks_info": (ctypes.c_int, [_VP, ctypes.POINTER(BlocksStats)]),
     "pgb_blocks_export": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, _VP]),
     "pgb_blocks_free": (None, [_VP]),
+    "pgb_blocks_offload": (ctypes.c_int, [_VP, _VP]),
+    "pgb_blocks_resident_bytes": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
     "pgb_tc_opts_default": (None, [ctypes.POINTER(TcOpts)]),
     "pgb_tc_run": (ctypes.c_int, [_VP, ctypes.POINTER(TcOpts), _VP, ctypes.POINTER(_VP)]),
     "pgb_tc_result_get": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), _VP, ctypes.c_int]),
     "pgb_tc_result_triples": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "pgb_tc_result_kernel_ms": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "pgb_tc_result_variant": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "pgb_tc_result_stream": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)]),
     "pgb_tc_result_free": (None, [_VP]),
     "pgb_tc_count_edges": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                           ctypes.c_int, ctypes.POINTER(TcOpts), ctypes.c_int, _VP,
@@ -367,6 +370,12 @@ def pgb_blocks_free(b: Blocks):
     b.free()
 
 
+def pgb_blocks_offload(b: Blocks, stream=None):
+    """Move the in-edge index of ``b`` to pinned host memory (streamed runs)."""
+    st = _stream(stream) if stream is not None else b.stream
+    _check(load().pgb_blocks_offload(b, st), "pgb_blocks_offload")
+
+
 def pgb_tc_opts_default(**kw) -> TcOpts:
     o = TcOpts()
     load().pgb_tc_opts_default(ctypes.byref(o))
@@ -420,6 +429,20 @@ def pgb_tc_result_variant(r: Result) -> int:
     v = ctypes.c_int()
     _check(load().pgb_tc_result_variant(r, ctypes.byref(v)), "pgb_tc_result_variant")
     return int(v.value)
+
+
+def pgb_blocks_resident_bytes(b: Blocks, per_vertex: bool = True) -> int:
+    """Device bytes a streamed run holds besides its two slots."""
+    v = ctypes.c_uint64()
+    _check(load().pgb_blocks_resident_bytes(b, int(per_vertex), ctypes.byref(v)), "pgb_blocks_resident_bytes")
+    return int(v.value)
+
+
+def pgb_tc_result_stream(r: Result) -> tuple[int, int]:
+    """(bytes copied host to device, chunks) of a streamed run; (0, 0) otherwise."""
+    nb, nc = ctypes.c_uint64(), ctypes.c_uint32()
+    _check(load().pgb_tc_result_stream(r, ctypes.byref(nb), ctypes.byref(nc)), "pgb_tc_result_stream")
+    return int(nb.value), int(nc.value)
 
 
 def pgb_tc_result_free(r: Result):

@@ -44,6 +44,10 @@ def test_version_and_errors_without_gpu():
     assert lib.pgb_graph_from_edges(None, None, 5, 10, 0, None, ctypes.byref(out)) == pgabb.PGB_E_INVAL
     assert lib.pgb_graph_from_edges(None, None, 0, 10, 7, None, ctypes.byref(out)) == pgabb.PGB_E_INVAL
     assert lib.pgb_tc_result_get(None, None, None, 0) == pgabb.PGB_E_INVAL
+    assert lib.pgb_blocks_offload(None, None) == pgabb.PGB_E_INVAL
+    u64, u32 = ctypes.c_uint64(), ctypes.c_uint32()
+    assert lib.pgb_blocks_resident_bytes(None, 1, ctypes.byref(u64)) == pgabb.PGB_E_INVAL
+    assert lib.pgb_tc_result_stream(None, ctypes.byref(u64), ctypes.byref(u32)) == pgabb.PGB_E_INVAL
     # freeing NULL handles is a no-op
     lib.pgb_graph_free(None)
     lib.pgb_blocks_free(None)
