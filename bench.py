@@ -312,6 +312,60 @@ def h2d_gbs(torch, nbytes=1 << 30, reps=5):
     return nbytes * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
 
 
+def tiers_bench(args):
+    """The runtime tiers on one partition each of R-MAT s24 and the grid
+    (count phase only, the partition built once): launch per block triple
+    versus the persistent autotuned kernel, each with and without CUDA-graph
+    replay.  Per-vertex counts on, written to a device tensor."""
+    import torch
+    from paper_2209_04541_b300 import pgabb as P
+    out = {}
+    for name in args.tiers_workloads.split(","):
+        w = dict(WORKLOADS[name])
+        s_np, d_np, n = generate(w)
+        stream = torch.cuda.current_stream()
+        g = P.pgb_graph_from_edges(torch.from_numpy(s_np).cuda(), torch.from_numpy(d_np).cuda(), n, stream)
+        del s_np, d_np
+        b = P.pgb_partition(g, w["p"], P.PGB_CUT_NNZ, stream)
+        g.free()
+        info = P.pgb_blocks_info(b)
+        tv = torch.zeros(n, dtype=torch.uint64, device="cuda")
+        rows = {}
+        T0 = None
+        for label, kw in (("plain", dict(mode=P.PGB_MODE_PLAIN)),
+                          ("plain+graph", dict(mode=P.PGB_MODE_PLAIN, use_graph=1)),
+                          ("persistent-auto", dict()),
+                          ("persistent-auto+graph", dict(use_graph=1))):
+            o = P.pgb_tc_opts_default(**kw)
+            walls, kms = [], []
+            for i in range(2 + args.tiers_steps):
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                r = P.pgb_tc_run(b, o, stream)
+                T, _ = P.pgb_tc_result_get(r, per_vertex=tv)
+                wall = time.perf_counter() - t
+                if i >= 2:
+                    walls.append(wall)
+                    kms.append(P.pgb_tc_result_kernel_ms(r))
+                var = P.pgb_tc_result_variant(r)
+                r.free()
+                T0 = T if T0 is None else T0
+                assert T == T0, "tiers disagree"
+            wall = statistics.median(walls)
+            rows[label] = {"edges_s": info["m"] / wall, "wall_ms": 1e3 * wall,
+                           "device_ms": statistics.median(kms),
+                           "kernel": "k_tc_hash" if var == P.PGB_VAR_HASH else
+                                     ("k_tc_tuple" if "plain" in label else "k_tc_persistent")}
+        b.free()
+        del tv
+        torch.cuda.empty_cache()
+        out[name] = {"workload": w["desc"], "unique_edges": info["m"], "triples": info["triples"],
+                     "triangles": T0, "tiers": rows}
+    return {"metric": "count-phase edges/s by runtime tier", "steps": args.tiers_steps,
+            "note": "device_ms: CUDA events around the counting launches (a replayed graph: the whole graph)",
+            "workloads": out}
+
+
 def stream_bench(args):
     """The streaming tier: count with the in-edge index in pinned host memory
     and a device budget, against the same graph fully resident."""
@@ -395,6 +449,9 @@ def main(argv=None):
     ap.add_argument("--serve-jobs", type=int, default=300)
     ap.add_argument("--serve-max-scale", type=int, default=18)
     ap.add_argument("--no-stream", action="store_true")
+    ap.add_argument("--no-tiers", action="store_true")
+    ap.add_argument("--tiers-workloads", default="rmat24,grid4096")
+    ap.add_argument("--tiers-steps", type=int, default=3)
     ap.add_argument("--stream-workload", choices=["rmat24", "rmat22", "rmat27"], default="rmat24")
     ap.add_argument("--stream-budget-gb", type=float, default=2.0)
     ap.add_argument("--stream-steps", type=int, default=3)
@@ -531,6 +588,12 @@ def main(argv=None):
             serve = serve_bench(args)
         except Exception as exc:  # reported, not hidden: the TC line stands on its own
             serve = {"error": f"{type(exc).__name__}: {exc}"}
+    tiers = None
+    if rank == 0 and not args.no_tiers:
+        try:
+            tiers = tiers_bench(args)
+        except Exception as exc:  # reported, not hidden
+            tiers = {"error": f"{type(exc).__name__}: {exc}"}
     streamed = None
     if rank == 0 and not args.no_stream:
         try:
@@ -552,7 +615,7 @@ def main(argv=None):
                                  % (8 * mraw / 1e9, 8 * m_u / 1e9)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "gpu_launches_per_step": launches / args.steps,
-                "clocks": clocks, "serve": serve, "stream": streamed}
+                "clocks": clocks, "serve": serve, "tiers": tiers, "stream": streamed}
         print(json.dumps(line), flush=True)
     if dist.is_initialized():
         dist.destroy_process_group()

@@ -19,7 +19,15 @@ static void* g_ctx = nullptr;
 static std::atomic<long> g_live{0};
 static std::atomic<uint64_t> g_launches{0};
 
-void note_launches(uint64_t k) { g_launches += k; }
+static thread_local uint64_t* t_capture_count = nullptr;
+
+void note_launches(uint64_t k) {
+    if (t_capture_count) *t_capture_count += k;
+    else g_launches += k;
+}
+
+void begin_launch_capture(uint64_t* counter) { t_capture_count = counter; }
+void end_launch_capture() { t_capture_count = nullptr; }
 
 void live_handles_add(int d) { g_live += d; }
 

@@ -47,6 +47,10 @@ void set_error(const std::string& msg);
 #define PGB_CHECK_LAUNCH(what) PGB_CHECK_LAUNCHES(what, 1)
 
 void note_launches(uint64_t k);
+// While a capture is open in this thread, launches are counted into
+// *counter instead (a captured launch runs only when the graph is replayed).
+void begin_launch_capture(uint64_t* counter);
+void end_launch_capture();
 
 template <class F>
 int guard(F&& f) {
@@ -159,6 +163,11 @@ struct pgb_blocks {
     bool offloaded = false;
     unsigned long long* h_xr = nullptr;
     uint32_t* h_itail = nullptr;
+    // chunking of the last streamed run's settings (stream.cu)
+    mutable std::shared_ptr<void> stream_plan;
+    // captured runs (use_graph), at most four settings (tc.cu)
+    mutable std::vector<std::shared_ptr<void>> run_plans;
+    mutable std::mutex plan_mu;
     ~pgb_blocks() {
         if (h_xr) cudaFreeHost(h_xr);
         if (h_itail) cudaFreeHost(h_itail);

@@ -46,31 +46,35 @@ static uint64_t resident_bytes(const pgb_blocks* b, bool pv) {
            kPartialsReserve;
 }
 
-void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, unsigned long long* tv, uint64_t budget,
-                   cudaStream_t s, DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
-                   cudaEvent_t ev1, uint64_t* streamed, uint32_t* nchunks_out) {
-    npartials = 0;
-    *streamed = 0;
-    *nchunks_out = 0;
-    DevBuf<VItem> ditems;
-    const uint32_t nitems = build_hash_items(b, 0, in_chunk, s, ditems);
-    if (nitems == 0) {
-        PGB_CUDA(cudaEventRecord(ev0, s));
-        PGB_CUDA(cudaEventRecord(ev1, s));
-        return;
+// The chunking of one (work-item size, budget, per-vertex) setting, kept on
+// the blocks handle: building it needs the items on the host once.
+struct StreamPlan {
+    struct Chunk {
+        uint32_t first, count, base, span;  // items [first, first+count), in-edges [base, base+span)
+    };
+    uint32_t in_chunk = 0;
+    uint64_t budget = 0;
+    bool pv = false;
+    int grid = 0;
+    std::vector<Chunk> chunks;
+    VItem* h_items = nullptr;  // pinned, in-edge ranges relative to their chunk's base
+    uint32_t nitems = 0, max_items = 0;
+    uint64_t slot_edges = 0;
+    ~StreamPlan() {
+        if (h_items) cudaFreeHost(h_items);
     }
-    // work items in in-edge order; a chunk is a run of items whose in-edge
-    // span fits one slot
-    std::vector<VItem> items(nitems);
-    PGB_CUDA(cudaMemcpyAsync(items.data(), ditems.ptr, (size_t)nitems * sizeof(VItem), cudaMemcpyDeviceToHost, s));
-    PGB_CUDA(cudaStreamSynchronize(s));
-    ditems.release();
-    std::stable_sort(items.begin(), items.end(),
-                     [](const VItem& x, const VItem& y) { return x.in_begin < y.in_begin; });
+};
+
+static std::shared_ptr<StreamPlan> make_plan(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint64_t budget,
+                                             cudaStream_t s) {
+    auto P = std::make_shared<StreamPlan>();
+    P->in_chunk = in_chunk;
+    P->budget = budget;
+    P->pv = pv;
+    P->grid = hash_grid(pv);
     // the budget covers everything the run holds on the device: the resident
     // arrays, the per-vertex counters, the per-launch partials (bounded by
     // kPartialsReserve) and the two stream slots
-    const int grid = hash_grid(pv);
     const uint64_t resident = resident_bytes(b, pv);
     uint64_t slot_bytes = kDefaultSlotBytes;
     if (budget) {
@@ -80,13 +84,22 @@ void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, unsigned lon
         slot_bytes = (budget - resident) / 2;
     }
     const uint64_t cap = slot_bytes / (kStreamBytesPerInEdge + sizeof(VItem));  // in-edges per slot
-    struct Chunk {
-        uint32_t first, count, base, span;
-    };
-    std::vector<Chunk> chunks;
-    uint32_t max_items = 0;
+    DevBuf<VItem> ditems;
+    const uint32_t nitems = build_hash_items(b, 0, in_chunk, s, ditems);
+    P->nitems = nitems;
+    if (nitems == 0) return P;
+    std::vector<VItem> items(nitems);
+    PGB_CUDA(cudaMemcpyAsync(items.data(), ditems.ptr, (size_t)nitems * sizeof(VItem), cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaStreamSynchronize(s));
+    ditems.release();
+    // work items in in-edge order; a chunk is a run of items whose in-edge
+    // span fits one slot
+    if (!std::is_sorted(items.begin(), items.end(),
+                        [](const VItem& x, const VItem& y) { return x.in_begin < y.in_begin; }))
+        std::stable_sort(items.begin(), items.end(),
+                         [](const VItem& x, const VItem& y) { return x.in_begin < y.in_begin; });
     for (uint32_t i = 0; i < nitems;) {
-        Chunk c{i, 0, items[i].in_begin, 0};
+        StreamPlan::Chunk c{i, 0, items[i].in_begin, 0};
         uint32_t end = items[i].in_end;
         // a slot holds the chunk's in-edges and its items; sizing both by
         // the larger of the two counts keeps the two slot arrays fixed
@@ -107,77 +120,113 @@ void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, unsigned lon
             items[k].in_begin -= c.base;
             items[k].in_end -= c.base;
         }
-        max_items = std::max(max_items, c.count);
-        chunks.push_back(c);
+        P->max_items = std::max(P->max_items, c.count);
+        P->slot_edges = std::max<uint64_t>(P->slot_edges, c.span);
+        P->chunks.push_back(c);
         i = j;
     }
-    // items in pinned memory so their copies are asynchronous
-    VItem* h_items = nullptr;
-    PGB_CUDA(cudaHostAlloc(&h_items, (size_t)nitems * sizeof(VItem), cudaHostAllocDefault));
-    std::unique_ptr<VItem, cudaError_t (*)(void*)> h_items_guard(h_items, cudaFreeHost);
-    std::memcpy(h_items, items.data(), (size_t)nitems * sizeof(VItem));
-
-    if ((uint64_t)grid * chunks.size() * 8 > kPartialsReserve)
-        fail(PGB_E_BUDGET, "device_budget leaves stream slots too small: " + std::to_string(chunks.size()) +
+    if ((uint64_t)P->grid * P->chunks.size() * 8 > kPartialsReserve)
+        fail(PGB_E_BUDGET, "device_budget leaves stream slots too small: " + std::to_string(P->chunks.size()) +
                                " chunks");
-    uint64_t slot_edges = 0;
-    for (const Chunk& ch : chunks) slot_edges = std::max<uint64_t>(slot_edges, ch.span);
+    // items in pinned memory so that their copies are asynchronous
+    PGB_CUDA(cudaHostAlloc(&P->h_items, (size_t)nitems * sizeof(VItem), cudaHostAllocDefault));
+    std::memcpy(P->h_items, items.data(), (size_t)nitems * sizeof(VItem));
+    return P;
+}
+
+static std::shared_ptr<StreamPlan> get_plan(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint64_t budget,
+                                            cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(b->plan_mu);
+    auto P = std::static_pointer_cast<StreamPlan>(b->stream_plan);
+    if (!P || P->in_chunk != in_chunk || P->budget != budget || P->pv != pv) {
+        P = make_plan(b, in_chunk, pv, budget, s);
+        b->stream_plan = P;
+    }
+    return P;
+}
+
+void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, unsigned long long* tv, uint64_t budget,
+                   cudaStream_t s, DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
+                   cudaEvent_t ev1, uint64_t* streamed, uint32_t* nchunks_out) {
+    npartials = 0;
+    *streamed = 0;
+    *nchunks_out = 0;
+    const std::shared_ptr<StreamPlan> P = get_plan(b, in_chunk, pv, budget, s);
+    if (P->nitems == 0) {
+        PGB_CUDA(cudaEventRecord(ev0, s));
+        PGB_CUDA(cudaEventRecord(ev1, s));
+        return;
+    }
+    const uint64_t slot_edges = P->slot_edges;
+    const uint32_t max_items = P->max_items;
+    const int grid = P->grid;
     DevBuf<unsigned long long> sxr[2] = {DevBuf<unsigned long long>(slot_edges, s),
                                          DevBuf<unsigned long long>(slot_edges, s)};
     DevBuf<uint32_t> stail[2] = {DevBuf<uint32_t>(slot_edges, s), DevBuf<uint32_t>(slot_edges, s)};
     DevBuf<VItem> sitems[2] = {DevBuf<VItem>(max_items, s), DevBuf<VItem>(max_items, s)};
-    DevBuf<HashGraph> sg[2] = {DevBuf<HashGraph>(1, s), DevBuf<HashGraph>(1, s)};
-    DevBuf<unsigned int> cursor[2] = {DevBuf<unsigned int>(1, s), DevBuf<unsigned int>(1, s)};
+    DevBuf<HashGraph> sg(2, s);
+    DevBuf<unsigned int> cursor(2, s);
     HashGraph hg[2];
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 2; ++k)
         hg[k] = HashGraph{b->rowptr.ptr, b->col.ptr, nullptr, b->colptr.ptr, sxr[k].ptr, tv, b->n, stail[k].ptr};
-        PGB_CUDA(cudaMemcpyAsync(sg[k].ptr, &hg[k], sizeof(HashGraph), cudaMemcpyHostToDevice, s));
-    }
-    npartials = (uint64_t)grid * chunks.size();
+    PGB_CUDA(cudaMemcpyAsync(sg.ptr, hg, sizeof(hg), cudaMemcpyHostToDevice, s));
+    npartials = (uint64_t)grid * P->chunks.size();
     partials.alloc(npartials, s);
 
-    cudaStream_t cs = nullptr;
+    // copies on cs; chunk c counts on ks[c & 1] so that the launch of chunk
+    // c + 1 fills the SMs that chunk c's last CTAs leave idle
+    cudaStream_t cs = nullptr, s1 = nullptr;
     PGB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaEvent_t ready[2], freed[2], start;
-    PGB_CUDA(cudaEventCreateWithFlags(&ready[0], cudaEventDisableTiming));
-    PGB_CUDA(cudaEventCreateWithFlags(&ready[1], cudaEventDisableTiming));
-    PGB_CUDA(cudaEventCreateWithFlags(&freed[0], cudaEventDisableTiming));
-    PGB_CUDA(cudaEventCreateWithFlags(&freed[1], cudaEventDisableTiming));
-    PGB_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    cudaEvent_t ready[2] = {}, freed[2] = {}, start = nullptr, done1 = nullptr;
     auto cleanup = [&] {
-        cudaStreamSynchronize(cs);
+        if (cs) cudaStreamSynchronize(cs);
+        if (s1) cudaStreamSynchronize(s1);
         for (int k = 0; k < 2; ++k) {
-            cudaEventDestroy(ready[k]);
-            cudaEventDestroy(freed[k]);
+            if (ready[k]) cudaEventDestroy(ready[k]);
+            if (freed[k]) cudaEventDestroy(freed[k]);
         }
-        cudaEventDestroy(start);
+        if (start) cudaEventDestroy(start);
+        if (done1) cudaEventDestroy(done1);
+        if (s1) cudaStreamDestroy(s1);
         cudaStreamDestroy(cs);
     };
     int rc = guard([&] {
-        // the side stream starts after everything already queued on s
+        PGB_CUDA(cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k) {
+            PGB_CUDA(cudaEventCreateWithFlags(&ready[k], cudaEventDisableTiming));
+            PGB_CUDA(cudaEventCreateWithFlags(&freed[k], cudaEventDisableTiming));
+        }
+        PGB_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+        PGB_CUDA(cudaEventCreateWithFlags(&done1, cudaEventDisableTiming));
+        // the side streams start after everything already queued on s
+        PGB_CUDA(cudaEventRecord(ev0, s));
         PGB_CUDA(cudaEventRecord(start, s));
         PGB_CUDA(cudaStreamWaitEvent(cs, start, 0));
-        PGB_CUDA(cudaEventRecord(ev0, s));
+        PGB_CUDA(cudaStreamWaitEvent(s1, start, 0));
+        const cudaStream_t ks[2] = {s, s1};
         uint64_t bytes = 0;
-        for (size_t c = 0; c < chunks.size(); ++c) {
+        for (size_t c = 0; c < P->chunks.size(); ++c) {
             const int k = (int)(c & 1);
-            const Chunk& ch = chunks[c];
+            const StreamPlan::Chunk& ch = P->chunks[c];
             if (c >= 2) PGB_CUDA(cudaStreamWaitEvent(cs, freed[k], 0));
             PGB_CUDA(cudaMemcpyAsync(sxr[k].ptr, b->h_xr + ch.base, (size_t)ch.span * 8, cudaMemcpyHostToDevice, cs));
             PGB_CUDA(cudaMemcpyAsync(stail[k].ptr, b->h_itail + ch.base, (size_t)ch.span * 4, cudaMemcpyHostToDevice,
                                      cs));
-            PGB_CUDA(cudaMemcpyAsync(sitems[k].ptr, h_items + ch.first, (size_t)ch.count * sizeof(VItem),
+            PGB_CUDA(cudaMemcpyAsync(sitems[k].ptr, P->h_items + ch.first, (size_t)ch.count * sizeof(VItem),
                                      cudaMemcpyHostToDevice, cs));
             PGB_CUDA(cudaEventRecord(ready[k], cs));
             bytes += (uint64_t)ch.span * kStreamBytesPerInEdge + (uint64_t)ch.count * sizeof(VItem);
-            PGB_CUDA(cudaStreamWaitEvent(s, ready[k], 0));
-            launch_hash(sg[k].ptr, 1, sitems[k].ptr, ch.count, pv, s, cursor[k].ptr, partials.ptr + c * grid, grid);
-            PGB_CUDA(cudaEventRecord(freed[k], s));
+            PGB_CUDA(cudaStreamWaitEvent(ks[k], ready[k], 0));
+            launch_hash(sg.ptr + k, 1, sitems[k].ptr, ch.count, pv, ks[k], cursor.ptr + k, partials.ptr + c * grid,
+                        grid);
+            PGB_CUDA(cudaEventRecord(freed[k], ks[k]));
         }
+        PGB_CUDA(cudaEventRecord(done1, s1));
+        PGB_CUDA(cudaStreamWaitEvent(s, done1, 0));
         PGB_CUDA(cudaEventRecord(ev1, s));
         *streamed = bytes;
-        *nchunks_out = (uint32_t)chunks.size();
-        // the slot buffers and pinned items must outlive the queued work
+        *nchunks_out = (uint32_t)P->chunks.size();
+        // the slot buffers live on s; the pinned items must outlive the copies
         PGB_CUDA(cudaStreamSynchronize(s));
     });
     cleanup();
@@ -215,6 +264,11 @@ int pgb_blocks_offload(pgb_blocks* b, void* stream) {
         }
         // the in-edge index leaves the device, and so do the arrays only the
         // edge-wise kernels use
+        {
+            // captured runs point at the arrays released below
+            std::lock_guard<std::mutex> lk(b->plan_mu);
+            b->run_plans.clear();
+        }
         b->xr.release();
         b->rowidx.release();
         {
