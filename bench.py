@@ -439,7 +439,7 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat24")
     ap.add_argument("--mode", choices=["persistent", "plain"], default="persistent")
     ap.add_argument("--order", choices=["weight", "locality"], default="weight")
-    ap.add_argument("--variant", choices=["auto", "bsearch", "hash"], default="auto")
+    ap.add_argument("--variant", choices=["auto", "bsearch", "merge", "hash"], default="auto")
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--per-vertex", type=int, default=1)
     ap.add_argument("--p", type=int, default=0, help="override the workload's p")
@@ -490,7 +490,8 @@ def main(argv=None):
     tv = torch.zeros(n, dtype=torch.uint64, device="cuda")
     P.load()
     mode = P.PGB_MODE_PERSISTENT if args.mode == "persistent" else P.PGB_MODE_PLAIN
-    variant = {"auto": P.PGB_VAR_AUTO, "bsearch": P.PGB_VAR_BSEARCH, "hash": P.PGB_VAR_HASH}[args.variant]
+    variant = {"auto": P.PGB_VAR_AUTO, "bsearch": P.PGB_VAR_BSEARCH, "merge": P.PGB_VAR_MERGE,
+               "hash": P.PGB_VAR_HASH}[args.variant]
     opts = P.pgb_tc_opts_default(mode=mode, per_vertex=args.per_vertex, chunk_edges=args.chunk, variant=variant,
                                  order=P.PGB_ORDER_WEIGHT if args.order == "weight" else P.PGB_ORDER_LOCALITY)
     info = {}
@@ -547,7 +548,7 @@ def main(argv=None):
     if mode == P.PGB_MODE_PLAIN:
         kname = "k_tc_tuple"
     else:
-        kname = "k_tc_persistent" if info["variant_used"] == P.PGB_VAR_BSEARCH else "k_tc_hash"
+        kname = "k_tc_hash" if info["variant_used"] == P.PGB_VAR_HASH else "k_tc_persistent"
     achieved = info["alg_bytes"] / (kernel_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_note, "alg_bytes": info["alg_bytes"],

@@ -85,12 +85,18 @@ extern "C" {
  * PGB_VAR_AUTO:    chosen by the autotuner (below).
  * PGB_VAR_BSEARCH: each element of the shorter list is binary-searched in
  *                  the longer one; work is flattened across a warp.
- * PGB_VAR_MERGE:   warp-cooperative merge of 32-element chunks.
+ * PGB_VAR_MERGE:   warp-cooperative merge: the warp takes one edge at a
+ *                  time and walks both lists in 32-entry chunks; each lane
+ *                  finds its entry of one chunk in the other chunk with a
+ *                  5-step shuffle search, and the chunk with the smaller
+ *                  last entry advances.  Suits long lists of similar length.
  * PGB_VAR_HASH:    middle-vertex form: the partial list of each middle
  *                  vertex v is held in shared memory (a bitmap over its
  *                  third-vertex rank range when that range is at most
  *                  262,144 ranks, else a hash table) and the lists of v's
  *                  in-neighbours after v are streamed through it.
+ * PLAIN mode runs PGB_VAR_BSEARCH or PGB_VAR_MERGE (PGB_VAR_HASH gives
+ * PGB_E_INVAL).
  * Autotuner (PGB_VAR_AUTO): PLAIN mode runs PGB_VAR_BSEARCH.  PERSISTENT
  * mode runs PGB_VAR_HASH when the graph averages at least 32 lookups per
  * oriented edge (probes >= 32 |E+|, see pgb_blocks_stats: long lists, skewed
@@ -255,7 +261,7 @@ int pgb_tc_result_get(pgb_tc_result* r, uint64_t* total, uint64_t* per_vertex, i
 /* PLAIN mode with per_triple = 1: counts[t] for queue entry t (T entries). */
 int pgb_tc_result_triples(pgb_tc_result* r, uint64_t* counts, int mem);
 
-/* The variant that ran (PGB_VAR_BSEARCH or PGB_VAR_HASH). */
+/* The variant that ran (PGB_VAR_BSEARCH, PGB_VAR_MERGE or PGB_VAR_HASH). */
 int pgb_tc_result_variant(pgb_tc_result* r, int* variant);
 
 /* Streamed runs: host-to-device bytes copied (in-edge index slices and work

@@ -128,6 +128,76 @@ __device__ __forceinline__ void warp_step(const Graph& G, uint32_t idx, bool val
     }
 }
 
+// Warp-cooperative merge (PGB_VAR_MERGE) over up to 32 edges: the warp
+// takes the lanes' edges one at a time and merges the two lists in chunks of
+// 32 entries.  Each lane holds one entry of each chunk and finds its A entry
+// among the B chunk with a 5-step shuffle search; the chunk whose last entry
+// is smaller advances (both when equal).  A common entry is seen in exactly
+// one step: once either chunk moves on, its entries cannot match later
+// entries of the other list.
+template <bool PV>
+__device__ __forceinline__ void warp_step_merge(const Graph& G, uint32_t idx, bool valid, uint32_t lo, uint32_t hi,
+                                                bool clip, unsigned long long& cnt, int lane) {
+    uint32_t xb = 0, xe = 0, yb = 0, ye = 0, u = 0, v = 0;
+    if (valid) {
+        const uint32_t e = __ldg(G.bedge + idx);
+        u = __ldg(G.rowidx + e);
+        v = __ldg(G.col + e);
+        xb = e + 1;
+        xe = __ldg(G.rowptr + u + 1);
+        yb = __ldg(G.rowptr + v);
+        ye = __ldg(G.rowptr + v + 1);
+        if (clip) {
+            xb = lower_bound(G.col, xb, xe, lo);
+            xe = lower_bound(G.col, xb, xe, hi);
+            yb = lower_bound(G.col, yb, ye, lo);
+            ye = lower_bound(G.col, yb, ye, hi);
+        }
+    }
+    unsigned work = __ballot_sync(kFull, xb < xe && yb < ye);
+    while (work) {
+        const int j = __ffs(work) - 1;
+        work &= work - 1;
+        uint32_t pa = __shfl_sync(kFull, xb, j);
+        const uint32_t ae = __shfl_sync(kFull, xe, j);
+        uint32_t pb = __shfl_sync(kFull, yb, j);
+        const uint32_t be = __shfl_sync(kFull, ye, j);
+        uint32_t c = 0;
+        while (pa < ae && pb < be) {
+            const uint32_t na = min(32u, ae - pa), nb = min(32u, be - pb);
+            const uint32_t av = (uint32_t)lane < na ? __ldg(G.col + pa + lane) : 0xffffffffu;
+            const uint32_t bv = (uint32_t)lane < nb ? __ldg(G.col + pb + lane) : 0xffffffffu;
+            const uint32_t amax = __shfl_sync(kFull, av, na - 1);
+            const uint32_t bmax = __shfl_sync(kFull, bv, nb - 1);
+            // first lane k of the B chunk with bv[k] >= av (31 if none)
+            int k = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const uint32_t probe = __shfl_sync(kFull, bv, k + step - 1);
+                if (probe < av) k += step;
+            }
+            const uint32_t at = __shfl_sync(kFull, bv, k);
+            const bool hit = (uint32_t)lane < na && at == av;
+            if (hit) {
+                ++c;
+                if (PV) atomicAdd(G.tv + av, 1ull);
+            }
+            if (amax <= bmax) pa += na;
+            if (bmax <= amax) pb += nb;
+        }
+        cnt += c;
+        if (PV) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kFull, c, o);
+            const uint32_t uj = __shfl_sync(kFull, u, j), vj = __shfl_sync(kFull, v, j);
+            if (lane == 0 && c) {
+                atomicAdd(G.tv + uj, (unsigned long long)c);
+                atomicAdd(G.tv + vj, (unsigned long long)c);
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ void cta_reduce_store(unsigned long long cnt, unsigned long long* __restrict__ slot) {
     __shared__ unsigned long long s_red[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -155,7 +225,10 @@ __global__ void __launch_bounds__(kThreads) k_tc_tuple(Graph G, Tuple t, unsigne
     const uint32_t end = t.e_begin + t.e_count;
     for (uint32_t i0 = t.e_begin + gw * 32; i0 < end; i0 += nw * 32) {
         const uint32_t idx = i0 + lane;
-        warp_step<PV>(G, idx, idx < end, t.lo, t.hi, t.clip != 0, cnt, s_edge[warp], lane);
+        if (t.variant == PGB_VAR_MERGE)
+            warp_step_merge<PV>(G, idx, idx < end, t.lo, t.hi, t.clip != 0, cnt, lane);
+        else
+            warp_step<PV>(G, idx, idx < end, t.lo, t.hi, t.clip != 0, cnt, s_edge[warp], lane);
     }
     cta_reduce_store(cnt, partials + blockIdx.x);
 }
@@ -194,7 +267,10 @@ __global__ void __launch_bounds__(kThreads)
         const uint32_t end = min(i0 + chunk, tu.e_begin + tu.e_count);
         for (uint32_t i = i0; i < end; i += 32) {
             const uint32_t idx = i + lane;
-            warp_step<PV>(G, idx, idx < end, tu.lo, tu.hi, tu.clip != 0, cnt, s_edge[warp], lane);
+            if (tu.variant == PGB_VAR_MERGE)
+                warp_step_merge<PV>(G, idx, idx < end, tu.lo, tu.hi, tu.clip != 0, cnt, lane);
+            else
+                warp_step<PV>(G, idx, idx < end, tu.lo, tu.hi, tu.clip != 0, cnt, s_edge[warp], lane);
         }
     }
     cta_reduce_store(cnt, partials + blockIdx.x);
@@ -279,7 +355,7 @@ struct pgb_tc_result {
 
 namespace pgb {
 
-static Tuple make_tuple(const pgb_blocks* b, uint32_t i, uint32_t j, uint32_t k0, uint32_t k1) {
+static Tuple make_tuple(const pgb_blocks* b, uint32_t i, uint32_t j, uint32_t k0, uint32_t k1, int variant) {
     Tuple t;
     const size_t ij = (size_t)i * b->p + j;
     t.e_begin = (uint32_t)b->block_off[ij];
@@ -288,7 +364,7 @@ static Tuple make_tuple(const pgb_blocks* b, uint32_t i, uint32_t j, uint32_t k0
     t.hi = b->cuts[k1 + 1];
     // v >= c_j and entries of both lists exceed v, so [c_j, n) needs no clipping
     t.clip = (t.lo > b->cuts[j] || t.hi < b->n) ? 1u : 0u;
-    t.variant = PGB_VAR_BSEARCH;
+    t.variant = (uint32_t)variant;
     return t;
 }
 
@@ -302,7 +378,7 @@ static Tuple make_tuple(const pgb_blocks* b, uint32_t i, uint32_t j, uint32_t k0
 constexpr uint64_t kHashMinLookupsPerEdge = 32;
 
 static int choose_variant(const pgb_blocks* b, const pgb_tc_opts& o) {
-    if (o.mode == PGB_MODE_PLAIN) return PGB_VAR_BSEARCH;
+    if (o.mode == PGB_MODE_PLAIN) return o.variant == PGB_VAR_MERGE ? PGB_VAR_MERGE : PGB_VAR_BSEARCH;
     if (b->offloaded) return PGB_VAR_HASH;  // only the hash kernel reads a streamed index
     if (o.variant != PGB_VAR_AUTO) return o.variant;
     return b->probes >= kHashMinLookupsPerEdge * b->m ? PGB_VAR_HASH : PGB_VAR_BSEARCH;
@@ -368,7 +444,7 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
         P->tv_orig.alloc(n, s);
     }
     // the edge-wise (binary-search) kernels walk edges block by block
-    if (o.mode == PGB_MODE_PLAIN || variant == PGB_VAR_BSEARCH) ensure_block_edge_index(b, s);
+    if (variant != PGB_VAR_HASH) ensure_block_edge_index(b, s);
     P->G = Graph{b->bedge.ptr, b->rowidx.ptr, b->col.ptr, b->rowptr.ptr, P->tv.ptr};
 
     if (o.mode == PGB_MODE_PLAIN) {
@@ -384,7 +460,7 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
             g = std::min<uint64_t>(std::max<uint64_t>(g, 1), (uint64_t)sm_count() * 8);
             P->grids[t] = (int)g;
             P->seg[t + 1] = P->seg[t] + g;
-            P->tuples[t] = make_tuple(b, q.i, q.j, q.k, q.k);
+            P->tuples[t] = make_tuple(b, q.i, q.j, q.k, q.k, variant);
         }
         P->npartials = P->seg[T];
         P->partials.alloc(std::max<uint64_t>(P->npartials, 1), s);
@@ -426,7 +502,7 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
         std::vector<Tuple> tuples;
         std::vector<uint32_t> cp(1, 0);
         for (uint32_t ij : ids) {
-            Tuple tu = make_tuple(b, ij / p, ij % p, ij % p, p - 1);
+            Tuple tu = make_tuple(b, ij / p, ij % p, ij % p, p - 1, variant);
             tuples.push_back(tu);
             cp.push_back(cp.back() + (tu.e_count + chunk - 1) / chunk);
         }
@@ -625,11 +701,11 @@ int pgb_tc_run(const pgb_blocks* b, const pgb_tc_opts* opts, void* stream, pgb_t
         if (opts) o = *opts; else pgb_tc_opts_default(&o);
         if (o.mode != PGB_MODE_PLAIN && o.mode != PGB_MODE_PERSISTENT) fail(PGB_E_INVAL, "bad mode");
         if (o.variant < PGB_VAR_AUTO || o.variant > PGB_VAR_HASH) fail(PGB_E_INVAL, "bad variant");
-        if (o.variant == PGB_VAR_MERGE) fail(PGB_E_INVAL, "the merge variant is not available in this build");
         if (o.mode == PGB_MODE_PLAIN && o.variant == PGB_VAR_HASH)
-            fail(PGB_E_INVAL, "PLAIN mode runs the binary-search variant only");
+            fail(PGB_E_INVAL, "PLAIN mode runs the edge-wise variants (binary search, merge) only");
         if (o.order != PGB_ORDER_WEIGHT && o.order != PGB_ORDER_LOCALITY) fail(PGB_E_INVAL, "bad order");
-        if (b->offloaded && (o.mode != PGB_MODE_PERSISTENT || o.variant == PGB_VAR_BSEARCH))
+        if (b->offloaded && (o.mode != PGB_MODE_PERSISTENT || o.variant == PGB_VAR_BSEARCH ||
+                             o.variant == PGB_VAR_MERGE))
             fail(PGB_E_STATE, "offloaded blocks run in PERSISTENT mode with the hash variant only");
         std::unique_ptr<pgb_tc_result> r(new pgb_tc_result());
         run(b, o, (cudaStream_t)stream, r.get());

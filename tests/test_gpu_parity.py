@@ -195,7 +195,7 @@ def test_from_csr_matches_edges():
     assert T == oT and np.array_equal(t, ot)
 
 
-VARIANTS = [P.PGB_VAR_BSEARCH, P.PGB_VAR_HASH]
+VARIANTS = [P.PGB_VAR_BSEARCH, P.PGB_VAR_MERGE, P.PGB_VAR_HASH]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -248,12 +248,46 @@ def test_hash_splits_heavy_middle_vertices():
             assert np.array_equal(gt, want_t)
 
 
-def test_plain_mode_rejects_hash_and_merge_is_unavailable():
+def test_plain_mode_rejects_hash():
     src, dst, n = graphgen.rmat(8, 8, 1)
-    with pytest.raises(P.PgbError):
+    with pytest.raises(P.PgbError) as ei:
         gpu_count(src, dst, n, 2, mode=P.PGB_MODE_PLAIN, variant=P.PGB_VAR_HASH)
-    with pytest.raises(P.PgbError):
-        gpu_count(src, dst, n, 2, variant=P.PGB_VAR_MERGE)
+    assert ei.value.code == P.PGB_E_INVAL
+
+
+@pytest.mark.parametrize("path", golden_files(), ids=lambda x: x.split("/")[-1])
+def test_plain_merge_golden(path):
+    """PLAIN mode with the merge variant: one launch per triple, every p."""
+    src, dst, n, T, t = load_golden(path)
+    for p in range(1, n + 1):
+        gT, gt, _, _, _ = gpu_count(src, dst, n, p, mode=P.PGB_MODE_PLAIN, variant=P.PGB_VAR_MERGE)
+        assert gT == T and np.array_equal(gt, t)
+
+
+def test_merge_long_balanced_lists():
+    """Lists far longer than one 32-entry chunk on both sides, with ragged
+    tails: K_200 (every edge's lists overlap in up to 198 entries) plus a
+    sparse random fringe; per-triple counts equal the binary-search ones."""
+    from math import comb
+    k = 200
+    a, b = np.triu_indices(k, 1)
+    rng = np.random.default_rng(77)
+    fs = rng.integers(0, 600, 3000)
+    fd = rng.integers(0, 600, 3000)
+    src = np.concatenate([a, fs]).astype(np.uint32)
+    dst = np.concatenate([b, fd]).astype(np.uint32)
+    n = 600
+    T, t, _ = oracle_count(src, dst, n)
+    assert T >= comb(k, 3)
+    for mode in MODES:
+        for p in (1, 3, 7):
+            gT, gt, tri, _, _ = gpu_count(src, dst, n, p, mode=mode, variant=P.PGB_VAR_MERGE,
+                                          per_triple=mode == P.PGB_MODE_PLAIN)
+            assert gT == T and np.array_equal(gt, t)
+            if mode == P.PGB_MODE_PLAIN:
+                _, _, tri_b, _, _ = gpu_count(src, dst, n, p, mode=mode, variant=P.PGB_VAR_BSEARCH,
+                                              per_triple=True)
+                assert np.array_equal(tri, tri_b)
 
 
 def test_autotuner_choice_and_counts():

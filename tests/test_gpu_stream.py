@@ -122,7 +122,7 @@ def test_offloaded_state_rules():
     # the partition's exports still work
     assert np.array_equal(P.pgb_blocks_export(b, P.PGB_EXPORT_COL), col_before)
     # only the persistent hash path reads a streamed index
-    for kw in (dict(mode=P.PGB_MODE_PLAIN), dict(variant=P.PGB_VAR_BSEARCH)):
+    for kw in (dict(mode=P.PGB_MODE_PLAIN), dict(variant=P.PGB_VAR_BSEARCH), dict(variant=P.PGB_VAR_MERGE)):
         with pytest.raises(P.PgbError) as ei:
             P.pgb_tc_run(b, P.pgb_tc_opts_default(**kw))
         assert ei.value.code == P.PGB_E_STATE
