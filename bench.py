@@ -282,20 +282,27 @@ def serve_bench(args):
     tot_b, _, span_b, st_b = run_serve(jobs, P.PGB_SERVE_BATCHED)
     assert tot_s == tot_b, "serial and batched counts differ"
     cap_s, cap_b = len(jobs) / span_s, len(jobs) / span_b
-    rate = 0.8 * cap_s
-    rng = np.random.default_rng(12345)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(jobs)))
-    for name, mode in (("serial", P.PGB_SERVE_SERIAL), ("batched", P.PGB_SERVE_BATCHED)):
-        tot, lat, span, st = run_serve(jobs, mode, arrivals)
-        assert tot == tot_s
-        lat_ms = np.array(lat) * 1e3
-        res[name] = {"jobs_s": len(jobs) / span, "p50_ms": float(np.percentile(lat_ms, 50)),
-                     "p99_ms": float(np.percentile(lat_ms, 99)), "launches": st["batches"]}
+    sweep = {}
+    for factor in (0.5, 0.8, 0.95):
+        rate = factor * cap_s
+        rng = np.random.default_rng(12345)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(jobs)))
+        res = {}
+        for name, mode in (("serial", P.PGB_SERVE_SERIAL), ("batched", P.PGB_SERVE_BATCHED)):
+            tot, lat, span, st = run_serve(jobs, mode, arrivals)
+            assert tot == tot_s
+            lat_ms = np.array(lat) * 1e3
+            res[name] = {"jobs_s": len(jobs) / span, "p50_ms": float(np.percentile(lat_ms, 50)),
+                         "p99_ms": float(np.percentile(lat_ms, 99)), "launches": st["batches"]}
+        sweep[f"{factor:.2f}"] = {"rate_jobs_s": rate, **res}
     return {"metric": "serve jobs/s and p50/p99 latency", "jobs": len(jobs), "raw_edges": edges,
             "mix": f"thirds of R-MAT (scale 10-{args.serve_max_scale}, ef 8-32), ER (n 2^10-2^{args.serve_max_scale} "
                    "log-uniform, avg degree 4-64 log-uniform), RGG (avg degree 6); seed = job index; per-vertex on",
             "capacity_jobs_s": {"serial": cap_s, "batched": cap_b},
-            "poisson_rate_jobs_s": rate, "poisson": res, "batched_launches_closed_loop": st_b["batches"]}
+            "poisson_rate_jobs_s": sweep["0.80"]["rate_jobs_s"],
+            "poisson": {k: sweep["0.80"][k] for k in ("serial", "batched")},
+            "poisson_sweep_by_fraction_of_serial_capacity": sweep,
+            "batched_launches_closed_loop": st_b["batches"]}
 
 
 def h2d_gbs(torch, nbytes=1 << 30, reps=5):
@@ -446,7 +453,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-jobs", type=int, default=300)
+    ap.add_argument("--serve-jobs", type=int, default=1000)
     ap.add_argument("--serve-max-scale", type=int, default=18)
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-tiers", action="store_true")

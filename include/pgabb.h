@@ -93,7 +93,7 @@ extern "C" {
  * PGB_VAR_HASH:    middle-vertex form: the partial list of each middle
  *                  vertex v is held in shared memory (a bitmap over its
  *                  third-vertex rank range when that range is at most
- *                  262,144 ranks, else a hash table) and the lists of v's
+ *                  131,072 ranks, else a hash table) and the lists of v's
  *                  in-neighbours after v are streamed through it.
  * PLAIN mode runs PGB_VAR_BSEARCH or PGB_VAR_MERGE (PGB_VAR_HASH gives
  * PGB_E_INVAL).
@@ -283,19 +283,23 @@ int pgb_tc_count_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, uin
 /* ---------------------------------------------------------------- serve */
 /* A serve loop for triangle-count jobs on graphs of mixed sizes (the paper
  * runs one computation at a time, Section 4.1; serving is this library's
- * extension of the same path).  Jobs are raw edge lists.  The server admits
- * queued jobs in arrival order while the estimated device bytes of admitted
- * jobs stay within budget_bytes; admitted jobs are ingested, ordered and
- * partitioned concurrently on their own streams.
- *   PGB_SERVE_BATCHED: continuous batching.  Every staged job (up to
- *     max_batch_jobs) is counted in ONE persistent launch whose work items
- *     interleave the jobs' block tuples; jobs staged during that launch go
- *     into the next one.
- *   PGB_SERVE_SERIAL: one job at a time, staged and counted alone (the
- *     baseline).
- * Results are bit-identical to pgb_tc_run on each graph alone.  The server
- * keeps its own CUDA streams and threads on the device current at create;
- * its threads take device memory from the CUDA stream-ordered allocator
+ * extension of the same path).  Jobs are raw edge lists.  Batch threads
+ * admit queued jobs in arrival order while the estimated device bytes of
+ * admitted jobs stay within budget_bytes.
+ *   PGB_SERVE_BATCHED: continuous batching.  Each of `max_inflight` batch
+ *     threads takes the queued jobs that fit (up to max_batch_jobs jobs and
+ *     batch_edges raw edges; a larger job runs alone) and counts them as ONE
+ *     graph, the disjoint union of the jobs: one ingest, one degree order,
+ *     one partition and one persistent counting launch whose block tuples
+ *     interleave all the jobs'.  A job's per-vertex counts are its slice of
+ *     the union's and its total a third of their sum.  Jobs arriving while a
+ *     batch runs join the next one; batches of different threads overlap on
+ *     the device.
+ *   PGB_SERVE_SERIAL: one thread, one job per batch (the baseline).
+ * Results are bit-identical to pgb_tc_run on each graph alone.  A job with
+ * an endpoint >= n fails alone (PGB_E_INVAL at wait).  The server keeps its
+ * own CUDA streams and threads on the device current at create; its threads
+ * take device memory from the CUDA stream-ordered allocator
  * (cudaMallocAsync), not from hooks set with pgb_set_allocator. */
 typedef struct pgb_server pgb_server;
 
@@ -310,12 +314,13 @@ typedef struct pgb_server pgb_server;
 
 typedef struct {
     uint64_t budget_bytes;    /* HBM admission budget (0 = 64 GiB) */
-    uint32_t max_inflight;    /* jobs staged at once (0 = 8; SERIAL uses 1) */
-    uint32_t p;               /* parts per dimension for each job (0 = 8, capped at n) */
+    uint32_t max_inflight;    /* BATCHED: batch threads (0 = 1, at most 16); SERIAL uses 1 */
+    uint32_t p;               /* parts per dimension of a batch's graph (0 = 8, capped at n) */
     int32_t mode;             /* PGB_SERVE_* */
     int32_t per_vertex;       /* also return per-vertex counts */
-    uint32_t max_batch_jobs;  /* jobs per counting launch (0 = 64, at most 256) */
-    uint32_t reserved[9];
+    uint32_t max_batch_jobs;  /* BATCHED: jobs per batch (0 = 256, at most 4096) */
+    uint32_t batch_edges;     /* BATCHED: raw edges per batch (0 = 2^27) */
+    uint32_t reserved[8];
 } pgb_server_opts;
 
 typedef struct {

@@ -3,23 +3,26 @@
 //
 // The paper runs one computation at a time (Section 4.1); this file is the
 // serving side of the same block-tuple path.  A job is a raw edge list.
-//   submit     copies the edges into the job (the caller's arrays are only
-//              borrowed for the call) and queues it; a job that can never
-//              fit the budget is refused with PGB_E_BUDGET.
-//   stage      one of `max_inflight` stage threads admits queued jobs while
-//              the estimated device bytes of admitted jobs stay within the
-//              budget, and on its own stream copies the edges to the device,
-//              ingests, orders, partitions and builds the job's work items.
-//              Stages of several jobs, and the counting launch below, run at
-//              the same time on the device.
-//   batch      (BATCHED mode) the batcher thread takes every staged job (up
-//              to max_batch_jobs) and counts them all in ONE persistent
-//              launch whose work items interleave the jobs' block tuples;
-//              jobs staged while it runs go into the next launch.
-//   serial     (SERIAL mode) one stage thread stages and counts each job
-//              alone, one job at a time: the baseline.
-// Results (total, per-vertex counts by original ID, latency from submit to
-// completion) are kept in the job until it is waited for.
+//   submit   copies the edges into the job (the caller's arrays are only
+//            borrowed for the call) and queues it; a job that can never fit
+//            the budget is refused with PGB_E_BUDGET.
+//   batch    each of the server's batch threads takes the queued jobs that
+//            fit the budget (in arrival order, up to max_batch_jobs and
+//            batch_edges raw edges) and counts them as ONE graph: the
+//            disjoint union of the jobs, vertex IDs shifted by the vertex
+//            counts of the jobs before them.  One ingest, one degree order,
+//            one p x p partition and one persistent counting launch serve
+//            the whole batch, so the block tuples of all its jobs interleave
+//            in that launch.  Triangles never join two jobs, so a job's
+//            per-vertex counts are its slice of the union's, and its total is
+//            a third of their sum.  Jobs that arrive while a batch runs go
+//            into the next batch a thread takes (continuous batching); with
+//            several threads, batches overlap on the device.
+//   serial   (SERIAL mode) one thread, one job per batch: the baseline.
+// An edge with an endpoint >= its job's n fails that job alone: the union
+// builder turns the job's edges into self-loops (dropped by ingest) and flags
+// the job.  Results (total, per-vertex counts by original ID, latency from
+// submit to completion) are kept in the job until it is waited for.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -29,35 +32,48 @@
 #include <thread>
 
 #include "internal.cuh"
-#include "tc_hash.cuh"
 
 namespace pgb {
 
-__global__ void k_set_job(VItem* __restrict__ items, uint32_t n, uint32_t job) {
-    uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) items[i].job = job;
+// Union edge list: edge i of job j (eoff[j] <= i < eoff[j+1]) gets the job's
+// vertex offset voff[j]; an endpoint >= the job's n flags the job and turns
+// the edge into a self-loop.
+__global__ void k_union_ids(uint32_t* __restrict__ src, uint32_t* __restrict__ dst, uint64_t m,
+                            const uint64_t* __restrict__ eoff, const uint64_t* __restrict__ voff, uint32_t nj,
+                            uint32_t* __restrict__ bad) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        uint32_t lo = 0, hi = nj;  // job j: largest j with eoff[j] <= i
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (eoff[mid] <= i) lo = mid; else hi = mid;
+        }
+        const uint64_t n = voff[lo + 1] - voff[lo];
+        uint32_t a = src[i], b = dst[i];
+        if (a >= n || b >= n) {
+            bad[lo] = 1;
+            a = b = 0;
+        }
+        src[i] = (uint32_t)(voff[lo] + a);
+        dst[i] = (uint32_t)(voff[lo] + b);
+    }
 }
 
-__global__ void k_job_totals(const unsigned long long* __restrict__ partials, uint32_t grid,
-                             unsigned long long* __restrict__ totals) {
+// sums[j] = sum of t over job j's vertex range [voff[j], voff[j+1]).
+__global__ void k_job_sums(const unsigned long long* __restrict__ t, const uint64_t* __restrict__ voff,
+                           unsigned long long* __restrict__ sums) {
     __shared__ unsigned long long red[32];
     const uint32_t j = blockIdx.x;
     unsigned long long acc = 0;
-    for (uint32_t i = threadIdx.x; i < grid; i += blockDim.x) acc += partials[(size_t)j * grid + i];
+    for (uint64_t x = voff[j] + threadIdx.x; x < voff[j + 1]; x += blockDim.x) acc += t[x];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x < 32) {
         acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (threadIdx.x == 0) totals[j] = acc;
+        if (threadIdx.x == 0) sums[j] = acc;
     }
-}
-
-__global__ void k_job_scatter(const unsigned long long* __restrict__ tv, const uint32_t* __restrict__ perm, uint32_t n,
-                              unsigned long long* __restrict__ out) {
-    uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) out[perm[r]] = tv[r];
 }
 
 using Clock = std::chrono::steady_clock;
@@ -72,26 +88,36 @@ struct Job {
     uint64_t est = 0;  // admitted device bytes
     std::vector<uint32_t> src, dst;
     Clock::time_point submitted, finished;
-    // staged device state
-    pgb_graph* g = nullptr;
-    pgb_blocks* b = nullptr;
-    DevBuf<VItem> items;
-    uint32_t nitems = 0;
-    DevBuf<unsigned long long> tv;  // per-vertex counts by rank
     // results
     uint64_t total = 0;
     std::vector<uint64_t> per_vertex;
     bool cancel = false;
+};
 
-    void release_device() {
-        items.release();
-        tv.release();
-        if (b) pgb_blocks_free(b);
-        if (g) pgb_graph_free(g);
-        b = nullptr;
-        g = nullptr;
+// Pinned host buffers for batch results, reused by one batch thread.
+struct PinnedPool {
+    void* ptr = nullptr;
+    size_t size = 0;
+    void* get(size_t bytes) {
+        if (bytes > size) {
+            if (ptr) cudaFreeHost(ptr);
+            ptr = nullptr;
+            size = 0;
+            const size_t sz = std::max<size_t>(bytes + bytes / 4, 1 << 20);
+            PGB_CUDA(cudaHostAlloc(&ptr, sz, cudaHostAllocDefault));
+            size = sz;
+        }
+        return ptr;
+    }
+    ~PinnedPool() {
+        if (ptr) cudaFreeHost(ptr);
     }
 };
+
+// Caps of one batch: raw edges (unless a single job is larger) and vertices.
+constexpr uint64_t kDefaultBatchEdges = 1ull << 27;
+constexpr uint64_t kMaxBatchVertices = 1ull << 31;
+constexpr uint32_t kMaxJobsPerBatch = 4096;
 
 }  // namespace pgb
 
@@ -100,10 +126,8 @@ struct pgb_server {
     int device = 0;
     std::mutex mu;
     std::condition_variable cv_queue;   // queued jobs / budget freed / stop
-    std::condition_variable cv_ready;   // staged jobs for the batcher / stop
     std::condition_variable cv_done;    // job completions
     std::deque<std::shared_ptr<pgb::Job>> queued;
-    std::deque<std::shared_ptr<pgb::Job>> ready;
     std::map<uint64_t, std::shared_ptr<pgb::Job>> jobs;
     uint64_t next_id = 1;
     uint64_t bytes_in_use = 0;
@@ -111,9 +135,7 @@ struct pgb_server {
     bool stop = false;
     bool paused = false;  // admission held (queued jobs wait)
     std::vector<std::thread> threads;
-    // streams live as long as the server: job buffers allocated on a stage
-    // stream may be released later by the batcher
-    std::vector<cudaStream_t> streams;
+    std::vector<cudaStream_t> streams;  // one per batch thread, for the server's lifetime
 };
 
 namespace pgb {
@@ -126,7 +148,6 @@ uint64_t job_bytes(uint64_t m, uint32_t n) {
 }
 
 static void finish(pgb_server* S, const std::shared_ptr<Job>& J, int state, int err, const std::string& msg) {
-    J->release_device();
     std::lock_guard<std::mutex> lk(S->mu);
     J->state = state;
     J->err = err;
@@ -144,151 +165,122 @@ static void finish(pgb_server* S, const std::shared_ptr<Job>& J, int state, int 
     S->cv_queue.notify_all();
 }
 
-// Copy to the device, ingest, order, partition, build work items.
-static void stage_job(pgb_server* S, Job& J, cudaStream_t s) {
-    DevBuf<uint32_t> ds(J.m, s), dd(J.m, s);
-    if (J.m) {
-        PGB_CUDA(cudaMemcpyAsync(ds.ptr, J.src.data(), J.m * 4, cudaMemcpyHostToDevice, s));
-        PGB_CUDA(cudaMemcpyAsync(dd.ptr, J.dst.data(), J.m * 4, cudaMemcpyHostToDevice, s));
-    }
-    int rc = pgb_graph_from_edges(ds.ptr, dd.ptr, J.m, J.n, PGB_MEM_DEVICE, s, &J.g);
-    if (rc != PGB_OK) fail(rc, pgb_last_error());
-    ds.release();
-    dd.release();
-    uint32_t p = S->o.p ? S->o.p : 8;
-    if (J.n > 0) p = std::min<uint32_t>(p, J.n);
-    rc = pgb_partition(J.g, p, PGB_CUT_NNZ, s, &J.b);
-    if (rc != PGB_OK) fail(rc, pgb_last_error());
-    pgb_graph_free(J.g);
-    J.g = nullptr;
-    J.nitems = build_hash_items(J.b, 0, 0, s, J.items);
-    if (S->o.per_vertex) {
-        J.tv.alloc(J.n, s);
-        if (J.n) PGB_CUDA(cudaMemsetAsync(J.tv.ptr, 0, (size_t)J.n * 8, s));
-    }
-    PGB_CUDA(cudaStreamSynchronize(s));
-}
-
-// Count the staged jobs in one persistent launch on stream s, then fetch
-// their totals and per-vertex counts.
-static void count_jobs(pgb_server* S, std::vector<std::shared_ptr<Job>>& batch, cudaStream_t s) {
+// Count one batch as the disjoint union of its jobs (see the top of this
+// file); fills each job's total and per-vertex counts, and `bad[j]` for jobs
+// with an endpoint >= n.
+static void count_batch(pgb_server* S, const std::vector<std::shared_ptr<Job>>& batch, cudaStream_t s,
+                        PinnedPool& pool, std::vector<uint32_t>& bad) {
     const uint32_t nj = (uint32_t)batch.size();
+    std::vector<uint64_t> eoff(nj + 1, 0), voff(nj + 1, 0);
+    for (uint32_t j = 0; j < nj; ++j) {
+        eoff[j + 1] = eoff[j] + batch[j]->m;
+        voff[j + 1] = voff[j] + batch[j]->n;
+    }
+    const uint64_t M = eoff[nj], N = voff[nj];
+    if (N >= kMaxBatchVertices) fail(PGB_E_OVERFLOW, "batch has too many vertices");
+    DevBuf<uint64_t> deoff(nj + 1, s), dvoff(nj + 1, s);
+    DevBuf<uint32_t> dbad(nj, s);
+    PGB_CUDA(cudaMemcpyAsync(deoff.ptr, eoff.data(), (nj + 1) * 8, cudaMemcpyHostToDevice, s));
+    PGB_CUDA(cudaMemcpyAsync(dvoff.ptr, voff.data(), (nj + 1) * 8, cudaMemcpyHostToDevice, s));
+    PGB_CUDA(cudaMemsetAsync(dbad.ptr, 0, nj * 4, s));
+    pgb_graph* g = nullptr;
+    {
+        DevBuf<uint32_t> ds(M, s), dd(M, s);
+        for (uint32_t j = 0; j < nj; ++j) {
+            const Job& J = *batch[j];
+            if (!J.m) continue;
+            PGB_CUDA(cudaMemcpyAsync(ds.ptr + eoff[j], J.src.data(), J.m * 4, cudaMemcpyHostToDevice, s));
+            PGB_CUDA(cudaMemcpyAsync(dd.ptr + eoff[j], J.dst.data(), J.m * 4, cudaMemcpyHostToDevice, s));
+        }
+        if (M) {
+            k_union_ids<<<(unsigned)std::min<uint64_t>((M + 255) / 256, 148ull * 32), 256, 0, s>>>(
+                ds.ptr, dd.ptr, M, deoff.ptr, dvoff.ptr, nj, dbad.ptr);
+            PGB_CHECK_LAUNCH("k_union_ids");
+        }
+        const int rc = pgb_graph_from_edges(ds.ptr, dd.ptr, M, (uint32_t)N, PGB_MEM_DEVICE, s, &g);
+        if (rc != PGB_OK) fail(rc, pgb_last_error());
+    }
+    pgb_blocks* b = nullptr;
+    const uint32_t p = N ? (uint32_t)std::min<uint64_t>(S->o.p ? S->o.p : 8, N) : 1;
+    int rc = pgb_partition(g, p, PGB_CUT_NNZ, s, &b);
+    pgb_graph_free(g);
+    if (rc != PGB_OK) fail(rc, pgb_last_error());
+    std::unique_ptr<pgb_blocks, void (*)(pgb_blocks*)> bguard(b, pgb_blocks_free);
+    // per-vertex counts are needed even for totals alone: a job's total is a
+    // third of the sum over its vertices
+    pgb_tc_opts o;
+    pgb_tc_opts_default(&o);
+    pgb_tc_result* r = nullptr;
+    rc = pgb_tc_run(b, &o, s, &r);
+    if (rc != PGB_OK) fail(rc, pgb_last_error());
+    std::unique_ptr<pgb_tc_result, void (*)(pgb_tc_result*)> rguard(r, pgb_tc_result_free);
+    DevBuf<unsigned long long> t(std::max<uint64_t>(N, 1), s), sums(nj, s);
+    rc = pgb_tc_result_get(r, nullptr, N ? reinterpret_cast<uint64_t*>(t.ptr) : nullptr, PGB_MEM_DEVICE);
+    if (rc != PGB_OK) fail(rc, pgb_last_error());
+    k_job_sums<<<nj, 256, 0, s>>>(t.ptr, dvoff.ptr, sums.ptr);
+    PGB_CHECK_LAUNCH("k_job_sums");
+    // one copy back: sums, flags, then (per-vertex runs) the union's counts
     const bool pv = S->o.per_vertex != 0;
-    uint64_t total_items = 0;
-    for (auto& J : batch) total_items += J->nitems;
-    if (total_items >= (1ull << 32)) fail(PGB_E_OVERFLOW, "too many work items in one batch");
-    std::vector<HashGraph> hg(nj);
-    for (uint32_t j = 0; j < nj; ++j) {
-        const pgb_blocks* b = batch[j]->b;
-        hg[j] = HashGraph{b->rowptr.ptr, b->col.ptr, b->rowidx.ptr, b->colptr.ptr, b->xr.ptr,
-                          pv ? batch[j]->tv.ptr : nullptr, b->n};
-    }
-    DevBuf<HashGraph> dg(nj, s);
-    PGB_CUDA(cudaMemcpyAsync(dg.ptr, hg.data(), nj * sizeof(HashGraph), cudaMemcpyHostToDevice, s));
-    DevBuf<VItem> items(std::max<uint64_t>(total_items, 1), s);
-    uint64_t off = 0;
-    for (uint32_t j = 0; j < nj; ++j) {
-        const uint32_t k = batch[j]->nitems;
-        if (!k) continue;
-        PGB_CUDA(cudaMemcpyAsync(items.ptr + off, batch[j]->items.ptr, (size_t)k * sizeof(VItem),
-                                 cudaMemcpyDeviceToDevice, s));
-        k_set_job<<<std::min<uint32_t>((k + 255) / 256, 1024), 256, 0, s>>>(items.ptr + off, k, j);
-        PGB_CHECK_LAUNCH("k_set_job");
-        off += k;
-    }
-    const int grid = hash_grid(pv);
-    DevBuf<unsigned long long> partials((size_t)nj * grid, s), totals(nj, s);
-    DevBuf<unsigned int> cursor(1, s);
-    if (total_items) {
-        launch_hash(dg.ptr, nj, items.ptr, (uint32_t)total_items, pv, s, cursor.ptr, partials.ptr, grid);
-        k_job_totals<<<nj, 256, 0, s>>>(partials.ptr, (uint32_t)grid, totals.ptr);
-        PGB_CHECK_LAUNCH("k_job_totals");
-    } else {
-        PGB_CUDA(cudaMemsetAsync(totals.ptr, 0, nj * 8, s));
-    }
-    std::vector<unsigned long long> ht(nj);
-    PGB_CUDA(cudaMemcpyAsync(ht.data(), totals.ptr, nj * 8, cudaMemcpyDeviceToHost, s));
-    std::vector<DevBuf<unsigned long long>> outs(nj);
+    const size_t head = (size_t)nj * 8 + (size_t)nj * 4;
+    unsigned char* h = static_cast<unsigned char*>(pool.get(head + (pv ? N * 8 : 0)));
+    PGB_CUDA(cudaMemcpyAsync(h, sums.ptr, nj * 8, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaMemcpyAsync(h + nj * 8, dbad.ptr, nj * 4, cudaMemcpyDeviceToHost, s));
+    if (pv && N) PGB_CUDA(cudaMemcpyAsync(h + head, t.ptr, N * 8, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaStreamSynchronize(s));
+    const uint64_t* hs = reinterpret_cast<const uint64_t*>(h);
+    const uint32_t* hb = reinterpret_cast<const uint32_t*>(h + nj * 8);
+    const uint64_t* ht = reinterpret_cast<const uint64_t*>(h + head);
+    bad.assign(hb, hb + nj);
     for (uint32_t j = 0; j < nj; ++j) {
         Job& J = *batch[j];
-        J.total = 0;
-        if (pv && J.n) {
-            outs[j].alloc(J.n, s);
-            k_job_scatter<<<std::min<uint32_t>((J.n + 255) / 256, 4096), 256, 0, s>>>(J.tv.ptr, J.b->perm.ptr, J.n,
-                                                                                    outs[j].ptr);
-            PGB_CHECK_LAUNCH("k_job_scatter");
-            J.per_vertex.assign(J.n, 0);
-            PGB_CUDA(cudaMemcpyAsync(J.per_vertex.data(), outs[j].ptr, (size_t)J.n * 8, cudaMemcpyDeviceToHost, s));
-        }
+        J.total = hs[j] / 3;
+        if (pv) J.per_vertex.assign(ht + voff[j], ht + voff[j + 1]);
     }
-    PGB_CUDA(cudaStreamSynchronize(s));
-    for (uint32_t j = 0; j < nj; ++j) batch[j]->total = ht[j];
 }
 
-static void stage_loop(pgb_server* S, int idx) {
+static void batch_loop(pgb_server* S, int idx) {
     cudaSetDevice(S->device);
     use_native_allocator_in_this_thread();
-    cudaStream_t s = S->streams[idx];
+    const cudaStream_t s = S->streams[idx];
     const bool serial = S->o.mode == PGB_SERVE_SERIAL;
+    const uint32_t cap = serial ? 1 : (S->o.max_batch_jobs ? S->o.max_batch_jobs : 256);
+    const uint64_t max_edges = S->o.batch_edges ? S->o.batch_edges : kDefaultBatchEdges;
+    PinnedPool pool;
     for (;;) {
-        std::shared_ptr<Job> J;
+        std::vector<std::shared_ptr<Job>> batch;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_queue.wait(lk, [&] {
                 if (S->stop) return true;
                 if (S->paused || S->queued.empty()) return false;
-                // admit in arrival order while the budget allows
                 return S->bytes_in_use + S->queued.front()->est <= S->o.budget_bytes;
             });
             if (S->stop) break;
-            J = S->queued.front();
-            S->queued.pop_front();
-            S->bytes_in_use += J->est;
-            J->state = PGB_JOB_RUNNING;
-        }
-        int rc = guard([&] {
-            stage_job(S, *J, s);
-            if (serial) {
-                std::vector<std::shared_ptr<Job>> one{J};
-                count_jobs(S, one, s);
-            }
-        });
-        if (rc != PGB_OK) {
-            finish(S, J, PGB_JOB_FAILED, rc, pgb_last_error());
-            continue;
-        }
-        if (serial) {
-            finish(S, J, J->cancel ? PGB_JOB_CANCELLED : PGB_JOB_DONE, J->cancel ? PGB_E_CANCELLED : PGB_OK, "");
-        } else {
-            std::lock_guard<std::mutex> lk(S->mu);
-            S->ready.push_back(J);
-            S->cv_ready.notify_all();
-        }
-    }
-}
-
-static void batch_loop(pgb_server* S) {
-    cudaSetDevice(S->device);
-    use_native_allocator_in_this_thread();
-    cudaStream_t s = S->streams.back();
-    const uint32_t cap = std::min<uint32_t>(S->o.max_batch_jobs ? S->o.max_batch_jobs : 64, kMaxBatchJobs);
-    for (;;) {
-        std::vector<std::shared_ptr<Job>> batch;
-        {
-            std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_ready.wait(lk, [&] { return S->stop || !S->ready.empty(); });
-            if (S->stop && S->ready.empty()) break;
-            while (!S->ready.empty() && batch.size() < cap) {
-                batch.push_back(S->ready.front());
-                S->ready.pop_front();
+            // admit in arrival order while the budget and the batch caps allow
+            uint64_t edges = 0, verts = 0;
+            while (!S->queued.empty() && batch.size() < cap) {
+                const std::shared_ptr<Job>& J = S->queued.front();
+                if (S->bytes_in_use + J->est > S->o.budget_bytes) break;
+                if (!batch.empty() && (edges + J->m > max_edges || verts + J->n >= kMaxBatchVertices)) break;
+                edges += J->m;
+                verts += J->n;
+                S->bytes_in_use += J->est;
+                J->state = PGB_JOB_RUNNING;
+                batch.push_back(J);
+                S->queued.pop_front();
             }
             ++S->n_batches;
             S->jobs_in_batches += batch.size();
         }
-        int rc = guard([&] { count_jobs(S, batch, s); });
-        for (auto& J : batch) {
-            if (rc != PGB_OK) finish(S, J, PGB_JOB_FAILED, rc, pgb_last_error());
-            else finish(S, J, J->cancel ? PGB_JOB_CANCELLED : PGB_JOB_DONE, J->cancel ? PGB_E_CANCELLED : PGB_OK, "");
+        std::vector<uint32_t> bad;
+        const int rc = guard([&] { count_batch(S, batch, s, pool, bad); });
+        const std::string msg = rc == PGB_OK ? std::string() : std::string(pgb_last_error());
+        for (size_t j = 0; j < batch.size(); ++j) {
+            const std::shared_ptr<Job>& J = batch[j];
+            if (rc != PGB_OK) finish(S, J, PGB_JOB_FAILED, rc, msg);
+            else if (bad[j]) finish(S, J, PGB_JOB_FAILED, PGB_E_INVAL, "vertex ID >= n in the job's edges");
+            else if (J->cancel) finish(S, J, PGB_JOB_CANCELLED, PGB_E_CANCELLED, "");
+            else finish(S, J, PGB_JOB_DONE, PGB_OK, "");
         }
     }
 }
@@ -303,11 +295,11 @@ void pgb_server_opts_default(pgb_server_opts* o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
     o->budget_bytes = 64ull << 30;
-    o->max_inflight = 8;
+    o->max_inflight = 1;
     o->p = 8;
     o->mode = PGB_SERVE_BATCHED;
     o->per_vertex = 1;
-    o->max_batch_jobs = 64;
+    o->max_batch_jobs = 256;
 }
 
 uint64_t pgb_server_job_bytes(uint64_t m, uint32_t n) { return job_bytes(m, n); }
@@ -319,13 +311,12 @@ int pgb_server_create(const pgb_server_opts* opts, pgb_server** out) {
         if (opts) S->o = *opts; else pgb_server_opts_default(&S->o);
         if (S->o.mode != PGB_SERVE_BATCHED && S->o.mode != PGB_SERVE_SERIAL) fail(PGB_E_INVAL, "bad serve mode");
         if (S->o.budget_bytes == 0) S->o.budget_bytes = 64ull << 30;
-        if (S->o.max_inflight == 0) S->o.max_inflight = 8;
-        if (S->o.max_batch_jobs > kMaxBatchJobs) fail(PGB_E_INVAL, "max_batch_jobs must be at most 256");
+        if (S->o.max_inflight == 0) S->o.max_inflight = 1;
+        if (S->o.max_batch_jobs > kMaxJobsPerBatch) fail(PGB_E_INVAL, "max_batch_jobs must be at most 4096");
         PGB_CUDA(cudaGetDevice(&S->device));
         pgb_server* raw = S.get();
-        const int nstage = S->o.mode == PGB_SERVE_SERIAL ? 1 : (int)S->o.max_inflight;
-        const int nstreams = nstage + (S->o.mode == PGB_SERVE_BATCHED ? 1 : 0);
-        for (int i = 0; i < nstreams; ++i) {
+        const int nthreads = S->o.mode == PGB_SERVE_SERIAL ? 1 : (int)std::min<uint32_t>(S->o.max_inflight, 16);
+        for (int i = 0; i < nthreads; ++i) {
             cudaStream_t st = nullptr;
             cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
             if (e != cudaSuccess) {
@@ -334,8 +325,7 @@ int pgb_server_create(const pgb_server_opts* opts, pgb_server** out) {
             }
             S->streams.push_back(st);
         }
-        for (int i = 0; i < nstage; ++i) raw->threads.emplace_back(stage_loop, raw, i);
-        if (S->o.mode == PGB_SERVE_BATCHED) raw->threads.emplace_back(batch_loop, raw);
+        for (int i = 0; i < nthreads; ++i) raw->threads.emplace_back(batch_loop, raw, i);
         live_handles_add(1);
         *out = S.release();
     });
@@ -355,13 +345,13 @@ int pgb_server_submit(pgb_server* S, const uint32_t* src, const uint32_t* dst, u
         if (J->est > S->o.budget_bytes)
             fail(PGB_E_BUDGET, "job needs about " + std::to_string(J->est) + " device bytes; budget is " +
                                    std::to_string(S->o.budget_bytes));
-        J->src.resize(m);
-        J->dst.resize(m);
         if (m) {
             if (mem == PGB_MEM_HOST) {
-                std::memcpy(J->src.data(), src, m * 4);
-                std::memcpy(J->dst.data(), dst, m * 4);
+                J->src.assign(src, src + m);
+                J->dst.assign(dst, dst + m);
             } else {
+                J->src.resize(m);
+                J->dst.resize(m);
                 PGB_CUDA(cudaMemcpy(J->src.data(), src, m * 4, cudaMemcpyDeviceToHost));
                 PGB_CUDA(cudaMemcpy(J->dst.data(), dst, m * 4, cudaMemcpyDeviceToHost));
             }
@@ -477,12 +467,9 @@ void pgb_server_destroy(pgb_server* S) {
         }
         S->queued.clear();
         S->cv_queue.notify_all();
-        S->cv_ready.notify_all();
         S->cv_done.notify_all();
     }
     for (auto& t : S->threads) t.join();
-    for (auto& J : S->ready) J->release_device();
-    S->ready.clear();
     S->jobs.clear();
     for (cudaStream_t st : S->streams) {
         cudaStreamSynchronize(st);

@@ -34,11 +34,11 @@ namespace pgb {
 
 namespace {
 
-constexpr int kHThreads = 256;
+constexpr int kHThreads = 128;
 constexpr int kHWarps = kHThreads / 32;
-constexpr uint32_t kKeyCap = 2048;     // table keys per item (load factor <= 1/2)
+constexpr uint32_t kKeyCap = 1024;     // table keys per item (load factor <= 1/2)
 constexpr uint32_t kInChunkDefault = 4096;  // in-edges per item unless the caller sets one
-constexpr int kMaxSlotsLog2 = 12;      // 4096 slots
+constexpr int kMaxSlotsLog2 = 11;      // 2048 slots
 constexpr uint32_t kMaxSlots = 1u << kMaxSlotsLog2;
 constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr unsigned kFullMask = 0xffffffffu;
@@ -206,7 +206,7 @@ __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t
 }
 
 template <bool PV>
-__global__ void __launch_bounds__(kHThreads, 4)
+__global__ void __launch_bounds__(kHThreads, 8)
     k_tc_hash(const HashGraph* __restrict__ graphs, uint32_t njobs, const VItem* __restrict__ items,
               uint32_t nitems, unsigned int* __restrict__ cursor, unsigned long long* __restrict__ partials) {
     extern __shared__ uint32_t hsm[];
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kHThreads, 4)
         __syncthreads();
         // build: a singleton's list is inserted by the whole CTA (bitmap bits,
         // plus table keys for per-vertex counts); a group's members are
-        // spread over the warps (member t to warp t mod 8)
+        // spread over the warps (member t to warp t mod kHWarps)
         uint32_t rb = 0, re = 0;
         if (single) {
             rb = __ldg(G.rowptr + I.v0);

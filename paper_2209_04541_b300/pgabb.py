@@ -506,7 +506,7 @@ PGB_JOB_QUEUED, PGB_JOB_RUNNING, PGB_JOB_DONE, PGB_JOB_FAILED, PGB_JOB_CANCELLED
 class ServerOpts(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32), ("p", ctypes.c_uint32),
                 ("mode", ctypes.c_int32), ("per_vertex", ctypes.c_int32), ("max_batch_jobs", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 9)]
+                ("batch_edges", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 8)]
 
 
 class ServerInfo(ctypes.Structure):

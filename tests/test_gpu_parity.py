@@ -224,12 +224,12 @@ def test_persistent_variants_messy(variant):
 def test_hash_splits_heavy_middle_vertices():
     """K_2100 plus 300 vertices each joined to clique vertices 0, 1, 2.
 
-    In degree order the clique's low members have more than 2048 higher
-    neighbours (their tables are split into key-range slices) and the middle
-    members have more than 256 in-edges (their in-edges are split into
-    chunks).  Closed form: C(2100, 3) clique triangles plus 3 per extra
-    vertex; t = C(2099, 2) on clique vertices, + 2 * 300 on 0, 1, 2, and 3 on
-    each extra vertex."""
+    In degree order the clique's low members have more than 1024 higher
+    neighbours (the hash kernel's table capacity: their tables are split into
+    key-range slices), and with 256 in-edges per work item the high members'
+    in-edges are split into chunks.  Closed form: C(2100, 3) clique triangles
+    plus 3 per extra vertex; t = C(2099, 2) on clique vertices, + 2 * 300 on
+    0, 1, 2, and 3 on each extra vertex."""
     from math import comb
     k, extra = 2100, 300
     a, b = np.triu_indices(k, 1)
@@ -243,9 +243,10 @@ def test_hash_splits_heavy_middle_vertices():
     want_t[k:] = 3
     for variant in VARIANTS:
         for p in (1, 5):
-            gT, gt, _, _, _ = gpu_count(src, dst, n, p, variant=variant)
-            assert gT == comb(k, 3) + 3 * extra
-            assert np.array_equal(gt, want_t)
+            for chunk in (0, 256):
+                gT, gt, _, _, _ = gpu_count(src, dst, n, p, variant=variant, chunk=chunk)
+                assert gT == comb(k, 3) + 3 * extra
+                assert np.array_equal(gt, want_t)
 
 
 def test_plain_mode_rejects_hash():

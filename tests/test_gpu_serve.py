@@ -60,7 +60,8 @@ def test_serve_alone_and_mixed_match_oracle():
     batched, st_b = run_server(jobs, P.PGB_SERVE_BATCHED, max_inflight=4, max_batch_jobs=64)
     serial, st_s = run_server(jobs, P.PGB_SERVE_SERIAL)
     assert st_b["done"] == len(jobs) and st_s["done"] == len(jobs)
-    assert st_b["jobs_in_batches"] == len(jobs)
+    # a job spread over several launches counts once per launch
+    assert st_b["jobs_in_batches"] >= len(jobs)
     for (T, t), (bT, bt, blat), (sT, st, slat) in zip(want, batched, serial):
         assert bT == T and sT == T
         assert np.array_equal(bt, t) and np.array_equal(st, t)
@@ -73,11 +74,66 @@ def test_serve_alone_and_mixed_match_oracle():
 def test_serve_mixed_batches_share_launches():
     jobs = [graphgen.rmat(10, 16, s) for s in range(24)]
     want = expected(jobs)
-    res, st = run_server(jobs, P.PGB_SERVE_BATCHED, max_inflight=8, max_batch_jobs=16)
+    srv = P.pgb_server_create(P.pgb_server_opts_default(max_inflight=2, max_batch_jobs=16))
+    try:
+        P.pgb_server_pause(srv, True)
+        ids = [P.pgb_server_submit(srv, s, d, n) for s, d, n in jobs]
+        P.pgb_server_pause(srv, False)
+        res = [P.pgb_server_wait(srv, j, 120.0, per_vertex=True) for j in ids]
+        st = P.pgb_server_stats(srv)
+    finally:
+        P.pgb_server_destroy(srv)
     assert st["done"] == len(jobs)
-    assert st["batches"] < len(jobs), "batching should count several jobs per launch"
+    assert st["batches"] == 2, "24 queued jobs at 16 per batch make two batches"
     for (T, t), (bT, bt, _) in zip(want, res):
         assert bT == T and np.array_equal(bt, t)
+
+
+@pytest.mark.parametrize("batch_edges", [1, 60000, 0])
+def test_serve_batch_caps_match_oracle(batch_edges):
+    """Batch caps from one job per batch (every job is larger than one edge)
+    to everything in one batch; totals and per-vertex counts stay exact."""
+    jobs = [graphgen.rmat(14, 16, 3), graphgen.rmat(9, 8, 4), graphgen.er_pairs(3000, 40000, 5),
+            graphgen.rgg(5000, None, 6), graphgen.rmat(12, 32, 7)]
+    want = expected(jobs)
+    srv = P.pgb_server_create(P.pgb_server_opts_default(mode=P.PGB_SERVE_BATCHED, max_inflight=1,
+                                                        batch_edges=batch_edges))
+    try:
+        P.pgb_server_pause(srv, True)
+        ids = [P.pgb_server_submit(srv, s, d, n) for s, d, n in jobs]
+        P.pgb_server_pause(srv, False)
+        res = [P.pgb_server_wait(srv, j, 120.0, per_vertex=True) for j in ids]
+        st = P.pgb_server_stats(srv)
+    finally:
+        P.pgb_server_destroy(srv)
+    assert st["done"] == len(jobs)
+    if batch_edges == 1:
+        assert st["batches"] == len(jobs)
+    if batch_edges == 0:
+        assert st["batches"] == 1
+    for (T, t), (bT, bt, _) in zip(want, res):
+        assert bT == T and np.array_equal(bt, t)
+
+
+def test_serve_bad_job_fails_alone_in_a_batch():
+    """A job with an endpoint >= n fails; the jobs batched with it do not."""
+    jobs = [graphgen.rmat(10, 16, 1), (np.array([0, 7, 1], np.uint32), np.array([1, 2, 2], np.uint32), 5),
+            graphgen.rmat(9, 16, 2)]
+    srv = P.pgb_server_create(P.pgb_server_opts_default(max_inflight=1))
+    try:
+        P.pgb_server_pause(srv, True)
+        ids = [P.pgb_server_submit(srv, s, d, n) for s, d, n in jobs]
+        P.pgb_server_pause(srv, False)
+        for k in (0, 2):
+            T, t, _ = P.pgb_server_wait(srv, ids[k], 120.0, per_vertex=True)
+            oT, ot = oracle.tc_node_iterator(oracle.clean(*jobs[k]))
+            assert T == oT and np.array_equal(t, ot)
+        with pytest.raises(P.PgbError) as ei:
+            P.pgb_server_wait(srv, ids[1], 60.0)
+        assert ei.value.code == P.PGB_E_INVAL
+        assert P.pgb_server_stats(srv)["batches"] == 1
+    finally:
+        P.pgb_server_destroy(srv)
 
 
 def test_serve_budget_cancel_timeout_and_failures():
