@@ -85,7 +85,7 @@ static std::shared_ptr<StreamPlan> make_plan(const pgb_blocks* b, uint32_t in_ch
     }
     const uint64_t cap = slot_bytes / (kStreamBytesPerInEdge + sizeof(VItem));  // in-edges per slot
     DevBuf<VItem> ditems;
-    const uint32_t nitems = build_hash_items(b, 0, in_chunk, s, ditems);
+    const uint32_t nitems = build_hash_items(b, in_chunk, s, ditems);
     P->nitems = nitems;
     if (nitems == 0) return P;
     std::vector<VItem> items(nitems);
@@ -164,12 +164,10 @@ void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, unsigned lon
                                          DevBuf<unsigned long long>(slot_edges, s)};
     DevBuf<uint32_t> stail[2] = {DevBuf<uint32_t>(slot_edges, s), DevBuf<uint32_t>(slot_edges, s)};
     DevBuf<VItem> sitems[2] = {DevBuf<VItem>(max_items, s), DevBuf<VItem>(max_items, s)};
-    DevBuf<HashGraph> sg(2, s);
     DevBuf<unsigned int> cursor(2, s);
     HashGraph hg[2];
     for (int k = 0; k < 2; ++k)
         hg[k] = HashGraph{b->rowptr.ptr, b->col.ptr, nullptr, b->colptr.ptr, sxr[k].ptr, tv, b->n, stail[k].ptr};
-    PGB_CUDA(cudaMemcpyAsync(sg.ptr, hg, sizeof(hg), cudaMemcpyHostToDevice, s));
     npartials = (uint64_t)grid * P->chunks.size();
     partials.alloc(npartials, s);
 
@@ -217,8 +215,7 @@ void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, unsigned lon
             PGB_CUDA(cudaEventRecord(ready[k], cs));
             bytes += (uint64_t)ch.span * kStreamBytesPerInEdge + (uint64_t)ch.count * sizeof(VItem);
             PGB_CUDA(cudaStreamWaitEvent(ks[k], ready[k], 0));
-            launch_hash(sg.ptr + k, 1, sitems[k].ptr, ch.count, pv, ks[k], cursor.ptr + k, partials.ptr + c * grid,
-                        grid);
+            launch_hash(hg[k], sitems[k].ptr, ch.count, pv, ks[k], cursor.ptr + k, partials.ptr + c * grid, grid);
             PGB_CUDA(cudaEventRecord(freed[k], ks[k]));
         }
         PGB_CUDA(cudaEventRecord(done1, s1));

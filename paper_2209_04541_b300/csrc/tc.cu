@@ -408,7 +408,7 @@ struct RunPlan {
     // PERSISTENT hash: work items
     DevBuf<VItem> items;
     uint32_t nitems = 0;
-    DevBuf<HashGraph> dg;
+    HashGraph H{};
     DevBuf<unsigned int> cursor;
     int grid = 0;
     const uint32_t* perm = nullptr;
@@ -471,11 +471,9 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
         }
     } else if (variant == PGB_VAR_HASH) {
         // middle-vertex hash variant (tc_hash.cu)
-        P->nitems = build_hash_items(b, 0, o.chunk_edges, s, P->items);
+        P->nitems = build_hash_items(b, o.chunk_edges, s, P->items);
         if (P->nitems) {
-            HashGraph H{b->rowptr.ptr, b->col.ptr, b->rowidx.ptr, b->colptr.ptr, b->xr.ptr, P->tv.ptr, b->n};
-            P->dg.alloc(1, s);
-            PGB_CUDA(cudaMemcpyAsync(P->dg.ptr, &H, sizeof(HashGraph), cudaMemcpyHostToDevice, s));
+            P->H = HashGraph{b->rowptr.ptr, b->col.ptr, b->rowidx.ptr, b->colptr.ptr, b->xr.ptr, P->tv.ptr, b->n};
             P->cursor.alloc(1, s);
             P->grid = hash_grid(P->per_vertex);
             P->npartials = (uint64_t)P->grid;
@@ -543,7 +541,7 @@ static void enqueue(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cudaEvent
         PGB_CHECK_LAUNCHES("k_tc_tuple", T);
     } else if (P.variant == PGB_VAR_HASH) {
         if (P.nitems)
-            launch_hash(P.dg.ptr, 1, P.items.ptr, P.nitems, P.per_vertex, s, P.cursor.ptr, P.partials.ptr, P.grid);
+            launch_hash(P.H, P.items.ptr, P.nitems, P.per_vertex, s, P.cursor.ptr, P.partials.ptr, P.grid);
     } else {
         PGB_CUDA(cudaMemsetAsync(P.cursor.ptr, 0, 4, s));
         if (P.per_vertex)

@@ -146,7 +146,7 @@ __global__ void k_items_count(const uint32_t* __restrict__ rowptr, const uint32_
 
 __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t* __restrict__ colptr,
                              const uint32_t* __restrict__ col, uint32_t n, uint32_t nwin, uint32_t in_chunk,
-                             uint32_t job, const uint32_t* __restrict__ offs, VItem* __restrict__ items) {
+                             const uint32_t* __restrict__ offs, VItem* __restrict__ items) {
     const int lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwin; w += nw) {
@@ -164,7 +164,7 @@ __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t
                 it.hi = n;
                 it.slots_log2 = (uint16_t)slots_for(W.keys);
                 it.clip = 0;
-                it.job = job;
+                it.pad = 0;
                 items[base] = it;
             }
             continue;
@@ -198,7 +198,7 @@ __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t
                     it.clip = 0;
                 }
                 it.slots_log2 = (uint16_t)slots_for(min(kKeyCap, W.dp - kk * kKeyCap));
-                it.job = job;
+                it.pad = 0;
                 items[out++] = it;
             }
         }
@@ -207,7 +207,7 @@ __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t
 
 template <bool PV>
 __global__ void __launch_bounds__(kHThreads, 8)
-    k_tc_hash(const HashGraph* __restrict__ graphs, uint32_t njobs, const VItem* __restrict__ items,
+    k_tc_hash(const HashGraph G, const VItem* __restrict__ items,
               uint32_t nitems, unsigned int* __restrict__ cursor, unsigned long long* __restrict__ partials) {
     extern __shared__ uint32_t hsm[];
     // Region A: the bitmap of a bitmap-mode item, or the keys and member
@@ -219,30 +219,25 @@ __global__ void __launch_bounds__(kHThreads, 8)
     uint32_t* regB = hsm + kRegionA;
     __shared__ uint32_t s_wsum[kHWarps];
     __shared__ VItem s_it, s_itn;      // current item and the next one (prefetched)
-    __shared__ HashGraph s_g, s_gn;
-    __shared__ unsigned long long s_jobcnt[kMaxBatchJobs];
+    __shared__ unsigned long long s_cnt;
     __shared__ uint32_t s_item, s_itemn, s_vmask, s_next;
     __shared__ uint32_t s_edge[kHWarps][32];
     __shared__ uint32_t s_vcnt[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (uint32_t i = tid; i < kRegionA; i += kHThreads) regA[i] = 0;
-    for (uint32_t j = tid; j < njobs; j += kHThreads) s_jobcnt[j] = 0;
+    if (tid == 0) s_cnt = 0;
     if (PV) s_edge[warp][lane] = 0;
     // thread 0 fetches the next item (index, descriptor, graph) ahead into
     // the second shared slot
     if (tid == 0) {
         s_itemn = atomicAdd(cursor, 1u);
-        if (s_itemn < nitems) {
-            s_itn = items[s_itemn];
-            s_gn = graphs[s_itn.job];
-        }
+        if (s_itemn < nitems) s_itn = items[s_itemn];
     }
     unsigned long long cnt = 0;
     for (;;) {
         if (tid == 0) {
             s_item = s_itemn;
             s_it = s_itn;
-            s_g = s_gn;
             s_vmask = 0;
             s_next = 0;
         }
@@ -250,7 +245,6 @@ __global__ void __launch_bounds__(kHThreads, 8)
         __syncthreads();
         if (s_item >= nitems) break;
         const VItem I = s_it;
-        const HashGraph& G = s_g;
         const bool single = I.nv == 1;
         // third-vertex range of the item: a singleton's partner entries all
         // exceed v, so its range starts at v + 1
@@ -323,10 +317,7 @@ __global__ void __launch_bounds__(kHThreads, 8)
         }
         if (tid == 0) {
             s_itemn = atomicAdd(cursor, 1u);
-            if (s_itemn < nitems) {
-                s_itn = items[s_itemn];
-                s_gn = graphs[s_itn.job];
-            }
+            if (s_itemn < nitems) s_itn = items[s_itemn];
         }
         const uint32_t vmask = s_vmask;
         // probe: warps take batches of 32 in-edges from a shared counter (so a
@@ -449,10 +440,10 @@ __global__ void __launch_bounds__(kHThreads, 8)
                 __syncwarp();
             }
         }
-        // the item's count goes to its job's shared accumulator
+        // the item's count goes to the CTA's shared accumulator
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFullMask, cnt, o);
-        if (lane == 0 && cnt) atomicAdd(&s_jobcnt[I.job], cnt);
+        if (lane == 0 && cnt) atomicAdd(&s_cnt, cnt);
         cnt = 0;
         __syncthreads();
         if (PV) {
@@ -481,9 +472,9 @@ __global__ void __launch_bounds__(kHThreads, 8)
         }
         __syncthreads();
     }
-    // per-job CTA totals: partials[job * gridDim.x + blockIdx.x]
+    // the CTA's total: partials[blockIdx.x]
     __syncthreads();
-    for (uint32_t j = tid; j < njobs; j += kHThreads) partials[(size_t)j * gridDim.x + blockIdx.x] = s_jobcnt[j];
+    if (tid == 0) partials[blockIdx.x] = s_cnt;
 }
 
 template <bool PV>
@@ -495,7 +486,7 @@ size_t hash_smem() {
 
 }  // namespace
 
-uint32_t build_hash_items(const pgb_blocks* b, uint32_t job, uint32_t in_chunk, cudaStream_t s,
+uint32_t build_hash_items(const pgb_blocks* b, uint32_t in_chunk, cudaStream_t s,
                           DevBuf<VItem>& items) {
     if (in_chunk == 0) in_chunk = kInChunkDefault;
     const uint32_t n = b->n;
@@ -519,7 +510,7 @@ uint32_t build_hash_items(const pgb_blocks* b, uint32_t job, uint32_t in_chunk, 
     PGB_CUDA(cudaStreamSynchronize(s));
     items.alloc(std::max<uint32_t>(nitems, 1), s);
     if (nitems) {
-        k_items_emit<<<wgrid, 256, 0, s>>>(b->rowptr.ptr, b->colptr.ptr, b->col.ptr, n, nwin, in_chunk, job, offs.ptr,
+        k_items_emit<<<wgrid, 256, 0, s>>>(b->rowptr.ptr, b->colptr.ptr, b->col.ptr, n, nwin, in_chunk, offs.ptr,
                                            items.ptr);
         PGB_CHECK_LAUNCH("k_items_emit");
     }
@@ -541,43 +532,15 @@ int hash_grid(bool pv) {
     return std::max(1, per_sm) * sms;
 }
 
-void launch_hash(const HashGraph* d_graphs, uint32_t njobs, const VItem* items, uint32_t nitems, bool pv,
+void launch_hash(const HashGraph& G, const VItem* items, uint32_t nitems, bool pv,
                  cudaStream_t s, unsigned int* cursor, unsigned long long* partials, int grid) {
-    if (njobs == 0 || njobs > kMaxBatchJobs) fail(PGB_E_INVAL, "jobs per launch must be in [1, 256]");
     const size_t smem = pv ? hash_smem<true>() : hash_smem<false>();
     PGB_CUDA(cudaMemsetAsync(cursor, 0, 4, s));
     if (pv)
-        k_tc_hash<true><<<grid, kHThreads, smem, s>>>(d_graphs, njobs, items, nitems, cursor, partials);
+        k_tc_hash<true><<<grid, kHThreads, smem, s>>>(G, items, nitems, cursor, partials);
     else
-        k_tc_hash<false><<<grid, kHThreads, smem, s>>>(d_graphs, njobs, items, nitems, cursor, partials);
+        k_tc_hash<false><<<grid, kHThreads, smem, s>>>(G, items, nitems, cursor, partials);
     PGB_CHECK_LAUNCH("k_tc_hash");
-}
-
-void run_hash(const pgb_blocks* b, const HashGraph& G, bool pv, uint32_t in_chunk, cudaStream_t s,
-              DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0, cudaEvent_t ev1,
-              HashRunStats* stats) {
-    npartials = 0;
-    DevBuf<VItem> items;
-    const uint32_t nitems = build_hash_items(b, 0, in_chunk, s, items);
-    if (nitems == 0) {
-        PGB_CUDA(cudaEventRecord(ev0, s));
-        PGB_CUDA(cudaEventRecord(ev1, s));
-        return;
-    }
-    DevBuf<HashGraph> dg(1, s);
-    PGB_CUDA(cudaMemcpyAsync(dg.ptr, &G, sizeof(HashGraph), cudaMemcpyHostToDevice, s));
-    DevBuf<unsigned int> cursor(1, s);
-    const int grid = hash_grid(pv);
-    npartials = (uint64_t)grid;
-    partials.alloc(npartials, s);
-    PGB_CUDA(cudaEventRecord(ev0, s));
-    launch_hash(dg.ptr, 1, items.ptr, nitems, pv, s, cursor.ptr, partials.ptr, grid);
-    PGB_CUDA(cudaEventRecord(ev1, s));
-    // the host copy of G above is pageable, so the copy is staged before return
-    if (stats) {
-        stats->items = nitems;
-        stats->grid = grid;
-    }
 }
 
 }  // namespace pgb

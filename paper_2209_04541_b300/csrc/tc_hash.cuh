@@ -20,40 +20,25 @@ struct HashGraph {
 struct VItem {
     uint32_t v0;          // first middle vertex (rank)
     uint32_t nv;          // consecutive middle vertices in the item (<= 32)
-    uint32_t in_begin;    // in-edge range [in_begin, in_end) of the job's in-edge index
+    uint32_t in_begin;    // in-edge range [in_begin, in_end) of the in-edge index
     uint32_t in_end;
     uint32_t lo, hi;      // third-vertex rank range
     uint16_t slots_log2;  // hash table size
     uint16_t clip;        // 1 when lists are clipped to [lo, hi)
-    uint32_t job;         // index into the launch's table of graphs
+    uint32_t pad;         // keeps items 32 bytes
 };
 
-constexpr uint32_t kMaxBatchJobs = 256;  // jobs one launch may interleave
-
-struct HashRunStats {
-    uint32_t items = 0;
-    int grid = 0;
-};
-
-// Work items of one partitioned graph, tagged `job`; returns their number
-// (synchronises `s` once to learn it).
-uint32_t build_hash_items(const pgb_blocks* b, uint32_t job, uint32_t in_chunk, cudaStream_t s, DevBuf<VItem>& items);
+// Work items of one partitioned graph; returns their number (synchronises
+// `s` once to learn it).  in_chunk: in-edges per item (0 = default).
+uint32_t build_hash_items(const pgb_blocks* b, uint32_t in_chunk, cudaStream_t s, DevBuf<VItem>& items);
 
 // CTAs of a persistent launch on the current device.
 int hash_grid(bool pv);
 
-// One persistent launch over the items of njobs graphs (d_graphs[job] in
-// device memory); partials must hold njobs * grid entries and receive
-// partials[job * grid + cta].
-void launch_hash(const HashGraph* d_graphs, uint32_t njobs, const VItem* items, uint32_t nitems, bool pv,
-                 cudaStream_t s, unsigned int* cursor, unsigned long long* partials, int grid);
-
-// Builds the work items and launches the persistent hash kernel on `s`
-// between events ev0 and ev1; per-CTA totals land in `partials`.
-// in_chunk: in-edges per work item (0 = default).
-void run_hash(const pgb_blocks* b, const HashGraph& G, bool pv, uint32_t in_chunk, cudaStream_t s,
-              DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0, cudaEvent_t ev1,
-              HashRunStats* stats);
+// One persistent launch over `nitems` work items of graph G; partials must
+// hold `grid` entries and receive one total per CTA.
+void launch_hash(const HashGraph& G, const VItem* items, uint32_t nitems, bool pv, cudaStream_t s,
+                 unsigned int* cursor, unsigned long long* partials, int grid);
 
 // Streamed run over blocks whose in-edge index is in pinned host memory:
 // chunks of work items whose in-edges fit two device slots within `budget`
