@@ -217,11 +217,40 @@ void pgb_blocks_free(pgb_blocks* b);
  * PGB_E_NOMEM (pinned allocation), PGB_E_CUDA. */
 int pgb_blocks_offload(pgb_blocks* b, void* stream);
 
+/* Block cache tier (Section 4.4's copies of a task's blocks, with eviction):
+ * moves the columns to pinned host memory as well, so that the device keeps
+ * only the row offsets, the rank permutation and the cuts (about 8 bytes per
+ * vertex; runs add 16 per vertex of counters).  Row block i of the columns
+ * (ranks [c_i, c_{i+1})) is one contiguous slice.  The in-edge index is
+ * re-sorted by (tail block, head, tail) into pinned host memory and cut into
+ * pieces of at most 2^21 in-edges of one block pair (tail block i, head
+ * block j); each piece's work items are built here, once.  A run keeps a
+ * cache of column slices on the device, as many as device_budget allows
+ * (at least two), evicting the least recently used slice that the current
+ * pieces do not need; it counts the pieces head-block group by head-block
+ * group so that the group's slices stay while the tail slices pass through,
+ * and overlaps the copies (side stream) with the counting launches.  Call it
+ * on resident blocks (PGB_E_STATE after pgb_blocks_offload); afterwards the
+ * blocks behave as offloaded (PERSISTENT + hash only; chunk_edges ignored).
+ * Needs about 36 bytes per edge of device memory while it builds the index.
+ * Synchronises `stream`.  Errors: PGB_E_INVAL, PGB_E_STATE, PGB_E_NOMEM,
+ * PGB_E_CUDA. */
+int pgb_blocks_offload_columns(pgb_blocks* b, void* stream);
+
+/* After pgb_blocks_offload_columns: the smallest device_budget whose column
+ * cache holds `slices` slices (capped at p) for runs with the given
+ * per_vertex setting.  Queries the current device.  Errors: PGB_E_INVAL
+ * (NULL), PGB_E_STATE (columns not offloaded). */
+int pgb_blocks_cache_budget(const pgb_blocks* b, int per_vertex, uint32_t slices, uint64_t* budget);
+
 /* The device bytes a streamed run on `b` holds besides its two stream slots:
  * 4(n+1) + 4(m+4) + 4(n+1) + 4n + 4(p+1) for the resident arrays, 16n for the
  * per-vertex counters when per_vertex != 0, and 16 MiB for the launches'
  * partial sums.  A device_budget must exceed it; the rest is split into two
  * slots of 44 bytes per in-edge (index entry plus one work item bound).
+ * After pgb_blocks_offload_columns: 4(n+1) + 4n + 4(p+1), 16n for the
+ * counters, and 16 MiB; a budget must also cover two piece slots and at
+ * least two column slices (PGB_E_BUDGET otherwise).
  * Errors: PGB_E_INVAL (NULL). */
 int pgb_blocks_resident_bytes(const pgb_blocks* b, int per_vertex, uint64_t* bytes);
 
@@ -264,9 +293,11 @@ int pgb_tc_result_triples(pgb_tc_result* r, uint64_t* counts, int mem);
 /* The variant that ran (PGB_VAR_BSEARCH, PGB_VAR_MERGE or PGB_VAR_HASH). */
 int pgb_tc_result_variant(pgb_tc_result* r, int* variant);
 
-/* Streamed runs: host-to-device bytes copied (in-edge index slices and work
- * items) and the number of chunks; both 0 for a run on resident blocks. */
-int pgb_tc_result_stream(pgb_tc_result* r, uint64_t* bytes, uint32_t* chunks);
+/* Streamed runs: host-to-device bytes copied (index slices, work items and,
+ * for column-offloaded blocks, column slices), the number of chunks (pieces
+ * for column-offloaded blocks) and, when slice_loads is not NULL, the column
+ * slices copied in (cache misses); all 0 for a run on resident blocks. */
+int pgb_tc_result_stream(pgb_tc_result* r, uint64_t* bytes, uint32_t* chunks, uint32_t* slice_loads);
 
 /* Device time of the counting kernels of this run in milliseconds (CUDA
  * events around the launches on the run's stream; for a streamed run this

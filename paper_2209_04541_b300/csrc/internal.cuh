@@ -163,6 +163,10 @@ struct pgb_blocks {
     bool offloaded = false;
     unsigned long long* h_xr = nullptr;
     uint32_t* h_itail = nullptr;
+    // columns offloaded too (pgb_blocks_offload_columns): slices, the
+    // tail-block-major index and the pieces' work items (stream.cu)
+    bool cols_offloaded = false;
+    std::shared_ptr<void> col_plan;
     // chunking of the last streamed run's settings (stream.cu)
     mutable std::shared_ptr<void> stream_plan;
     // captured runs (use_graph), at most four settings (tc.cu)
@@ -200,5 +204,7 @@ void ingest_keys(pgb_graph* g, const uint32_t* src, const uint32_t* dst, uint64_
 void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, pgb_blocks* b);
 void ensure_block_edge_index(const pgb_blocks* b, cudaStream_t s);
 void copy_out(void* dst, const void* src_dev, size_t bytes, int mem, cudaStream_t s);
+// Pinned host copy of the columns after pgb_blocks_offload_columns, else null.
+const uint32_t* offloaded_columns(const pgb_blocks* b);
 
 }  // namespace pgb

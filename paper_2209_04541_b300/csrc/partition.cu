@@ -447,7 +447,14 @@ int pgb_blocks_export(const pgb_blocks* b, int what, void* dst, int mem, void* s
                 PGB_CUDA(cudaStreamSynchronize(s));
                 break;
             }
-            case PGB_EXPORT_COL: copy_out(dst, b->col.ptr, b->m * 4, mem, s); break;
+            case PGB_EXPORT_COL:
+                if (b->cols_offloaded) {
+                    if (b->m)
+                        PGB_CUDA(cudaMemcpyAsync(dst, offloaded_columns(b), b->m * 4, cudaMemcpyDefault, s));
+                } else {
+                    copy_out(dst, b->col.ptr, b->m * 4, mem, s);
+                }
+                break;
             case PGB_EXPORT_CUTS: host_or_dev(b->cuts.data(), b->cuts.size() * 4); break;
             case PGB_EXPORT_BLOCK_EDGES: host_or_dev(b->block_edges.data(), b->block_edges.size() * 8); break;
             case PGB_EXPORT_TRIPLES: {

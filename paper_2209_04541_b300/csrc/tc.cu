@@ -342,7 +342,8 @@ struct pgb_tc_result {
     uint64_t ntriples = 0;
     int variant = PGB_VAR_BSEARCH;  // the variant that ran
     uint64_t streamed = 0;          // host-to-device bytes of a streamed run
-    uint32_t chunks = 0;            // stream chunks of a streamed run (0 = resident)
+    uint32_t chunks = 0;            // stream chunks (or pieces) of a streamed run (0 = resident)
+    uint32_t slice_loads = 0;       // column slices copied in (column-streamed runs)
     pgb::DevBuf<unsigned long long> total;
     pgb::DevBuf<unsigned long long> tv_orig;
     pgb::DevBuf<unsigned long long> triple_counts;
@@ -473,7 +474,7 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
         // middle-vertex hash variant (tc_hash.cu)
         P->nitems = build_hash_items(b, o.chunk_edges, s, P->items);
         if (P->nitems) {
-            P->H = HashGraph{b->rowptr.ptr, b->col.ptr, b->rowidx.ptr, b->colptr.ptr, b->xr.ptr, P->tv.ptr, b->n};
+            P->H = resident_hash_graph(b, P->tv.ptr);
             P->cursor.alloc(1, s);
             P->grid = hash_grid(P->per_vertex);
             P->npartials = (uint64_t)P->grid;
@@ -614,8 +615,12 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
             tv.alloc(n, s);
             if (n) PGB_CUDA(cudaMemsetAsync(tv.ptr, 0, (size_t)n * 8, s));
         }
-        run_streaming(b, o.chunk_edges, r->per_vertex, tv.ptr, o.device_budget, s, partials, npartials, r->ev0,
-                      r->ev1, &r->streamed, &r->chunks);
+        if (b->cols_offloaded)
+            run_column_streaming(b, r->per_vertex, tv.ptr, o.device_budget, s, partials, npartials, r->ev0, r->ev1,
+                                 &r->streamed, &r->chunks, &r->slice_loads);
+        else
+            run_streaming(b, o.chunk_edges, r->per_vertex, tv.ptr, o.device_budget, s, partials, npartials, r->ev0,
+                          r->ev1, &r->streamed, &r->chunks);
         if (npartials)
             k_reduce_sum<<<1, 1024, 0, s>>>(partials.ptr, npartials, r->total.ptr);
         else
@@ -746,11 +751,12 @@ int pgb_tc_result_variant(pgb_tc_result* r, int* variant) {
     });
 }
 
-int pgb_tc_result_stream(pgb_tc_result* r, uint64_t* bytes, uint32_t* chunks) {
+int pgb_tc_result_stream(pgb_tc_result* r, uint64_t* bytes, uint32_t* chunks, uint32_t* slice_loads) {
     return guard([&] {
         if (!r || !bytes || !chunks) fail(PGB_E_INVAL, "NULL argument");
         *bytes = r->streamed;
         *chunks = r->chunks;
+        if (slice_loads) *slice_loads = r->slice_loads;
     });
 }
 

@@ -70,6 +70,12 @@ __device__ __forceinline__ uint32_t hlower_bound(const uint32_t* __restrict__ a,
     return b;
 }
 
+// hlower_bound over an array whose entry q is stored at a[q - base].
+__device__ __forceinline__ uint32_t hlower_bound_b(const uint32_t* __restrict__ a, uint32_t base, uint32_t b,
+                                                   uint32_t e, uint32_t x) {
+    return hlower_bound(a, b - base, e - base, x) + base;
+}
+
 __device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFullMask, x, o);
@@ -114,15 +120,13 @@ struct WindowInfo {
     uint32_t mine;  // singleton items of this lane
 };
 
-__device__ __forceinline__ WindowInfo window_info(const uint32_t* __restrict__ rowptr,
-                                                  const uint32_t* __restrict__ colptr, uint32_t n, uint32_t w,
-                                                  uint32_t in_chunk, int lane) {
+__device__ __forceinline__ WindowInfo window_info(const ItemSpace& sp, uint32_t w, uint32_t in_chunk, int lane) {
     WindowInfo W;
-    W.v = w * 32 + lane;
+    W.v = sp.w0 + w * 32 + lane;
     W.dp = W.dm = 0;
-    if (W.v < n) {
-        W.dp = rowptr[W.v + 1] - rowptr[W.v];
-        W.dm = colptr[W.v + 1] - colptr[W.v];
+    if (W.v < sp.n) {
+        W.dp = sp.rowptr[W.v + 1] - sp.rowptr[W.v];
+        W.dm = sp.colptr[W.v + 1 - sp.cbase] - sp.colptr[W.v - sp.cbase];
     }
     W.act = W.dp > 0 && W.dm > 0;
     W.keys = warp_sum(W.act ? W.dp : 0);
@@ -133,38 +137,38 @@ __device__ __forceinline__ WindowInfo window_info(const uint32_t* __restrict__ r
 }
 
 // counts[nwin - 1 - w] = items of window w (windows of high ranks first).
-__global__ void k_items_count(const uint32_t* __restrict__ rowptr, const uint32_t* __restrict__ colptr, uint32_t n,
-                              uint32_t nwin, uint32_t in_chunk, uint32_t* __restrict__ counts) {
+__global__ void k_items_count(const ItemSpace sp, uint32_t in_chunk, uint32_t* __restrict__ counts) {
     const int lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwin; w += nw) {
-        WindowInfo W = window_info(rowptr, colptr, n, w, in_chunk, lane);
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < sp.nwin; w += nw) {
+        WindowInfo W = window_info(sp, w, in_chunk, lane);
         uint32_t c = W.keys == 0 ? 0 : (W.group ? 1 : warp_sum(W.mine));
-        if (lane == 0) counts[nwin - 1 - w] = c;
+        if (lane == 0) counts[sp.nwin - 1 - w] = c;
     }
 }
 
-__global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t* __restrict__ colptr,
-                             const uint32_t* __restrict__ col, uint32_t n, uint32_t nwin, uint32_t in_chunk,
-                             const uint32_t* __restrict__ offs, VItem* __restrict__ items) {
+__global__ void k_items_emit(const ItemSpace sp, uint32_t in_chunk, const uint32_t* __restrict__ offs,
+                             VItem* __restrict__ items) {
     const int lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwin; w += nw) {
-        WindowInfo W = window_info(rowptr, colptr, n, w, in_chunk, lane);
+    const uint32_t n = sp.n;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < sp.nwin; w += nw) {
+        WindowInfo W = window_info(sp, w, in_chunk, lane);
         if (W.keys == 0) continue;
-        const uint32_t base = offs[nwin - 1 - w];
+        const uint32_t base = offs[sp.nwin - 1 - w];
+        const unsigned act = __ballot_sync(kFullMask, W.act);
         if (W.group) {
             if (lane == 0) {
                 VItem it;
-                it.v0 = w * 32;
-                it.nv = min(32u, n - w * 32);
-                it.in_begin = colptr[it.v0];
-                it.in_end = colptr[it.v0 + it.nv];
+                it.v0 = sp.w0 + w * 32;
+                it.nv = min(32u, n - it.v0);
+                it.in_begin = sp.colptr[it.v0 - sp.cbase];
+                it.in_end = sp.colptr[it.v0 + it.nv - sp.cbase];
                 it.lo = 0;
                 it.hi = n;
                 it.slots_log2 = (uint16_t)slots_for(W.keys);
                 it.clip = 0;
-                it.pad = 0;
+                it.mask = act;
                 items[base] = it;
             }
             continue;
@@ -179,7 +183,7 @@ __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t
         if (!W.mine) continue;
         const uint32_t na = (W.dm + in_chunk - 1) / in_chunk;
         const uint32_t nk = (W.dp + kKeyCap - 1) / kKeyCap;
-        const uint32_t rb = rowptr[W.v], cb = colptr[W.v];
+        const uint32_t rb = sp.rowptr[W.v], cb = sp.colptr[W.v - sp.cbase];
         uint32_t out = base + excl;
         for (uint32_t a = 0; a < na; ++a) {
             for (uint32_t kk = 0; kk < nk; ++kk) {
@@ -189,8 +193,8 @@ __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t
                 it.in_begin = cb + a * in_chunk;
                 it.in_end = min(it.in_begin + in_chunk, cb + W.dm);
                 if (nk > 1) {
-                    it.lo = col[rb + kk * kKeyCap];
-                    it.hi = (kk + 1 < nk) ? col[rb + (kk + 1) * kKeyCap] : n;
+                    it.lo = sp.col[rb + kk * kKeyCap - sp.vbase];
+                    it.hi = (kk + 1 < nk) ? sp.col[rb + (kk + 1) * kKeyCap - sp.vbase] : n;
                     it.clip = 1;
                 } else {
                     it.lo = 0;
@@ -198,7 +202,7 @@ __global__ void k_items_emit(const uint32_t* __restrict__ rowptr, const uint32_t
                     it.clip = 0;
                 }
                 it.slots_log2 = (uint16_t)slots_for(min(kKeyCap, W.dp - kk * kKeyCap));
-                it.pad = 0;
+                it.mask = 1u;
                 items[out++] = it;
             }
         }
@@ -271,24 +275,27 @@ __global__ void __launch_bounds__(kHThreads, 8)
             rb = __ldg(G.rowptr + I.v0);
             re = __ldg(G.rowptr + I.v0 + 1);
             if (I.clip) {
-                rb = hlower_bound(G.col, rb, re, I.lo);
-                re = hlower_bound(G.col, rb, re, I.hi);
+                rb = hlower_bound_b(G.col, G.vbase, rb, re, I.lo);
+                re = hlower_bound_b(G.col, G.vbase, rb, re, I.hi);
             }
             if (tid == 0 && rb < re) s_vmask = 1u;
             for (uint32_t q = rb + tid; q < re; q += kHThreads) {
-                const uint32_t x = __ldg(G.col + q);
+                const uint32_t x = __ldg(G.col + (q - G.vbase));
                 if (bitmap) atomicOr(&regA[(x - rlo) >> 5], 1u << ((x - rlo) & 31));
                 else table_insert(keys, masks, x, 0u, L);
             }
         } else {
             for (uint32_t t = warp; t < I.nv; t += kHWarps) {
                 const uint32_t v = I.v0 + t;
-                if (__ldg(G.colptr + v + 1) == __ldg(G.colptr + v)) continue;
+                // only members with in-edges in this item's index: the table
+                // is sized for their lists alone
+                if (!((I.mask >> t) & 1u)) continue;
                 const uint32_t b = __ldg(G.rowptr + v), e = __ldg(G.rowptr + v + 1);
                 if (b >= e) continue;
                 const uint32_t bit = 1u << t;
                 if (lane == 0) atomicOr(&s_vmask, bit);
-                for (uint32_t q = b + lane; q < e; q += 32) table_insert(keys, masks, __ldg(G.col + q), bit, L);
+                for (uint32_t q = b + lane; q < e; q += 32)
+                    table_insert(keys, masks, __ldg(G.col + (q - G.vbase)), bit, L);
             }
         }
         __syncthreads();
@@ -335,12 +342,12 @@ __global__ void __launch_bounds__(kHThreads, 8)
                 e = xb - 1;
                 // a singleton item's in-edges all end at v0; a group's need
                 // the head read back to pick the member bit
-                const uint32_t v = single ? I.v0 : __ldg(G.col + e);
+                const uint32_t v = single ? I.v0 : __ldg(G.colu + (e - G.ubase));
                 vbit = 1u << (v - I.v0);
                 if (vmask & vbit) {
                     if (I.clip) {
-                        xb = hlower_bound(G.col, xb, xe, I.lo);
-                        xe = hlower_bound(G.col, xb, xe, I.hi);
+                        xb = hlower_bound_b(G.colu, G.ubase, xb, xe, I.lo);
+                        xe = hlower_bound_b(G.colu, G.ubase, xb, xe, I.hi);
                     }
                     sb = xb;
                     sl = xe - xb;
@@ -381,7 +388,7 @@ __global__ void __launch_bounds__(kHThreads, 8)
                     bits[j] = __shfl_sync(kFullMask, vbit, o);
                     own[j] = o;
                     qb[j] = 4 * ((lo_[j] >> 2) + (f - o_ex));
-                    qv[j] = f < total ? __ldg(reinterpret_cast<const uint4*>(G.col + qb[j]))
+                    qv[j] = f < total ? __ldg(reinterpret_cast<const uint4*>(G.colu + (qb[j] - G.ubase)))
                                       : make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
                     if (f >= total) hi_[j] = 0;
                 }
@@ -451,7 +458,7 @@ __global__ void __launch_bounds__(kHThreads, 8)
                 // the key of rank i is the i-th entry of v's (clipped) list
                 for (uint32_t i = tid; i < re - rb; i += kHThreads) {
                     const uint32_t c = cnts[i];
-                    if (c) atomicAdd(G.tv + __ldg(G.col + rb + i), (unsigned long long)c);
+                    if (c) atomicAdd(G.tv + __ldg(G.col + (rb + i - G.vbase)), (unsigned long long)c);
                 }
             } else {
                 for (uint32_t i = tid; i < S; i += kHThreads) {
@@ -463,7 +470,7 @@ __global__ void __launch_bounds__(kHThreads, 8)
         }
         // leave region A all zero for the next item
         if (bitmap) {
-            for (uint32_t q = rb + tid; q < re; q += kHThreads) regA[(__ldg(G.col + q) - rlo) >> 5] = 0;
+            for (uint32_t q = rb + tid; q < re; q += kHThreads) regA[(__ldg(G.col + (q - G.vbase)) - rlo) >> 5] = 0;
         } else {
             for (uint32_t i = tid; i < S; i += kHThreads) {
                 regA[i] = 0;
@@ -486,19 +493,17 @@ size_t hash_smem() {
 
 }  // namespace
 
-uint32_t build_hash_items(const pgb_blocks* b, uint32_t in_chunk, cudaStream_t s,
-                          DevBuf<VItem>& items) {
+uint32_t build_hash_items_in(const ItemSpace& sp, uint32_t in_chunk, cudaStream_t s, DevBuf<VItem>& items) {
     if (in_chunk == 0) in_chunk = kInChunkDefault;
-    const uint32_t n = b->n;
-    const uint32_t nwin = (n + 31) / 32;
-    if (b->m == 0 || nwin == 0) {
+    const uint32_t nwin = sp.nwin;
+    if (nwin == 0) {
         items.alloc(1, s);
         return 0;
     }
     DevBuf<uint32_t> counts((size_t)nwin + 1, s), offs((size_t)nwin + 1, s);
     PGB_CUDA(cudaMemsetAsync(counts.ptr + nwin, 0, 4, s));
     const int wgrid = (int)std::min<uint64_t>(((uint64_t)nwin * 32 + 255) / 256, 148ull * 64);
-    k_items_count<<<wgrid, 256, 0, s>>>(b->rowptr.ptr, b->colptr.ptr, n, nwin, in_chunk, counts.ptr);
+    k_items_count<<<wgrid, 256, 0, s>>>(sp, in_chunk, counts.ptr);
     PGB_CHECK_LAUNCH("k_items_count");
     Scratch scratch;
     size_t tmp = 0;
@@ -510,11 +515,25 @@ uint32_t build_hash_items(const pgb_blocks* b, uint32_t in_chunk, cudaStream_t s
     PGB_CUDA(cudaStreamSynchronize(s));
     items.alloc(std::max<uint32_t>(nitems, 1), s);
     if (nitems) {
-        k_items_emit<<<wgrid, 256, 0, s>>>(b->rowptr.ptr, b->colptr.ptr, b->col.ptr, n, nwin, in_chunk, offs.ptr,
-                                           items.ptr);
+        k_items_emit<<<wgrid, 256, 0, s>>>(sp, in_chunk, offs.ptr, items.ptr);
         PGB_CHECK_LAUNCH("k_items_emit");
     }
     return nitems;
+}
+
+uint32_t build_hash_items(const pgb_blocks* b, uint32_t in_chunk, cudaStream_t s, DevBuf<VItem>& items) {
+    if (b->m == 0) {
+        items.alloc(1, s);
+        return 0;
+    }
+    const ItemSpace sp{b->rowptr.ptr, b->colptr.ptr, b->col.ptr, 0, 0, 0, (b->n + 31) / 32, b->n};
+    return build_hash_items_in(sp, in_chunk, s, items);
+}
+
+HashGraph resident_hash_graph(const pgb_blocks* b, unsigned long long* tv) {
+    HashGraph G{b->rowptr.ptr, b->col.ptr, b->rowidx.ptr, b->xr.ptr, tv, b->n};
+    G.colu = b->col.ptr;
+    return G;
 }
 
 int hash_grid(bool pv) {

@@ -7,13 +7,24 @@ namespace pgb {
 
 struct HashGraph {
     const uint32_t* __restrict__ rowptr;
-    const uint32_t* __restrict__ col;
+    const uint32_t* __restrict__ col;     // rows of the middle vertices: entry q at col[q - vbase]
     const uint32_t* __restrict__ rowidx;
-    const uint32_t* __restrict__ colptr;
     const unsigned long long* __restrict__ xr;
     unsigned long long* __restrict__ tv;  // per-vertex counts, rank space (may be null)
     uint32_t n;                           // vertices
     const uint32_t* __restrict__ itail = nullptr;  // tail of each in-edge (streamed runs), else null
+    const uint32_t* __restrict__ colu = nullptr;   // rows of the tails: entry q at colu[q - ubase]
+    uint32_t vbase = 0, ubase = 0;                 // ubase is a multiple of 4
+};
+
+// Where the item builder finds the heads of a set of in-edges: window w
+// covers heads w0 + 32w .. w0 + 32w + 31; in-degrees come from
+// colptr[v - cbase], out-rows from rowptr (global) and col[q - vbase].
+struct ItemSpace {
+    const uint32_t* rowptr;
+    const uint32_t* colptr;
+    const uint32_t* col;
+    uint32_t cbase, vbase, w0, nwin, n;
 };
 
 // One work item of the middle-vertex kernel (built on the device).
@@ -25,12 +36,19 @@ struct VItem {
     uint32_t lo, hi;      // third-vertex rank range
     uint16_t slots_log2;  // hash table size
     uint16_t clip;        // 1 when lists are clipped to [lo, hi)
-    uint32_t pad;         // keeps items 32 bytes
+    uint32_t mask;        // members with in-edges and out-edges in this item's index (bit t: v0 + t)
 };
 
 // Work items of one partitioned graph; returns their number (synchronises
 // `s` once to learn it).  in_chunk: in-edges per item (0 = default).
 uint32_t build_hash_items(const pgb_blocks* b, uint32_t in_chunk, cudaStream_t s, DevBuf<VItem>& items);
+
+// The same over an item space (a range of heads with their own in-edge
+// offsets); item in-edge ranges are positions in those offsets.
+uint32_t build_hash_items_in(const ItemSpace& sp, uint32_t in_chunk, cudaStream_t s, DevBuf<VItem>& items);
+
+// The graph view of a resident partition for the hash kernel.
+HashGraph resident_hash_graph(const pgb_blocks* b, unsigned long long* tv);
 
 // CTAs of a persistent launch on the current device.
 int hash_grid(bool pv);
@@ -47,5 +65,13 @@ void launch_hash(const HashGraph& G, const VItem* items, uint32_t nitems, bool p
 void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, unsigned long long* tv, uint64_t budget,
                    cudaStream_t s, DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
                    cudaEvent_t ev1, uint64_t* streamed, uint32_t* nchunks);
+
+// Run over blocks whose columns are offloaded too: pieces of block pairs
+// (tail block, head block) with their column slices in a device cache that
+// the budget sizes.  Returns after the work completes; partials gets two
+// running totals.
+void run_column_streaming(const pgb_blocks* b, bool pv, unsigned long long* tv, uint64_t budget, cudaStream_t s,
+                          DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
+                          cudaEvent_t ev1, uint64_t* streamed, uint32_t* npieces, uint32_t* slice_loads);
 
 }  // namespace pgb

@@ -108,7 +108,10 @@ _SIGS = {
     "pgb_tc_result_triples": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "pgb_tc_result_kernel_ms": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "pgb_tc_result_variant": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
-    "pgb_tc_result_stream": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)]),
+    "pgb_tc_result_stream": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32),
+                                            ctypes.POINTER(ctypes.c_uint32)]),
+    "pgb_blocks_offload_columns": (ctypes.c_int, [_VP, _VP]),
+    "pgb_blocks_cache_budget": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]),
     "pgb_tc_result_free": (None, [_VP]),
     "pgb_tc_count_edges": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                           ctypes.c_int, ctypes.POINTER(TcOpts), ctypes.c_int, _VP,
@@ -431,6 +434,20 @@ def pgb_tc_result_variant(r: Result) -> int:
     return int(v.value)
 
 
+def pgb_blocks_offload_columns(b: Blocks, stream=None):
+    """Move the columns and a tail-block-major in-edge index of ``b`` to pinned
+    host memory (block-cache runs)."""
+    st = _stream(stream) if stream is not None else b.stream
+    _check(load().pgb_blocks_offload_columns(b, st), "pgb_blocks_offload_columns")
+
+
+def pgb_blocks_cache_budget(b: Blocks, slices: int, per_vertex: bool = True) -> int:
+    """Smallest device_budget whose column cache holds ``slices`` slices."""
+    v = ctypes.c_uint64()
+    _check(load().pgb_blocks_cache_budget(b, int(per_vertex), slices, ctypes.byref(v)), "pgb_blocks_cache_budget")
+    return int(v.value)
+
+
 def pgb_blocks_resident_bytes(b: Blocks, per_vertex: bool = True) -> int:
     """Device bytes a streamed run holds besides its two slots."""
     v = ctypes.c_uint64()
@@ -438,10 +455,14 @@ def pgb_blocks_resident_bytes(b: Blocks, per_vertex: bool = True) -> int:
     return int(v.value)
 
 
-def pgb_tc_result_stream(r: Result) -> tuple[int, int]:
-    """(bytes copied host to device, chunks) of a streamed run; (0, 0) otherwise."""
-    nb, nc = ctypes.c_uint64(), ctypes.c_uint32()
-    _check(load().pgb_tc_result_stream(r, ctypes.byref(nb), ctypes.byref(nc)), "pgb_tc_result_stream")
+def pgb_tc_result_stream(r: Result, slice_loads: bool = False):
+    """(bytes copied host to device, chunks) of a streamed run, plus the column
+    slices copied in when ``slice_loads``; zeros for a resident run."""
+    nb, nc, nl = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load().pgb_tc_result_stream(r, ctypes.byref(nb), ctypes.byref(nc), ctypes.byref(nl)),
+           "pgb_tc_result_stream")
+    if slice_loads:
+        return int(nb.value), int(nc.value), int(nl.value)
     return int(nb.value), int(nc.value)
 
 
