@@ -374,67 +374,95 @@ def tiers_bench(args):
 
 
 def stream_bench(args):
-    """The streaming tier: count with the in-edge index in pinned host memory
-    and a device budget, against the same graph fully resident."""
+    """The streaming tiers against the same graph fully resident: the in-edge
+    index in pinned host memory (budget --stream-budget-gb), and the block
+    cache with the columns offloaded too (budget --cache-budget-gb)."""
     import torch
     from paper_2209_04541_b300 import pgabb as P
     w = dict(WORKLOADS[args.stream_workload])
     mraw = raw_edge_count(w)
-    hs = torch.empty(mraw, dtype=torch.uint32, pin_memory=True)
-    hd = torch.empty(mraw, dtype=torch.uint32, pin_memory=True)
-    _, _, n = generate(w, out=(hs.numpy(), hd.numpy()))
-    stream = torch.cuda.current_stream()
-    t0 = time.perf_counter()
-    g = P.pgb_graph_from_edges(hs.cuda(), hd.cuda(), n, stream)
-    del hs, hd
-    b = P.pgb_partition(g, w["p"], P.PGB_CUT_NNZ, stream)
-    g.free()
-    torch.cuda.synchronize()
-    prep_s = time.perf_counter() - t0
-    torch.cuda.empty_cache()
-    info = P.pgb_blocks_info(b)
-    m = info["m"]
-    budget = int(args.stream_budget_gb * (1 << 30))
 
-    def timed(opts, reps):
+    def build():
+        hs = torch.empty(mraw, dtype=torch.uint32, pin_memory=True)
+        hd = torch.empty(mraw, dtype=torch.uint32, pin_memory=True)
+        _, _, n = generate(w, out=(hs.numpy(), hd.numpy()))
+        stream = torch.cuda.current_stream()
+        t0 = time.perf_counter()
+        g = P.pgb_graph_from_edges(hs.cuda(), hd.cuda(), n, stream)
+        del hs, hd
+        b = P.pgb_partition(g, w["p"], P.PGB_CUT_NNZ, stream)
+        g.free()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        return b, n, time.perf_counter() - t0
+
+    def timed(b, opts, reps):
         out = []
         for _ in range(reps):
             torch.cuda.synchronize()
             t = time.perf_counter()
-            r = P.pgb_tc_run(b, opts, stream)
+            r = P.pgb_tc_run(b, opts)
             T, tv = P.pgb_tc_result_get(r, per_vertex=True)
             wall = time.perf_counter() - t
-            out.append((T, tv, wall, P.pgb_tc_result_kernel_ms(r), P.pgb_tc_result_stream(r)))
+            out.append((T, tv, wall, P.pgb_tc_result_kernel_ms(r), P.pgb_tc_result_stream(r, slice_loads=True)))
             r.free()
         return out
 
     reps = max(3, args.stream_steps)
-    res = timed(P.pgb_tc_opts_default(), 1 + reps)[1:]
+    b, n, prep_s = build()
+    info = P.pgb_blocks_info(b)
+    m = info["m"]
+    res = timed(b, P.pgb_tc_opts_default(), 1 + reps)[1:]
     T, tv_res = res[0][0], res[0][1]
-    res_ms = statistics.median(x[3] for x in res)
-    res_wall = statistics.median(x[2] for x in res)
-    P.pgb_blocks_offload(b, stream)
-    floor = P.pgb_blocks_resident_bytes(b, True)
-    st = timed(P.pgb_tc_opts_default(device_budget=budget), 1 + reps)[1:]
-    for x in st:
-        assert x[0] == T and np.array_equal(x[1], tv_res), "streamed counts differ from resident counts"
     assert int(tv_res.sum(dtype=np.uint64)) == 3 * T
-    st_ms = statistics.median(x[3] for x in st)
-    st_wall = statistics.median(x[2] for x in st)
-    nbytes, chunks = st[0][4]
     link = h2d_gbs(torch)
+
+    def summary(runs, budget, floor):
+        for x in runs:
+            assert x[0] == T and np.array_equal(x[1], tv_res), "streamed counts differ from resident counts"
+        kms = statistics.median(x[3] for x in runs)
+        wall = statistics.median(x[2] for x in runs)
+        nbytes, chunks, loads = runs[0][4]
+        return {"device_budget_bytes": budget, "resident_floor_bytes": floor, "chunks": chunks,
+                "slice_loads": loads, "streamed_bytes": nbytes, "value": m / wall, "unit": "edges/s",
+                "wall_ms": 1e3 * wall, "kernel_ms": kms, "link_gbs": nbytes / (kms / 1e3) / 1e9,
+                "link_frac": nbytes / (kms / 1e3) / 1e9 / link}
+
+    out = {"metric": "streamed TC edges/s", "workload": w["desc"], "n": n, "unique_edges": m, "triangles": T,
+           "resident_graph_bytes": 4 * m + 12 * m + 4 * m + 12 * (n + 1), "steps": reps, "preprocess_s": prep_s,
+           "h2d_peak_gbs": link,
+           "resident": {"value": m / statistics.median(x[2] for x in res), "unit": "edges/s",
+                        "wall_ms": 1e3 * statistics.median(x[2] for x in res),
+                        "kernel_ms": statistics.median(x[3] for x in res)},
+           "check": "streamed totals and per-vertex counts equal the resident run's; sum t = 3T"}
+    # tier 1: the in-edge index streamed, columns resident
+    budget = int(args.stream_budget_gb * (1 << 30))
+    P.pgb_blocks_offload(b)
+    out["index"] = summary(timed(b, P.pgb_tc_opts_default(device_budget=budget), 1 + reps)[1:], budget,
+                           P.pgb_blocks_resident_bytes(b, True))
     b.free()
-    return {"metric": "streamed TC edges/s (in-edge index from pinned host memory)",
-            "workload": w["desc"], "n": n, "unique_edges": m, "triangles": T,
-            "device_budget_bytes": budget, "resident_floor_bytes": floor,
-            "resident_graph_bytes": 4 * m + 12 * m + 4 * m + 12 * (n + 1),
-            "chunks": chunks, "streamed_bytes": nbytes, "steps": reps,
-            "streamed": {"value": m / (st_wall), "unit": "edges/s", "wall_ms": 1e3 * st_wall, "kernel_ms": st_ms,
-                         "link_gbs": nbytes / (st_ms / 1e3) / 1e9},
-            "resident": {"value": m / res_wall, "unit": "edges/s", "wall_ms": 1e3 * res_wall, "kernel_ms": res_ms},
-            "h2d_peak_gbs": link, "link_frac": nbytes / (st_ms / 1e3) / 1e9 / link,
-            "preprocess_s": prep_s,
-            "check": "streamed total and per-vertex counts equal the resident run's; sum t = 3T"}
+    torch.cuda.empty_cache()
+    # tier 2: the block cache (columns offloaded too), from a fresh partition
+    if args.cache_budget_gb > 0:
+        b, _, _ = build()
+        t0 = time.perf_counter()
+        P.pgb_blocks_offload_columns(b)
+        off_s = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+        budget = int(args.cache_budget_gb * (1 << 30))
+        two = P.pgb_blocks_cache_budget(b, 2)
+        if budget < two:
+            out["cache"] = {"error": f"budget below two slices ({two} bytes)"}
+        else:
+            c = summary(timed(b, P.pgb_tc_opts_default(device_budget=budget), 1 + reps)[1:], budget,
+                        P.pgb_blocks_resident_bytes(b, True))
+            c["offload_s"] = off_s
+            c["slices_in_cache"] = sum(1 for k in range(1, info["p"] + 1)
+                                       if P.pgb_blocks_cache_budget(b, k) <= budget)
+            out["cache"] = c
+        b.free()
+        torch.cuda.empty_cache()
+    return out
 
 
 def main(argv=None):
@@ -462,6 +490,8 @@ def main(argv=None):
     ap.add_argument("--stream-workload", choices=["rmat24", "rmat22", "rmat27"], default="rmat24")
     ap.add_argument("--stream-budget-gb", type=float, default=2.0)
     ap.add_argument("--stream-steps", type=int, default=3)
+    ap.add_argument("--cache-budget-gb", type=float, default=1.0,
+                    help="block cache tier budget (0 = skip the tier)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

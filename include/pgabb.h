@@ -271,7 +271,11 @@ typedef struct {
     uint32_t chunk_edges;  /* PERSISTENT: binary-search variant: edges per
                               dequeued chunk; hash variant: in-edges per work
                               item (0 = default) */
-    uint32_t reserved[7];
+    uint32_t hash_threads; /* hash variant: threads per CTA, 128 (8 CTAs per
+                              SM, bitmaps over up to 131,072 ranks) or 256 (4
+                              per SM, 262,144 ranks); 0 = autotuned: 256 for
+                              graphs of at least 2^26 vertices */
+    uint32_t reserved[6];
 } pgb_tc_opts;
 
 void pgb_tc_opts_default(pgb_tc_opts* o);

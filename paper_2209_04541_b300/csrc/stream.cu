@@ -56,7 +56,8 @@ struct StreamPlan {
     uint32_t in_chunk = 0;
     uint64_t budget = 0;
     bool pv = false;
-    int grid = 0;
+    uint32_t threads_opt = 0;
+    int grid = 0, threads = 128;
     std::vector<Chunk> chunks;
     VItem* h_items = nullptr;  // pinned, in-edge ranges relative to their chunk's base
     uint32_t nitems = 0, max_items = 0;
@@ -66,13 +67,15 @@ struct StreamPlan {
     }
 };
 
-static std::shared_ptr<StreamPlan> make_plan(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint64_t budget,
-                                             cudaStream_t s) {
+static std::shared_ptr<StreamPlan> make_plan(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint32_t threads,
+                                             uint64_t budget, cudaStream_t s) {
     auto P = std::make_shared<StreamPlan>();
     P->in_chunk = in_chunk;
     P->budget = budget;
     P->pv = pv;
-    P->grid = hash_grid(pv);
+    P->threads_opt = threads;
+    P->threads = threads ? (int)threads : hash_threads(b->n);
+    P->grid = hash_grid(pv, P->threads);
     // the budget covers everything the run holds on the device: the resident
     // arrays, the per-vertex counters, the per-launch partials (bounded by
     // kPartialsReserve) and the two stream slots
@@ -86,7 +89,7 @@ static std::shared_ptr<StreamPlan> make_plan(const pgb_blocks* b, uint32_t in_ch
     }
     const uint64_t cap = slot_bytes / (kStreamBytesPerInEdge + sizeof(VItem));  // in-edges per slot
     DevBuf<VItem> ditems;
-    const uint32_t nitems = build_hash_items(b, in_chunk, s, ditems);
+    const uint32_t nitems = build_hash_items(b, in_chunk, P->threads, s, ditems);
     P->nitems = nitems;
     if (nitems == 0) return P;
     std::vector<VItem> items(nitems);
@@ -135,24 +138,25 @@ static std::shared_ptr<StreamPlan> make_plan(const pgb_blocks* b, uint32_t in_ch
     return P;
 }
 
-static std::shared_ptr<StreamPlan> get_plan(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint64_t budget,
-                                            cudaStream_t s) {
+static std::shared_ptr<StreamPlan> get_plan(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint32_t threads,
+                                            uint64_t budget, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(b->plan_mu);
     auto P = std::static_pointer_cast<StreamPlan>(b->stream_plan);
-    if (!P || P->in_chunk != in_chunk || P->budget != budget || P->pv != pv) {
-        P = make_plan(b, in_chunk, pv, budget, s);
+    if (!P || P->in_chunk != in_chunk || P->budget != budget || P->pv != pv || P->threads_opt != threads) {
+        P = make_plan(b, in_chunk, pv, threads, budget, s);
         b->stream_plan = P;
     }
     return P;
 }
 
-void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, unsigned long long* tv, uint64_t budget,
+void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint32_t threads, unsigned long long* tv,
+                   uint64_t budget,
                    cudaStream_t s, DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
                    cudaEvent_t ev1, uint64_t* streamed, uint32_t* nchunks_out) {
     npartials = 0;
     *streamed = 0;
     *nchunks_out = 0;
-    const std::shared_ptr<StreamPlan> P = get_plan(b, in_chunk, pv, budget, s);
+    const std::shared_ptr<StreamPlan> P = get_plan(b, in_chunk, pv, threads, budget, s);
     if (P->nitems == 0) {
         PGB_CUDA(cudaEventRecord(ev0, s));
         PGB_CUDA(cudaEventRecord(ev1, s));
@@ -219,7 +223,8 @@ void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, unsigned lon
             PGB_CUDA(cudaEventRecord(ready[k], cs));
             bytes += (uint64_t)ch.span * kStreamBytesPerInEdge + (uint64_t)ch.count * sizeof(VItem);
             PGB_CUDA(cudaStreamWaitEvent(ks[k], ready[k], 0));
-            launch_hash(hg[k], sitems[k].ptr, ch.count, pv, ks[k], cursor.ptr + k, partials.ptr + c * grid, grid);
+            launch_hash(hg[k], sitems[k].ptr, ch.count, pv, ks[k], cursor.ptr + k, partials.ptr + c * grid, grid,
+                        P->threads);
             PGB_CUDA(cudaEventRecord(freed[k], ks[k]));
         }
         PGB_CUDA(cudaEventRecord(done1, s1));
@@ -466,7 +471,8 @@ static std::shared_ptr<ColPlan> build_col_plan(pgb_blocks* b, cudaStream_t s) {
         if (lc.count < len) lc.alloc(len, s);
         k_local_colptr<<<(len + 255) / 256, 256, 0, s>>>(bh.ptr, e0, e1, w0, len, lc.ptr);
         PGB_CHECK_LAUNCH("k_local_colptr");
-        const ItemSpace sp{b->rowptr.ptr, lc.ptr, b->col.ptr, w0, 0, w0, nwin, n};
+        // items that fit either CTA shape: the smaller table capacity
+        const ItemSpace sp{b->rowptr.ptr, lc.ptr, b->col.ptr, w0, 0, w0, nwin, n, 1024};
         DevBuf<VItem> its;
         const uint32_t ni = build_hash_items_in(sp, 0, s, its);
         ColPiece pc{pairs[k].first, pairs[k].second, e0, e1, all.size(), all.size() + ni};
@@ -508,10 +514,10 @@ __global__ void k_add_partials(const unsigned long long* __restrict__ partials, 
 // (in-edges, items), the launch grid, and the bytes held besides the slices.
 struct ColSizes {
     uint64_t max_slice = 0, max_edges = 0, max_items = 0, fixed = 0;
-    int grid = 0;
+    int grid = 0, threads = 128;
 };
 
-static ColSizes col_sizes(const pgb_blocks* b, bool pv) {
+static ColSizes col_sizes(const pgb_blocks* b, bool pv, uint32_t threads) {
     const ColPlan& P = *std::static_pointer_cast<ColPlan>(b->col_plan);
     ColSizes z;
     for (uint32_t i = 0; i < b->p; ++i) z.max_slice = std::max<uint64_t>(z.max_slice, P.slice_len[i]);
@@ -519,14 +525,16 @@ static ColSizes col_sizes(const pgb_blocks* b, bool pv) {
         z.max_edges = std::max(z.max_edges, c.e1 - c.e0);
         z.max_items = std::max(z.max_items, c.it1 - c.it0);
     }
-    z.grid = hash_grid(pv);
+    z.threads = threads ? (int)threads : hash_threads(b->n);
+    z.grid = hash_grid(pv, z.threads);
     z.fixed = col_resident_bytes(b, pv) + 2 * (std::max<uint64_t>(z.max_edges, 1) * 12 +
                                                std::max<uint64_t>(z.max_items, 1) * sizeof(VItem)) +
               2ull * z.grid * 8 + 16;
     return z;
 }
 
-void run_column_streaming(const pgb_blocks* b, bool pv, unsigned long long* tv, uint64_t budget, cudaStream_t s,
+void run_column_streaming(const pgb_blocks* b, bool pv, uint32_t threads, unsigned long long* tv, uint64_t budget,
+                          cudaStream_t s,
                           DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
                           cudaEvent_t ev1, uint64_t* streamed, uint32_t* npieces_out, uint32_t* loads_out) {
     const ColPlan& P = *std::static_pointer_cast<ColPlan>(b->col_plan);
@@ -542,7 +550,7 @@ void run_column_streaming(const pgb_blocks* b, bool pv, unsigned long long* tv, 
         PGB_CUDA(cudaEventRecord(ev1, s));
         return;
     }
-    const ColSizes z = col_sizes(b, pv);
+    const ColSizes z = col_sizes(b, pv, threads);
     const uint64_t max_slice = z.max_slice, max_edges = z.max_edges, max_items = z.max_items;
     const int grid = z.grid;
     uint32_t C = p;  // slices the cache holds
@@ -682,7 +690,8 @@ void run_column_streaming(const pgb_blocks* b, bool pv, unsigned long long* tv, 
             Gr.colu = slot[si].ptr;
             Gr.ubase = P.slice_lo[c.i];
             if (ni) {
-                launch_hash(Gr, pit[k].ptr, (uint32_t)ni, pv, ss, cursor.ptr + k, part.ptr + (size_t)k * grid, grid);
+                launch_hash(Gr, pit[k].ptr, (uint32_t)ni, pv, ss, cursor.ptr + k, part.ptr + (size_t)k * grid, grid,
+                            z.threads);
                 k_add_partials<<<1, 256, 0, ss>>>(part.ptr + (size_t)k * grid, (uint32_t)grid, partials.ptr + k);
                 PGB_CHECK_LAUNCH("k_add_partials");
             }
@@ -725,7 +734,7 @@ int pgb_blocks_cache_budget(const pgb_blocks* b, int per_vertex, uint32_t slices
     return guard([&] {
         if (!b || !budget) fail(PGB_E_INVAL, "NULL argument");
         if (!b->cols_offloaded) fail(PGB_E_STATE, "the columns are not offloaded");
-        const ColSizes z = col_sizes(b, per_vertex != 0);
+        const ColSizes z = col_sizes(b, per_vertex != 0, 0);
         *budget = z.fixed + (uint64_t)std::min(slices, b->p) * z.max_slice * 4;
     });
 }

@@ -392,7 +392,7 @@ struct RunPlan {
     // settings the plan was made for
     int mode = 0, variant = 0, order = 0;
     bool per_vertex = false, per_triple = false;
-    uint32_t chunk_edges = 0;
+    uint32_t chunk_edges = 0, hash_threads_opt = 0;
     uint32_t n = 0;
     DevBuf<unsigned long long> tv, partials, total, tv_orig, triple_counts;
     uint64_t npartials = 0;
@@ -411,7 +411,7 @@ struct RunPlan {
     uint32_t nitems = 0;
     HashGraph H{};
     DevBuf<unsigned int> cursor;
-    int grid = 0;
+    int grid = 0, threads = 128;
     const uint32_t* perm = nullptr;
     // graph replay
     cudaGraphExec_t exec = nullptr;
@@ -421,7 +421,8 @@ struct RunPlan {
 
     bool same(const pgb_tc_opts& o, int var) const {
         return mode == o.mode && variant == var && order == o.order && per_vertex == (o.per_vertex != 0) &&
-               per_triple == (o.mode == PGB_MODE_PLAIN && o.per_triple != 0) && chunk_edges == o.chunk_edges;
+               per_triple == (o.mode == PGB_MODE_PLAIN && o.per_triple != 0) && chunk_edges == o.chunk_edges &&
+               hash_threads_opt == o.hash_threads;
     }
     ~RunPlan() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -437,6 +438,7 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
     P->per_vertex = o.per_vertex != 0;
     P->per_triple = o.mode == PGB_MODE_PLAIN && o.per_triple != 0;
     P->chunk_edges = o.chunk_edges;
+    P->hash_threads_opt = o.hash_threads;
     const uint32_t n = P->n = b->n;
     P->perm = b->perm.ptr;
     P->total.alloc(1, s);
@@ -472,11 +474,12 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
         }
     } else if (variant == PGB_VAR_HASH) {
         // middle-vertex hash variant (tc_hash.cu)
-        P->nitems = build_hash_items(b, o.chunk_edges, s, P->items);
+        P->threads = o.hash_threads ? (int)o.hash_threads : hash_threads(b->n);
+        P->nitems = build_hash_items(b, o.chunk_edges, P->threads, s, P->items);
         if (P->nitems) {
             P->H = resident_hash_graph(b, P->tv.ptr);
             P->cursor.alloc(1, s);
-            P->grid = hash_grid(P->per_vertex);
+            P->grid = hash_grid(P->per_vertex, P->threads);
             P->npartials = (uint64_t)P->grid;
             P->partials.alloc(P->npartials, s);
         }
@@ -542,7 +545,8 @@ static void enqueue(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cudaEvent
         PGB_CHECK_LAUNCHES("k_tc_tuple", T);
     } else if (P.variant == PGB_VAR_HASH) {
         if (P.nitems)
-            launch_hash(P.H, P.items.ptr, P.nitems, P.per_vertex, s, P.cursor.ptr, P.partials.ptr, P.grid);
+            launch_hash(P.H, P.items.ptr, P.nitems, P.per_vertex, s, P.cursor.ptr, P.partials.ptr, P.grid,
+                        P.threads);
     } else {
         PGB_CUDA(cudaMemsetAsync(P.cursor.ptr, 0, 4, s));
         if (P.per_vertex)
@@ -616,11 +620,11 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
             if (n) PGB_CUDA(cudaMemsetAsync(tv.ptr, 0, (size_t)n * 8, s));
         }
         if (b->cols_offloaded)
-            run_column_streaming(b, r->per_vertex, tv.ptr, o.device_budget, s, partials, npartials, r->ev0, r->ev1,
-                                 &r->streamed, &r->chunks, &r->slice_loads);
+            run_column_streaming(b, r->per_vertex, o.hash_threads, tv.ptr, o.device_budget, s, partials, npartials,
+                                 r->ev0, r->ev1, &r->streamed, &r->chunks, &r->slice_loads);
         else
-            run_streaming(b, o.chunk_edges, r->per_vertex, tv.ptr, o.device_budget, s, partials, npartials, r->ev0,
-                          r->ev1, &r->streamed, &r->chunks);
+            run_streaming(b, o.chunk_edges, r->per_vertex, o.hash_threads, tv.ptr, o.device_budget, s, partials,
+                          npartials, r->ev0, r->ev1, &r->streamed, &r->chunks);
         if (npartials)
             k_reduce_sum<<<1, 1024, 0, s>>>(partials.ptr, npartials, r->total.ptr);
         else
@@ -707,6 +711,8 @@ int pgb_tc_run(const pgb_blocks* b, const pgb_tc_opts* opts, void* stream, pgb_t
         if (o.mode == PGB_MODE_PLAIN && o.variant == PGB_VAR_HASH)
             fail(PGB_E_INVAL, "PLAIN mode runs the edge-wise variants (binary search, merge) only");
         if (o.order != PGB_ORDER_WEIGHT && o.order != PGB_ORDER_LOCALITY) fail(PGB_E_INVAL, "bad order");
+        if (o.hash_threads != 0 && o.hash_threads != 128 && o.hash_threads != 256)
+            fail(PGB_E_INVAL, "hash_threads must be 0, 128 or 256");
         if (b->offloaded && (o.mode != PGB_MODE_PERSISTENT || o.variant == PGB_VAR_BSEARCH ||
                              o.variant == PGB_VAR_MERGE))
             fail(PGB_E_STATE, "offloaded blocks run in PERSISTENT mode with the hash variant only");

@@ -34,18 +34,18 @@ namespace pgb {
 
 namespace {
 
-constexpr int kHThreads = 128;
-constexpr int kHWarps = kHThreads / 32;
-constexpr uint32_t kKeyCap = 1024;     // table keys per item (load factor <= 1/2)
 constexpr uint32_t kInChunkDefault = 4096;  // in-edges per item unless the caller sets one
-constexpr int kMaxSlotsLog2 = 11;      // 2048 slots
-constexpr uint32_t kMaxSlots = 1u << kMaxSlotsLog2;
 constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr unsigned kFullMask = 0xffffffffu;
+// Table keys per work item of a CTA shape (tables stay at most half full).
+constexpr uint32_t key_capacity(int threads) { return 32u * threads / 4; }
+
+// Graphs with at least this many vertices run the 256-thread shape: its
+// wider bitmaps serve more of the top-ranked middle vertices (measured on
+// R-MAT: scale 27 runs 13% faster with it, scale 22 26% slower).
+constexpr uint32_t kWideShapeVertices = 1u << 26;
 constexpr int kUnrollPV = 4;           // 16-byte quad loads per lane issued together (per-vertex run)
 constexpr int kUnrollGlobal = 4;       // the same for a global-count run
-constexpr uint32_t kRegionA = 2 * kMaxSlots;        // words: hash keys + masks, or a bitmap
-constexpr uint32_t kBitmapBits = 32 * kRegionA;    // widest third-vertex range held as a bitmap
 
 __device__ __forceinline__ uint32_t hslot(uint32_t x, uint32_t log2s) { return (x * 0x9E3779B1u) >> (32 - log2s); }
 
@@ -131,8 +131,8 @@ __device__ __forceinline__ WindowInfo window_info(const ItemSpace& sp, uint32_t 
     W.act = W.dp > 0 && W.dm > 0;
     W.keys = warp_sum(W.act ? W.dp : 0);
     W.ins = warp_sum(W.act ? W.dm : 0);
-    W.group = W.keys > 0 && W.keys <= kKeyCap && W.ins <= in_chunk;
-    W.mine = (W.act && !W.group) ? ((W.dm + in_chunk - 1) / in_chunk) * ((W.dp + kKeyCap - 1) / kKeyCap) : 0;
+    W.group = W.keys > 0 && W.keys <= sp.keycap && W.ins <= in_chunk;
+    W.mine = (W.act && !W.group) ? ((W.dm + in_chunk - 1) / in_chunk) * ((W.dp + sp.keycap - 1) / sp.keycap) : 0;
     return W;
 }
 
@@ -182,7 +182,8 @@ __global__ void k_items_emit(const ItemSpace sp, uint32_t in_chunk, const uint32
         excl -= W.mine;
         if (!W.mine) continue;
         const uint32_t na = (W.dm + in_chunk - 1) / in_chunk;
-        const uint32_t nk = (W.dp + kKeyCap - 1) / kKeyCap;
+        const uint32_t kc = sp.keycap;
+        const uint32_t nk = (W.dp + kc - 1) / kc;
         const uint32_t rb = sp.rowptr[W.v], cb = sp.colptr[W.v - sp.cbase];
         uint32_t out = base + excl;
         for (uint32_t a = 0; a < na; ++a) {
@@ -193,15 +194,15 @@ __global__ void k_items_emit(const ItemSpace sp, uint32_t in_chunk, const uint32
                 it.in_begin = cb + a * in_chunk;
                 it.in_end = min(it.in_begin + in_chunk, cb + W.dm);
                 if (nk > 1) {
-                    it.lo = sp.col[rb + kk * kKeyCap - sp.vbase];
-                    it.hi = (kk + 1 < nk) ? sp.col[rb + (kk + 1) * kKeyCap - sp.vbase] : n;
+                    it.lo = sp.col[rb + kk * kc - sp.vbase];
+                    it.hi = (kk + 1 < nk) ? sp.col[rb + (kk + 1) * kc - sp.vbase] : n;
                     it.clip = 1;
                 } else {
                     it.lo = 0;
                     it.hi = n;
                     it.clip = 0;
                 }
-                it.slots_log2 = (uint16_t)slots_for(min(kKeyCap, W.dp - kk * kKeyCap));
+                it.slots_log2 = (uint16_t)slots_for(min(kc, W.dp - kk * kc));
                 it.mask = 1u;
                 items[out++] = it;
             }
@@ -209,8 +210,13 @@ __global__ void k_items_emit(const ItemSpace sp, uint32_t in_chunk, const uint32
     }
 }
 
-template <bool PV>
-__global__ void __launch_bounds__(kHThreads, 8)
+// Two CTA shapes: T = 128 threads (8 CTAs per SM, a 16 KB region A: bitmaps
+// over up to 131,072 ranks) and T = 256 (4 CTAs per SM, 32 KB: 262,144
+// ranks).  Region A holds the bitmap or the table keys and masks (half of it
+// each: up to 2,048 or 4,096 slots, so 1,024 or 2,048 keys per item); thread
+// t owns words [32t, 32t + 32) of it in the bitmap prefix scan.
+template <bool PV, int T>
+__global__ void __launch_bounds__(T, 1024 / T)
     k_tc_hash(const HashGraph G, const VItem* __restrict__ items,
               uint32_t nitems, unsigned int* __restrict__ cursor, unsigned long long* __restrict__ partials) {
     extern __shared__ uint32_t hsm[];
@@ -220,28 +226,42 @@ __global__ void __launch_bounds__(kHThreads, 8)
     // 16-bit running popcount per pair of bitmap words, then one counter per key,
     // indexed by the key's rank in v's sorted list.
     uint32_t* regA = hsm;
+    constexpr int kHThreads = T, kHWarps = T / 32;
+    constexpr uint32_t kRegionA = 32u * T;           // words
+    constexpr uint32_t kBitmapBits = 32u * kRegionA;  // widest third-vertex range held as a bitmap
+    constexpr uint32_t kMaxSlots = kRegionA / 2;     // table slots (keys, then member masks)
     uint32_t* regB = hsm + kRegionA;
     __shared__ uint32_t s_wsum[kHWarps];
     __shared__ VItem s_it, s_itn;      // current item and the next one (prefetched)
     __shared__ unsigned long long s_cnt;
-    __shared__ uint32_t s_item, s_itemn, s_vmask, s_next;
+    __shared__ uint32_t s_item, s_itemn, s_vmask, s_next, s_rb, s_re, s_rbn, s_ren;
     __shared__ uint32_t s_edge[kHWarps][32];
     __shared__ uint32_t s_vcnt[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (uint32_t i = tid; i < kRegionA; i += kHThreads) regA[i] = 0;
     if (tid == 0) s_cnt = 0;
     if (PV) s_edge[warp][lane] = 0;
-    // thread 0 fetches the next item (index, descriptor, graph) ahead into
-    // the second shared slot
-    if (tid == 0) {
+    // thread 0 fetches the next item, and a singleton's row bounds, ahead
+    // into the second shared slot
+    auto prefetch = [&] {
         s_itemn = atomicAdd(cursor, 1u);
-        if (s_itemn < nitems) s_itn = items[s_itemn];
-    }
+        if (s_itemn < nitems) {
+            const VItem nx = items[s_itemn];
+            s_itn = nx;
+            if (nx.nv == 1) {
+                s_rbn = __ldg(G.rowptr + nx.v0);
+                s_ren = __ldg(G.rowptr + nx.v0 + 1);
+            }
+        }
+    };
+    if (tid == 0) prefetch();
     unsigned long long cnt = 0;
     for (;;) {
         if (tid == 0) {
             s_item = s_itemn;
             s_it = s_itn;
+            s_rb = s_rbn;
+            s_re = s_ren;
             s_vmask = 0;
             s_next = 0;
         }
@@ -255,6 +275,16 @@ __global__ void __launch_bounds__(kHThreads, 8)
         const uint32_t rlo = I.clip ? I.lo : (single ? I.v0 + 1 : 0);
         const uint32_t rhi = I.clip ? I.hi : G.n;
         const bool bitmap = single && rhi - rlo <= kBitmapBits;
+        // a singleton's (clipped) list; its row bounds came with the item
+        uint32_t rb = 0, re = 0;
+        if (single) {
+            rb = s_rb;
+            re = s_re;
+            if (I.clip) {
+                rb = hlower_bound_b(G.col, G.vbase, rb, re, I.lo);
+                re = hlower_bound_b(G.col, G.vbase, rb, re, I.hi);
+            }
+        }
         const uint32_t L = I.slots_log2, S = 1u << L;
         uint32_t* keys = regA;
         uint32_t* masks = regA + kMaxSlots;
@@ -263,21 +293,14 @@ __global__ void __launch_bounds__(kHThreads, 8)
         if (!bitmap)
             for (uint32_t i = tid; i < S; i += kHThreads) keys[i] = kEmpty;
         if (PV) {
-            const uint32_t nc = bitmap ? kKeyCap : S;
+            const uint32_t nc = bitmap ? re - rb : S;
             for (uint32_t i = tid; i < nc; i += kHThreads) cnts[i] = 0;
         }
         __syncthreads();
         // build: a singleton's list is inserted by the whole CTA (bitmap bits,
         // plus table keys for per-vertex counts); a group's members are
         // spread over the warps (member t to warp t mod kHWarps)
-        uint32_t rb = 0, re = 0;
         if (single) {
-            rb = __ldg(G.rowptr + I.v0);
-            re = __ldg(G.rowptr + I.v0 + 1);
-            if (I.clip) {
-                rb = hlower_bound_b(G.col, G.vbase, rb, re, I.lo);
-                re = hlower_bound_b(G.col, G.vbase, rb, re, I.hi);
-            }
             if (tid == 0 && rb < re) s_vmask = 1u;
             for (uint32_t q = rb + tid; q < re; q += kHThreads) {
                 const uint32_t x = __ldg(G.col + (q - G.vbase));
@@ -322,10 +345,7 @@ __global__ void __launch_bounds__(kHThreads, 8)
             }
             __syncthreads();
         }
-        if (tid == 0) {
-            s_itemn = atomicAdd(cursor, 1u);
-            if (s_itemn < nitems) s_itn = items[s_itemn];
-        }
+        if (tid == 0) prefetch();
         const uint32_t vmask = s_vmask;
         // probe: warps take batches of 32 in-edges from a shared counter (so a
         // warp with short lists takes more batches)
@@ -404,6 +424,7 @@ __global__ void __launch_bounds__(kHThreads, 8)
                         bool hit;
                         uint32_t h = 0;
                         if (bitmap) {
+                            // entries outside the list's span cannot match
                             const uint32_t d = x - rlo;
                             const uint32_t word = regA[d >> 5];
                             hit = (word >> (d & 31)) & 1u;
@@ -484,11 +505,29 @@ __global__ void __launch_bounds__(kHThreads, 8)
     if (tid == 0) partials[blockIdx.x] = s_cnt;
 }
 
-template <bool PV>
+template <bool PV, int T>
 size_t hash_smem() {
     // region B: max(slot counters, 16-bit word prefix + per-key counters)
+    constexpr uint32_t kRegionA = 32u * T, kMaxSlots = kRegionA / 2, kKeyCap = kMaxSlots / 2;
     constexpr uint32_t kRegionB = (kRegionA / 4 + kKeyCap) > kMaxSlots ? (kRegionA / 4 + kKeyCap) : kMaxSlots;
     return (size_t)(kRegionA + (PV ? kRegionB : 0)) * sizeof(uint32_t);
+}
+
+template <bool PV, int T>
+int grid_of() {
+    int dev = 0, sms = 0, per_sm = 0;
+    PGB_CUDA(cudaGetDevice(&dev));
+    PGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smem = hash_smem<PV, T>();
+    PGB_CUDA(cudaFuncSetAttribute(k_tc_hash<PV, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_hash<PV, T>, T, smem));
+    return std::max(1, per_sm) * sms;
+}
+
+template <bool PV, int T>
+void launch_shape(const HashGraph& G, const VItem* items, uint32_t nitems, cudaStream_t s, unsigned int* cursor,
+                  unsigned long long* partials, int grid) {
+    k_tc_hash<PV, T><<<grid, T, hash_smem<PV, T>(), s>>>(G, items, nitems, cursor, partials);
 }
 
 }  // namespace
@@ -521,12 +560,14 @@ uint32_t build_hash_items_in(const ItemSpace& sp, uint32_t in_chunk, cudaStream_
     return nitems;
 }
 
-uint32_t build_hash_items(const pgb_blocks* b, uint32_t in_chunk, cudaStream_t s, DevBuf<VItem>& items) {
+uint32_t build_hash_items(const pgb_blocks* b, uint32_t in_chunk, int threads, cudaStream_t s,
+                          DevBuf<VItem>& items) {
     if (b->m == 0) {
         items.alloc(1, s);
         return 0;
     }
-    const ItemSpace sp{b->rowptr.ptr, b->colptr.ptr, b->col.ptr, 0, 0, 0, (b->n + 31) / 32, b->n};
+    const ItemSpace sp{b->rowptr.ptr, b->colptr.ptr, b->col.ptr, 0, 0, 0, (b->n + 31) / 32, b->n,
+                       key_capacity(threads)};
     return build_hash_items_in(sp, in_chunk, s, items);
 }
 
@@ -536,29 +577,23 @@ HashGraph resident_hash_graph(const pgb_blocks* b, unsigned long long* tv) {
     return G;
 }
 
-int hash_grid(bool pv) {
-    int dev = 0, sms = 0, per_sm = 0;
-    PGB_CUDA(cudaGetDevice(&dev));
-    PGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const size_t smem = pv ? hash_smem<true>() : hash_smem<false>();
-    if (pv) {
-        PGB_CUDA(cudaFuncSetAttribute(k_tc_hash<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        PGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_hash<true>, kHThreads, smem));
-    } else {
-        PGB_CUDA(cudaFuncSetAttribute(k_tc_hash<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        PGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_hash<false>, kHThreads, smem));
-    }
-    return std::max(1, per_sm) * sms;
+int hash_threads(uint32_t n) { return n >= kWideShapeVertices ? 256 : 128; }
+
+int hash_grid(bool pv, int threads) {
+    if (threads == 256) return pv ? grid_of<true, 256>() : grid_of<false, 256>();
+    return pv ? grid_of<true, 128>() : grid_of<false, 128>();
 }
 
-void launch_hash(const HashGraph& G, const VItem* items, uint32_t nitems, bool pv,
-                 cudaStream_t s, unsigned int* cursor, unsigned long long* partials, int grid) {
-    const size_t smem = pv ? hash_smem<true>() : hash_smem<false>();
+void launch_hash(const HashGraph& G, const VItem* items, uint32_t nitems, bool pv, cudaStream_t s,
+                 unsigned int* cursor, unsigned long long* partials, int grid, int threads) {
     PGB_CUDA(cudaMemsetAsync(cursor, 0, 4, s));
-    if (pv)
-        k_tc_hash<true><<<grid, kHThreads, smem, s>>>(G, items, nitems, cursor, partials);
-    else
-        k_tc_hash<false><<<grid, kHThreads, smem, s>>>(G, items, nitems, cursor, partials);
+    if (threads == 256) {
+        if (pv) launch_shape<true, 256>(G, items, nitems, s, cursor, partials, grid);
+        else launch_shape<false, 256>(G, items, nitems, s, cursor, partials, grid);
+    } else {
+        if (pv) launch_shape<true, 128>(G, items, nitems, s, cursor, partials, grid);
+        else launch_shape<false, 128>(G, items, nitems, s, cursor, partials, grid);
+    }
     PGB_CHECK_LAUNCH("k_tc_hash");
 }
 

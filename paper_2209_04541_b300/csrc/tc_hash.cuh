@@ -25,6 +25,7 @@ struct ItemSpace {
     const uint32_t* colptr;
     const uint32_t* col;
     uint32_t cbase, vbase, w0, nwin, n;
+    uint32_t keycap;  // table keys per item: 1024 (fits both CTA shapes) or 2048 (256 threads only)
 };
 
 // One work item of the middle-vertex kernel (built on the device).
@@ -39,9 +40,11 @@ struct VItem {
     uint32_t mask;        // members with in-edges and out-edges in this item's index (bit t: v0 + t)
 };
 
-// Work items of one partitioned graph; returns their number (synchronises
-// `s` once to learn it).  in_chunk: in-edges per item (0 = default).
-uint32_t build_hash_items(const pgb_blocks* b, uint32_t in_chunk, cudaStream_t s, DevBuf<VItem>& items);
+// Work items of one partitioned graph for the hash kernel with `threads`
+// per CTA; returns their number (synchronises `s` once to learn it).
+// in_chunk: in-edges per item (0 = default).
+uint32_t build_hash_items(const pgb_blocks* b, uint32_t in_chunk, int threads, cudaStream_t s,
+                          DevBuf<VItem>& items);
 
 // The same over an item space (a range of heads with their own in-edge
 // offsets); item in-edge ranges are positions in those offsets.
@@ -50,19 +53,25 @@ uint32_t build_hash_items_in(const ItemSpace& sp, uint32_t in_chunk, cudaStream_
 // The graph view of a resident partition for the hash kernel.
 HashGraph resident_hash_graph(const pgb_blocks* b, unsigned long long* tv);
 
-// CTAs of a persistent launch on the current device.
-int hash_grid(bool pv);
+// Threads per CTA of the hash kernel for a graph of n vertices (128 or 256;
+// part of the run-level autotuner).
+int hash_threads(uint32_t n);
+
+// CTAs of a persistent launch of that shape on the current device.
+int hash_grid(bool pv, int threads);
 
 // One persistent launch over `nitems` work items of graph G; partials must
 // hold `grid` entries and receive one total per CTA.
 void launch_hash(const HashGraph& G, const VItem* items, uint32_t nitems, bool pv, cudaStream_t s,
-                 unsigned int* cursor, unsigned long long* partials, int grid);
+                 unsigned int* cursor, unsigned long long* partials, int grid, int threads);
 
 // Streamed run over blocks whose in-edge index is in pinned host memory:
 // chunks of work items whose in-edges fit two device slots within `budget`
 // bytes (0 = 1 GiB slots), copied on a side stream while the previous chunk
-// counts on `s`.  Returns after the work completes.
-void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, unsigned long long* tv, uint64_t budget,
+// counts on `s`.  threads: CTA shape (0 = autotuned).  Returns after the
+// work completes.
+void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint32_t threads, unsigned long long* tv,
+                   uint64_t budget,
                    cudaStream_t s, DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
                    cudaEvent_t ev1, uint64_t* streamed, uint32_t* nchunks);
 
@@ -70,7 +79,8 @@ void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, unsigned lon
 // (tail block, head block) with their column slices in a device cache that
 // the budget sizes.  Returns after the work completes; partials gets two
 // running totals.
-void run_column_streaming(const pgb_blocks* b, bool pv, unsigned long long* tv, uint64_t budget, cudaStream_t s,
+void run_column_streaming(const pgb_blocks* b, bool pv, uint32_t threads, unsigned long long* tv, uint64_t budget,
+                          cudaStream_t s,
                           DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
                           cudaEvent_t ev1, uint64_t* streamed, uint32_t* npieces, uint32_t* slice_loads);
 

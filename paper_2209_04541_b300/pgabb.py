@@ -70,7 +70,7 @@ class TcOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("variant", ctypes.c_int32), ("per_vertex", ctypes.c_int32),
                 ("per_triple", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("device_budget", ctypes.c_uint64), ("chunk_edges", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 7)]
+                ("hash_threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 6)]
 
 
 class BlocksStats(ctypes.Structure):

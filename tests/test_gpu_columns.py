@@ -32,8 +32,9 @@ def _oracle(src, dst, n):
     return oracle.tc_node_iterator(oracle.clean(src, dst, n))
 
 
-def _run(b, per_vertex=True, budget=0):
-    r = P.pgb_tc_run(b, P.pgb_tc_opts_default(per_vertex=int(per_vertex), device_budget=budget))
+def _run(b, per_vertex=True, budget=0, threads=0):
+    r = P.pgb_tc_run(b, P.pgb_tc_opts_default(per_vertex=int(per_vertex), device_budget=budget,
+                                              hash_threads=threads))
     T, t = P.pgb_tc_result_get(r, per_vertex=per_vertex)
     nbytes, pieces, loads = P.pgb_tc_result_stream(r, slice_loads=True)
     assert P.pgb_tc_result_variant(r) == P.PGB_VAR_HASH
@@ -114,8 +115,9 @@ def test_heavy_heads_and_key_slices_column_tier():
     for p in (1, 4, 9):
         b = _blocks(src, dst, n, p)
         P.pgb_blocks_offload_columns(b)
-        T, t, _, _, _ = _run(b, True, P.pgb_blocks_cache_budget(b, 2))
-        assert T == oT and np.array_equal(t, ot)
+        for threads in (128, 256):
+            T, t, _, _, _ = _run(b, True, P.pgb_blocks_cache_budget(b, 2), threads)
+            assert T == oT and np.array_equal(t, ot)
 
 
 def test_empty_and_edgeless_column_tier():

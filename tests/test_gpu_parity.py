@@ -23,7 +23,8 @@ P = pgabb
 
 
 def gpu_count(src, dst, n, p, rule=P.PGB_CUT_NNZ, mode=P.PGB_MODE_PERSISTENT, per_vertex=True,
-              device=True, chunk=0, order=P.PGB_ORDER_WEIGHT, per_triple=False, variant=P.PGB_VAR_AUTO):
+              device=True, chunk=0, order=P.PGB_ORDER_WEIGHT, per_triple=False, variant=P.PGB_VAR_AUTO,
+              hash_threads=0):
     if device:
         s = torch.from_numpy(np.ascontiguousarray(src, np.uint32)).cuda()
         d = torch.from_numpy(np.ascontiguousarray(dst, np.uint32)).cuda()
@@ -32,7 +33,7 @@ def gpu_count(src, dst, n, p, rule=P.PGB_CUT_NNZ, mode=P.PGB_MODE_PERSISTENT, pe
     g = P.pgb_graph_from_edges(s, d, n)
     b = P.pgb_partition(g, p, rule)
     opts = P.pgb_tc_opts_default(mode=mode, per_vertex=int(per_vertex), chunk_edges=chunk, order=order,
-                                 per_triple=int(per_triple), variant=variant)
+                                 per_triple=int(per_triple), variant=variant, hash_threads=hash_threads)
     r = P.pgb_tc_run(b, opts)
     T, t = P.pgb_tc_result_get(r, per_vertex=per_vertex)
     tri = P.pgb_tc_result_triples(r) if per_triple else None
@@ -247,6 +248,35 @@ def test_hash_splits_heavy_middle_vertices():
                 gT, gt, _, _, _ = gpu_count(src, dst, n, p, variant=variant, chunk=chunk)
                 assert gT == comb(k, 3) + 3 * extra
                 assert np.array_equal(gt, want_t)
+
+
+@pytest.mark.parametrize("threads", [128, 256])
+def test_hash_cta_shapes(threads):
+    """Both CTA shapes of the hash kernel (the autotuner picks 256 threads
+    only for graphs of 2^26+ vertices, so they are forced here)."""
+    for path in golden_files():
+        src, dst, n, T, t = load_golden(path)
+        for p in sorted({1, 2, n}):
+            gT, gt, _, _, _ = gpu_count(src, dst, n, p, variant=P.PGB_VAR_HASH, hash_threads=threads)
+            assert gT == T and np.array_equal(gt, t)
+    for seed in range(3):
+        rng = np.random.default_rng(800 + seed)
+        n = int(rng.integers(2, 3000))
+        src, dst = messy_random(n, int(rng.integers(0, 20 * n)), rng)
+        T, t, _ = oracle_count(src, dst, n)
+        gT, gt, _, _, _ = gpu_count(src, dst, n, int(rng.integers(1, 9)), variant=P.PGB_VAR_HASH,
+                                    hash_threads=threads)
+        assert gT == T and np.array_equal(gt, t)
+    src, dst, n = graphgen.rmat(15, 16, 21)
+    oT, ot = oracle.tc_node_iterator(oracle.clean(src, dst, n))
+    for pv in (True, False):
+        gT, gt, _, _, _ = gpu_count(src, dst, n, 8, variant=P.PGB_VAR_HASH, hash_threads=threads, per_vertex=pv)
+        assert gT == oT
+        if pv:
+            assert np.array_equal(gt, ot)
+    with pytest.raises(P.PgbError) as ei:
+        gpu_count(src, dst, n, 8, variant=P.PGB_VAR_HASH, hash_threads=192)
+    assert ei.value.code == P.PGB_E_INVAL
 
 
 def test_plain_mode_rejects_hash():

@@ -36,8 +36,9 @@ def _oracle(src, dst, n):
     return oracle.tc_node_iterator(g)
 
 
-def _streamed(b, per_vertex, budget):
-    r = P.pgb_tc_run(b, P.pgb_tc_opts_default(per_vertex=int(per_vertex), device_budget=budget))
+def _streamed(b, per_vertex, budget, threads=0):
+    r = P.pgb_tc_run(b, P.pgb_tc_opts_default(per_vertex=int(per_vertex), device_budget=budget,
+                                              hash_threads=threads))
     T, t = P.pgb_tc_result_get(r, per_vertex=per_vertex)
     nbytes, chunks = P.pgb_tc_result_stream(r)
     assert P.pgb_tc_result_variant(r) == P.PGB_VAR_HASH
@@ -68,13 +69,14 @@ def test_rmat_streamed_matches_oracle_and_resident(per_vertex):
         assert np.array_equal(t1, ot)
 
 
-def test_tiny_slots_many_chunks():
+@pytest.mark.parametrize("threads", [128, 256])
+def test_tiny_slots_many_chunks(threads):
     """Slots of 4096 in-edges, the largest work item: hundreds of chunks."""
     src, dst, n = graphgen.rmat(14, 16, 5)
     oT, ot = _oracle(src, dst, n)
     b = _blocks(src, dst, n, 4)
     P.pgb_blocks_offload(b)
-    T, t, _, chunks = _streamed(b, True, _budget(b, True, 4096))
+    T, t, _, chunks = _streamed(b, True, _budget(b, True, 4096), threads)
     assert chunks > 20
     assert T == oT and np.array_equal(t, ot)
 
