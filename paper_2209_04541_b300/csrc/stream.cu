@@ -565,7 +565,10 @@ void run_column_streaming(const pgb_blocks* b, bool pv, uint32_t threads, unsign
     }
     // task order: head blocks in groups of G; the group's head slices stay
     // while the tail blocks pass, so each tail slice is loaded once per group
-    const uint32_t G = std::max<uint32_t>(1, C > 1 ? C - 1 : 1);
+    // with four slices or more, the next piece's copies are issued before
+    // this piece's launch (queue lookahead), which needs one more slice
+    const bool look = C >= 4;
+    const uint32_t G = look ? C - 2 : std::max<uint32_t>(1, C > 1 ? C - 1 : 1);
     std::vector<std::vector<uint32_t>> by_pair((size_t)p * p);
     for (uint32_t k = 0; k < P.pieces.size(); ++k) by_pair[(size_t)P.pieces[k].i * p + P.pieces[k].j].push_back(k);
     std::vector<uint32_t> order;
@@ -659,20 +662,24 @@ void run_column_streaming(const pgb_blocks* b, bool pv, uint32_t threads, unsign
             slot_tick[victim] = ++tick;
             return (uint32_t)victim;
         };
-        for (size_t t = 0; t < order.size(); ++t) {
+        std::vector<uint32_t> ssj(order.size()), ssi(order.size());
+        // copies of piece t: its slices (never evicting those of the piece
+        // staged before it, nor its head group's) and its index and items
+        auto stage = [&](size_t t) {
             const ColPiece& c = P.pieces[order[t]];
             const int k = (int)(t & 1);
-            const cudaStream_t ss = ks[k];
-            // slices: the head block's group stays; keep both of this task's
             const uint32_t G0 = (c.j / G) * G, G1 = std::min(p, G0 + G);
             std::vector<uint32_t> keep;
             for (uint32_t jj = G0; jj < G1; ++jj)
                 if (blk_slot[jj] >= 0) keep.push_back(jj);
             keep.push_back(c.i);
             keep.push_back(c.j);
-            const uint32_t sj = acquire(c.j, keep);
-            const uint32_t si = acquire(c.i, keep);
-            // the piece: index slice and work items into piece slot k
+            if (look && t > 0) {  // staged ahead of the launch of piece t - 1
+                keep.push_back(P.pieces[order[t - 1]].i);
+                keep.push_back(P.pieces[order[t - 1]].j);
+            }
+            ssj[t] = acquire(c.j, keep);
+            ssi[t] = acquire(c.i, keep);
             if (t >= 2) PGB_CUDA(cudaStreamWaitEvent(cs, piece_done[k], 0));
             const uint64_t ne = c.e1 - c.e0, ni = c.it1 - c.it0;
             PGB_CUDA(cudaMemcpyAsync(px[k].ptr, P.h_bx + c.e0, ne * 8, cudaMemcpyHostToDevice, cs));
@@ -682,6 +689,14 @@ void run_column_streaming(const pgb_blocks* b, bool pv, uint32_t threads, unsign
                                          cs));
             PGB_CUDA(cudaEventRecord(piece_ready[k], cs));
             bytes += ne * 12 + ni * sizeof(VItem);
+        };
+        // the counting launch of piece t on stream t & 1
+        auto launch = [&](size_t t) {
+            const ColPiece& c = P.pieces[order[t]];
+            const int k = (int)(t & 1);
+            const cudaStream_t ss = ks[k];
+            const uint32_t sj = ssj[t], si = ssi[t];
+            const uint64_t ni = c.it1 - c.it0;
             PGB_CUDA(cudaStreamWaitEvent(ss, piece_ready[k], 0));
             PGB_CUDA(cudaStreamWaitEvent(ss, slot_ready[sj], 0));
             PGB_CUDA(cudaStreamWaitEvent(ss, slot_ready[si], 0));
@@ -699,6 +714,18 @@ void run_column_streaming(const pgb_blocks* b, bool pv, uint32_t threads, unsign
             for (uint32_t q : {sj, si}) {
                 PGB_CUDA(cudaEventRecord(k ? slot_used1[q] : slot_used0[q], ss));
                 (k ? used1 : used0)[q] = true;
+            }
+        };
+        if (look) {
+            if (!order.empty()) stage(0);
+            for (size_t t = 0; t < order.size(); ++t) {
+                if (t + 1 < order.size()) stage(t + 1);
+                launch(t);
+            }
+        } else {
+            for (size_t t = 0; t < order.size(); ++t) {
+                stage(t);
+                launch(t);
             }
         }
         PGB_CUDA(cudaEventRecord(done1, s1));
