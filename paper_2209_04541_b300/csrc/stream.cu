@@ -525,7 +525,9 @@ static ColSizes col_sizes(const pgb_blocks* b, bool pv, uint32_t threads) {
         z.max_edges = std::max(z.max_edges, c.e1 - c.e0);
         z.max_items = std::max(z.max_items, c.it1 - c.it0);
     }
-    z.threads = threads ? (int)threads : hash_threads(b->n);
+    // pieces hold one tail block's in-edges, so items are small: the
+    // 128-thread shape serves them better at every size measured
+    z.threads = threads ? (int)threads : 128;
     z.grid = hash_grid(pv, z.threads);
     z.fixed = col_resident_bytes(b, pv) + 2 * (std::max<uint64_t>(z.max_edges, 1) * 12 +
                                                std::max<uint64_t>(z.max_items, 1) * sizeof(VItem)) +
