@@ -45,6 +45,8 @@ import graphgen  # noqa: E402
 WORKLOADS = {
     "rmat24": dict(kind="rmat", scale=24, ef=16, p=32, seed=1,
                    desc="R-MAT scale 24, edge factor 16 (a,b,c,d = .57,.19,.19,.05), seeded relabel; p=32"),
+    "rmat23": dict(kind="rmat", scale=23, ef=16, p=32, seed=1,
+                   desc="R-MAT scale 23, edge factor 16 (a,b,c,d = .57,.19,.19,.05), seeded relabel; p=32"),
     "rmat22": dict(kind="rmat", scale=22, ef=16, p=32, seed=1,
                    desc="R-MAT scale 22, edge factor 16 (a,b,c,d = .57,.19,.19,.05), seeded relabel; p=32"),
     "rmat20": dict(kind="rmat", scale=20, ef=16, p=16, seed=1,

@@ -244,7 +244,7 @@ int pgb_blocks_offload_columns(pgb_blocks* b, void* stream);
 int pgb_blocks_cache_budget(const pgb_blocks* b, int per_vertex, uint32_t slices, uint64_t* budget);
 
 /* The device bytes a streamed run on `b` holds besides its two stream slots:
- * 4(n+1) + 4(m+4) + 4(n+1) + 4n + 4(p+1) for the resident arrays, 16n for the
+ * 4(n+1) + 4(m+8) + 4(n+1) + 4n + 4(p+1) for the resident arrays, 16n for the
  * per-vertex counters when per_vertex != 0, and 16 MiB for the launches'
  * partial sums.  A device_budget must exceed it; the rest is split into two
  * slots of 44 bytes per in-edge (index entry plus one work item bound).

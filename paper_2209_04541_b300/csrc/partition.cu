@@ -257,10 +257,10 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
 
     // --- orientation: sort (low rank, high rank) keys
     b->rowptr.alloc((size_t)n + 1, s);
-    // 4 spare entries: the counting kernels read rows with aligned 16-byte
-    // loads, whose last load may extend up to 3 entries past the last edge
-    b->col.alloc(m + 4, s);
-    PGB_CUDA(cudaMemsetAsync(b->col.ptr + m, 0, 16, s));
+    // 8 spare entries: the counting kernels read rows with aligned 32-byte
+    // loads, whose last load may extend up to 7 entries past the last edge
+    b->col.alloc(m + 8, s);
+    PGB_CUDA(cudaMemsetAsync(b->col.ptr + m, 0, 32, s));
     b->rowidx.alloc(m, s);
     if (m > 0) {
         DevBuf<uint64_t> ok(m, s), oalt(m, s);

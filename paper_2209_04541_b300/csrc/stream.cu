@@ -43,7 +43,7 @@ constexpr uint64_t kDefaultSlotBytes = 1ull << 30;
 // Device bytes a streamed run holds besides its two slots.
 static uint64_t resident_bytes(const pgb_blocks* b, bool pv) {
     const uint64_t n = b->n;
-    return 4 * (n + 1) + 4 * (b->m + 4) + 4 * (n + 1) + 4 * n + 4 * ((uint64_t)b->p + 1) + (pv ? 16 * n : 0) +
+    return 4 * (n + 1) + 4 * (b->m + 8) + 4 * (n + 1) + 4 * n + 4 * ((uint64_t)b->p + 1) + (pv ? 16 * n : 0) +
            kPartialsReserve;
 }
 
@@ -264,13 +264,13 @@ struct ColPiece {
 };
 
 struct ColPlan {
-    uint32_t* h_col = nullptr;  // m + 8 columns (zero padded), pinned
+    uint32_t* h_col = nullptr;  // m + 16 columns (zero padded), pinned
     unsigned long long* h_bx = nullptr;  // index by (tail block, head, tail): tail-row range, pinned
     uint32_t* h_bt = nullptr;            // the tails, pinned
     VItem* h_items = nullptr;            // every piece's work items, pinned
     uint64_t nitems = 0;
     std::vector<ColPiece> pieces;
-    std::vector<uint32_t> slice_lo, slice_len;  // per row block: first column (a multiple of 4), length
+    std::vector<uint32_t> slice_lo, slice_len;  // per row block: first column (a multiple of 8), length
     ~ColPlan() {
         if (h_col) cudaFreeHost(h_col);
         if (h_bx) cudaFreeHost(h_bx);
@@ -378,14 +378,14 @@ static std::shared_ptr<ColPlan> build_col_plan(pgb_blocks* b, cudaStream_t s) {
         P->slice_lo.resize(p);
         P->slice_len.resize(p);
         for (uint32_t i = 0; i < p; ++i) {
-            const uint32_t lo = pos[i] & ~3u;
-            const uint32_t hi = ((pos[i + 1] + 3) & ~3u) + 4;  // aligned quad loads may read past the row
+            const uint32_t lo = pos[i] & ~7u;
+            const uint32_t hi = ((pos[i + 1] + 7) & ~7u) + 8;  // aligned 32-byte loads may read past the row
             P->slice_lo[i] = lo;
             P->slice_len[i] = hi - lo;
         }
     }
-    PGB_CUDA(cudaHostAlloc(&P->h_col, (size_t)(m + 8) * 4, cudaHostAllocDefault));
-    std::memset(P->h_col + m, 0, 8 * 4);
+    PGB_CUDA(cudaHostAlloc(&P->h_col, (size_t)(m + 16) * 4, cudaHostAllocDefault));
+    std::memset(P->h_col + m, 0, 16 * 4);
     if (m) PGB_CUDA(cudaMemcpyAsync(P->h_col, b->col.ptr, (size_t)m * 4, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaHostAlloc(&P->h_bx, (size_t)std::max<uint64_t>(m, 1) * 8, cudaHostAllocDefault));
     PGB_CUDA(cudaHostAlloc(&P->h_bt, (size_t)std::max<uint64_t>(m, 1) * 4, cudaHostAllocDefault));

@@ -13,11 +13,12 @@
 //
 // Work items (built on the device, heaviest middle vertices first):
 //   group item:     up to 32 consecutive ranks whose partial lists hold at
-//                   most kKeyCap entries in total and whose in-edges number
-//                   at most in_chunk; table entries carry a 32-bit mask of
-//                   the group members that own the key;
+//                   most K entries in total (K: the table capacity of the
+//                   CTA shape) and whose in-edges number at most in_chunk;
+//                   table entries carry a 32-bit mask of the group members
+//                   that own the key;
 //   singleton item: one middle vertex, a run of at most in_chunk of its
-//                   in-edges, and a slice of at most kKeyCap entries of its
+//                   in-edges, and a slice of at most K entries of its
 //                   list (the slice is a third-vertex rank range [lo, hi),
 //                   i.e. a narrower column-block run; both lists are clipped).
 // Per-vertex counts: a shared counter per table slot collects t[w], a
@@ -44,8 +45,7 @@ constexpr uint32_t key_capacity(int threads) { return 32u * threads / 4; }
 // wider bitmaps serve more of the top-ranked middle vertices (measured on
 // R-MAT: scale 27 runs 13% faster with it, scale 22 26% slower).
 constexpr uint32_t kWideShapeVertices = 1u << 26;
-constexpr int kUnrollPV = 4;           // 16-byte quad loads per lane issued together (per-vertex run)
-constexpr int kUnrollGlobal = 4;       // the same for a global-count run
+constexpr int kPairSlots = 3;          // 32-byte loads (8 entries) per lane issued together
 
 __device__ __forceinline__ uint32_t hslot(uint32_t x, uint32_t log2s) { return (x * 0x9E3779B1u) >> (32 - log2s); }
 
@@ -373,13 +373,13 @@ __global__ void __launch_bounds__(T, 1024 / T)
                     sl = xe - xb;
                 }
             }
-            // The lists of the batch, cut into aligned 4-entry quads, form one
-            // sequence that the lanes share: each lane takes kUnroll quads
-            // per step with one 16-byte load each, so many loads per lane are
-            // in flight across in-edge boundaries, and the owner lookup is paid
-            // once per 4 entries.
-            const uint32_t qa = sb >> 2;
-            const uint32_t nq = sl ? ((sb + sl + 3) >> 2) - qa : 0;
+            // The lists of the batch, cut into aligned 8-entry pairs of quads,
+            // form one sequence that the lanes share: each lane takes
+            // kPairSlots pairs per step with two 16-byte loads each, so many
+            // loads per lane are in flight across in-edge boundaries, and the
+            // owner lookup is paid once per 8 entries.
+            const uint32_t qa = sb >> 3;
+            const uint32_t nq = sl ? ((sb + sl + 7) >> 3) - qa : 0;
             uint32_t incl = nq;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -389,9 +389,9 @@ __global__ void __launch_bounds__(T, 1024 / T)
             const uint32_t total = __shfl_sync(kFullMask, incl, 31);
             const uint32_t excl = incl - nq;
             const uint32_t send = sb + sl;
-            constexpr int U = PV ? kUnrollPV : kUnrollGlobal;
+            constexpr int U = kPairSlots;
             for (uint32_t r0 = 0; r0 < total; r0 += 32 * U) {
-                uint4 qv[U];
+                uint4 qv[U], qw[U];
                 uint32_t qb[U], lo_[U], hi_[U], bits[U], own[U];
 #pragma unroll
                 for (int j = 0; j < U; ++j) {
@@ -407,24 +407,28 @@ __global__ void __launch_bounds__(T, 1024 / T)
                     hi_[j] = __shfl_sync(kFullMask, send, o);
                     bits[j] = __shfl_sync(kFullMask, vbit, o);
                     own[j] = o;
-                    qb[j] = 4 * ((lo_[j] >> 2) + (f - o_ex));
-                    qv[j] = f < total ? __ldg(reinterpret_cast<const uint4*>(G.colu + (qb[j] - G.ubase)))
-                                      : make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+                    qb[j] = 8 * ((lo_[j] >> 3) + (f - o_ex));
+                    if (f < total) {
+                        const uint4* a = reinterpret_cast<const uint4*>(G.colu + (qb[j] - G.ubase));
+                        qv[j] = __ldg(a);
+                        qw[j] = __ldg(a + 1);
+                    } else {
+                        qv[j] = qw[j] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+                    }
                     if (f >= total) hi_[j] = 0;
                 }
 #pragma unroll
                 for (int j = 0; j < U; ++j) {
-                    const uint32_t xv[4] = {qv[j].x, qv[j].y, qv[j].z, qv[j].w};
+                    const uint32_t xv[8] = {qv[j].x, qv[j].y, qv[j].z, qv[j].w, qw[j].x, qw[j].y, qw[j].z, qw[j].w};
                     uint32_t h4 = 0;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < 8; ++i) {
                         const uint32_t p = qb[j] + i;
                         if (p < lo_[j] || p >= hi_[j]) continue;
                         const uint32_t x = xv[i];
                         bool hit;
                         uint32_t h = 0;
                         if (bitmap) {
-                            // entries outside the list's span cannot match
                             const uint32_t d = x - rlo;
                             const uint32_t word = regA[d >> 5];
                             hit = (word >> (d & 31)) & 1u;

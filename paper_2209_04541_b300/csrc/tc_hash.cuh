@@ -14,7 +14,7 @@ struct HashGraph {
     uint32_t n;                           // vertices
     const uint32_t* __restrict__ itail = nullptr;  // tail of each in-edge (streamed runs), else null
     const uint32_t* __restrict__ colu = nullptr;   // rows of the tails: entry q at colu[q - ubase]
-    uint32_t vbase = 0, ubase = 0;                 // ubase is a multiple of 4
+    uint32_t vbase = 0, ubase = 0;                 // ubase is a multiple of 8 (32-byte loads)
 };
 
 // Where the item builder finds the heads of a set of in-edges: window w
