@@ -472,7 +472,7 @@ static std::shared_ptr<ColPlan> build_col_plan(pgb_blocks* b, cudaStream_t s) {
         k_local_colptr<<<(len + 255) / 256, 256, 0, s>>>(bh.ptr, e0, e1, w0, len, lc.ptr);
         PGB_CHECK_LAUNCH("k_local_colptr");
         // items that fit either CTA shape: the smaller table capacity
-        const ItemSpace sp{b->rowptr.ptr, lc.ptr, b->col.ptr, w0, 0, w0, nwin, n, 1024};
+        const ItemSpace sp{b->rowptr.ptr, lc.ptr, b->col.ptr, w0, 0, w0, nwin, n, 1024, 131072};
         DevBuf<VItem> its;
         const uint32_t ni = build_hash_items_in(sp, 0, s, its);
         ColPiece pc{pairs[k].first, pairs[k].second, e0, e1, all.size(), all.size() + ni};

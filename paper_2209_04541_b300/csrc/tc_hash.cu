@@ -38,8 +38,10 @@ namespace {
 constexpr uint32_t kInChunkDefault = 4096;  // in-edges per item unless the caller sets one
 constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr unsigned kFullMask = 0xffffffffu;
-// Table keys per work item of a CTA shape (tables stay at most half full).
+// Table keys per work item of a CTA shape (tables stay at most half full),
+// and the widest third-vertex range it holds as a bitmap.
 constexpr uint32_t key_capacity(int threads) { return 32u * threads / 4; }
+constexpr uint32_t bitmap_range(int threads) { return 32u * 32u * threads; }
 
 // Graphs with at least this many vertices run the 256-thread shape: its
 // wider bitmaps serve more of the top-ranked middle vertices (measured on
@@ -111,13 +113,23 @@ __device__ __forceinline__ uint32_t table_find(const uint32_t* keys, uint32_t x,
     return kEmpty;
 }
 
-// Item decisions for the window of 32 ranks starting at 32 * w (one warp).
+// Item decisions for the window of 32 ranks starting at w0 + 32 w (one warp).
+// A window whose active lists fit one table is one group item.  Otherwise:
+//   - a lane too big for one item (more keys than the capacity or more
+//     in-edges than in_chunk), or whose range fits a bitmap, is a singleton,
+//     split into in-edge chunks and key slices;
+//   - the other active lanes ("light") form runs of consecutive ranks whose
+//     keys fit one table and whose in-edges fit in_chunk, scanned greedily in
+//     rank order; a run of two or more is a group item, a run of one a
+//     singleton.  Without runs, mid-rank windows would give one small item
+//     per vertex, each paying the per-item barriers.
 struct WindowInfo {
     uint32_t v, dp, dm;
     bool act;
-    uint32_t keys, ins;
-    bool group;
-    uint32_t mine;  // singleton items of this lane
+    uint32_t keys, ins;  // the whole window's active lanes
+    bool group;          // the whole window is one group item
+    uint32_t mine;       // items this lane emits
+    uint32_t run_len, run_mask, run_keys;  // a run starting at this lane (run_len > 0)
 };
 
 __device__ __forceinline__ WindowInfo window_info(const ItemSpace& sp, uint32_t w, uint32_t in_chunk, int lane) {
@@ -132,7 +144,47 @@ __device__ __forceinline__ WindowInfo window_info(const ItemSpace& sp, uint32_t 
     W.keys = warp_sum(W.act ? W.dp : 0);
     W.ins = warp_sum(W.act ? W.dm : 0);
     W.group = W.keys > 0 && W.keys <= sp.keycap && W.ins <= in_chunk;
-    W.mine = (W.act && !W.group) ? ((W.dm + in_chunk - 1) / in_chunk) * ((W.dp + sp.keycap - 1) / sp.keycap) : 0;
+    W.run_len = W.run_mask = W.run_keys = 0;
+    W.mine = 0;
+    if (W.group || W.keys == 0) return W;
+    const bool light = W.act && W.dp <= sp.keycap && W.dm <= in_chunk && sp.n - W.v - 1 > sp.bitmap_bits;
+    const bool heavy = W.act && !light;
+    if (heavy) W.mine = ((W.dm + in_chunk - 1) / in_chunk) * ((W.dp + sp.keycap - 1) / sp.keycap);
+    // the same greedy scan in every lane (uniform), each keeping its own run
+    uint32_t rs = 32, rlast = 0, rk = 0, ri = 0, rm = 0;
+    auto close = [&] {
+        if (rs < 32 && lane == (int)rs) {
+            W.run_len = rlast - rs + 1;
+            W.run_mask = rm;
+            W.run_keys = rk;
+            W.mine = 1;
+        }
+        rs = 32;
+    };
+    for (uint32_t t = 0; t < 32; ++t) {
+        const bool lt = __shfl_sync(kFullMask, light, t);
+        const bool ht = __shfl_sync(kFullMask, heavy, t);
+        const uint32_t dpt = __shfl_sync(kFullMask, W.dp, t);
+        const uint32_t dmt = __shfl_sync(kFullMask, W.dm, t);
+        if (ht) {
+            close();
+        } else if (lt) {
+            if (rs < 32 && (rk + dpt > sp.keycap || ri + dmt > in_chunk)) close();
+            if (rs == 32) {
+                rs = t;
+                rk = ri = rm = 0;
+            }
+            rk += dpt;
+            ri += dmt;
+            rm |= 1u << (t - rs);
+            rlast = t;
+        } else if (rs < 32) {
+            // an inactive lane inside a run: its in-edges lie in the run's range
+            if (ri + dmt > in_chunk) close();
+            else ri += dmt;
+        }
+    }
+    close();
     return W;
 }
 
@@ -147,6 +199,21 @@ __global__ void k_items_count(const ItemSpace sp, uint32_t in_chunk, uint32_t* _
     }
 }
 
+__device__ __forceinline__ VItem group_item(const ItemSpace& sp, uint32_t v0, uint32_t nv, uint32_t keys,
+                                            uint32_t mask) {
+    VItem it;
+    it.v0 = v0;
+    it.nv = nv;
+    it.in_begin = sp.colptr[v0 - sp.cbase];
+    it.in_end = sp.colptr[v0 + nv - sp.cbase];
+    it.lo = 0;
+    it.hi = sp.n;
+    it.slots_log2 = (uint16_t)slots_for(keys);
+    it.clip = 0;
+    it.mask = mask;
+    return it;
+}
+
 __global__ void k_items_emit(const ItemSpace sp, uint32_t in_chunk, const uint32_t* __restrict__ offs,
                              VItem* __restrict__ items) {
     const int lane = threadIdx.x & 31;
@@ -159,17 +226,8 @@ __global__ void k_items_emit(const ItemSpace sp, uint32_t in_chunk, const uint32
         const unsigned act = __ballot_sync(kFullMask, W.act);
         if (W.group) {
             if (lane == 0) {
-                VItem it;
-                it.v0 = sp.w0 + w * 32;
-                it.nv = min(32u, n - it.v0);
-                it.in_begin = sp.colptr[it.v0 - sp.cbase];
-                it.in_end = sp.colptr[it.v0 + it.nv - sp.cbase];
-                it.lo = 0;
-                it.hi = n;
-                it.slots_log2 = (uint16_t)slots_for(W.keys);
-                it.clip = 0;
-                it.mask = act;
-                items[base] = it;
+                const uint32_t v0 = sp.w0 + w * 32;
+                items[base] = group_item(sp, v0, min(32u, n - v0), W.keys, act);
             }
             continue;
         }
@@ -181,11 +239,16 @@ __global__ void k_items_emit(const ItemSpace sp, uint32_t in_chunk, const uint32
         }
         excl -= W.mine;
         if (!W.mine) continue;
+        uint32_t out = base + excl;
+        if (W.run_len > 1) {
+            items[out] = group_item(sp, W.v, W.run_len, W.run_keys, W.run_mask);
+            continue;
+        }
+        // a singleton: in-edge chunks times key slices
         const uint32_t na = (W.dm + in_chunk - 1) / in_chunk;
         const uint32_t kc = sp.keycap;
         const uint32_t nk = (W.dp + kc - 1) / kc;
         const uint32_t rb = sp.rowptr[W.v], cb = sp.colptr[W.v - sp.cbase];
-        uint32_t out = base + excl;
         for (uint32_t a = 0; a < na; ++a) {
             for (uint32_t kk = 0; kk < nk; ++kk) {
                 VItem it;
@@ -571,7 +634,7 @@ uint32_t build_hash_items(const pgb_blocks* b, uint32_t in_chunk, int threads, c
         return 0;
     }
     const ItemSpace sp{b->rowptr.ptr, b->colptr.ptr, b->col.ptr, 0, 0, 0, (b->n + 31) / 32, b->n,
-                       key_capacity(threads)};
+                       key_capacity(threads), bitmap_range(threads)};
     return build_hash_items_in(sp, in_chunk, s, items);
 }
 

@@ -25,7 +25,8 @@ struct ItemSpace {
     const uint32_t* colptr;
     const uint32_t* col;
     uint32_t cbase, vbase, w0, nwin, n;
-    uint32_t keycap;  // table keys per item: 1024 (fits both CTA shapes) or 2048 (256 threads only)
+    uint32_t keycap;       // table keys per item: 1024 (fits both CTA shapes) or 2048 (256 threads only)
+    uint32_t bitmap_bits;  // widest range a singleton holds as a bitmap (such vertices are never grouped)
 };
 
 // One work item of the middle-vertex kernel (built on the device).
