@@ -479,6 +479,8 @@ def main(argv=None):
     ap.add_argument("--variant", choices=["auto", "bsearch", "merge", "hash"], default="auto")
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--per-vertex", type=int, default=1)
+    ap.add_argument("--hash-threads", type=int, default=0, choices=[0, 128, 256],
+                    help="CTA shape of the hash kernel (0 = autotuned)")
     ap.add_argument("--p", type=int, default=0, help="override the workload's p")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -532,6 +534,7 @@ def main(argv=None):
     variant = {"auto": P.PGB_VAR_AUTO, "bsearch": P.PGB_VAR_BSEARCH, "merge": P.PGB_VAR_MERGE,
                "hash": P.PGB_VAR_HASH}[args.variant]
     opts = P.pgb_tc_opts_default(mode=mode, per_vertex=args.per_vertex, chunk_edges=args.chunk, variant=variant,
+                                 hash_threads=args.hash_threads,
                                  order=P.PGB_ORDER_WEIGHT if args.order == "weight" else P.PGB_ORDER_LOCALITY)
     info = {}
 

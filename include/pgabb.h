@@ -274,7 +274,7 @@ typedef struct {
     uint32_t hash_threads; /* hash variant: threads per CTA, 128 (8 CTAs per
                               SM, bitmaps over up to 131,072 ranks) or 256 (4
                               per SM, 262,144 ranks); 0 = autotuned: 256 for
-                              graphs of at least 2^26 vertices, 128 always
+                              graphs of at least 2^24 vertices, 128 always
                               for column-offloaded blocks */
     uint32_t reserved[6];
 } pgb_tc_opts;

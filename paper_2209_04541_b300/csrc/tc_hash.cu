@@ -44,9 +44,10 @@ constexpr uint32_t key_capacity(int threads) { return 32u * threads / 4; }
 constexpr uint32_t bitmap_range(int threads) { return 32u * 32u * threads; }
 
 // Graphs with at least this many vertices run the 256-thread shape: its
-// wider bitmaps serve more of the top-ranked middle vertices (measured on
-// R-MAT: scale 27 runs 13% faster with it, scale 22 26% slower).
-constexpr uint32_t kWideShapeVertices = 1u << 26;
+// wider bitmaps and larger tables serve more of the top-ranked middle
+// vertices (measured on R-MAT kernels: 256 threads is 10% faster at scale 24
+// and 27% at scale 27; 128 threads is 9% faster at scale 23 and 31% at 22).
+constexpr uint32_t kWideShapeVertices = 1u << 24;
 constexpr int kPairSlots = 3;          // 32-byte loads (8 entries) per lane issued together
 
 __device__ __forceinline__ uint32_t hslot(uint32_t x, uint32_t log2s) { return (x * 0x9E3779B1u) >> (32 - log2s); }
