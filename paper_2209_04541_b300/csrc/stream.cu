@@ -394,7 +394,8 @@ static std::shared_ptr<ColPlan> build_col_plan(pgb_blocks* b, cudaStream_t s) {
         return P;
     }
     // tail-block-major order: a stable sort of the head-major index by the
-    // tail's block keeps (head, tail) order inside each block
+    // tail's block keeps the head order (and each head's tail order) inside
+    // each block
     DevBuf<uint32_t> itail(m, s);
     k_gather_tails<<<grid_for(m), 256, 0, s>>>(b->xr.ptr, m, b->rowidx.ptr, itail.ptr);
     PGB_CHECK_LAUNCH("k_gather_tails");
