@@ -447,11 +447,15 @@ def stream_bench(args):
     # tier 2: the block cache (columns offloaded too), from a fresh partition
     if args.cache_budget_gb > 0:
         b, _, _ = build()
+        budget = int(args.cache_budget_gb * (1 << 30))
+        # row ranges sized so that about five slices fit the budget beside the
+        # resident arrays (24 bytes per vertex) and the piece slots
+        avail = budget - 24 * n - (128 << 20)
+        slices = info["p"] if avail <= 0 else min(info["p"], max(2, -(-20 * m // avail)))
         t0 = time.perf_counter()
-        P.pgb_blocks_offload_columns(b)
+        P.pgb_blocks_offload_columns(b, slices)
         off_s = time.perf_counter() - t0
         torch.cuda.empty_cache()
-        budget = int(args.cache_budget_gb * (1 << 30))
         two = P.pgb_blocks_cache_budget(b, 2)
         if budget < two:
             out["cache"] = {"error": f"budget below two slices ({two} bytes)"}
@@ -459,7 +463,8 @@ def stream_bench(args):
             c = summary(timed(b, P.pgb_tc_opts_default(device_budget=budget), 1 + reps)[1:], budget,
                         P.pgb_blocks_resident_bytes(b, True))
             c["offload_s"] = off_s
-            c["slices_in_cache"] = sum(1 for k in range(1, info["p"] + 1)
+            c["slices"] = slices
+            c["slices_in_cache"] = sum(1 for k in range(1, slices + 1)
                                        if P.pgb_blocks_cache_budget(b, k) <= budget)
             out["cache"] = c
         b.free()

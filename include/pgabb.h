@@ -220,11 +220,14 @@ int pgb_blocks_offload(pgb_blocks* b, void* stream);
 /* Block cache tier (Section 4.4's copies of a task's blocks, with eviction):
  * moves the columns to pinned host memory as well, so that the device keeps
  * only the row offsets, the rank permutation and the cuts (about 8 bytes per
- * vertex; runs add 16 per vertex of counters).  Row block i of the columns
- * (ranks [c_i, c_{i+1})) is one contiguous slice.  The in-edge index is
- * re-sorted by (tail block, head, tail) into pinned host memory and cut into
- * pieces of at most 2^21 in-edges of one block pair (tail block i, head
- * block j); each piece's work items are built here, once.  A run keeps a
+ * vertex; runs add 16 per vertex of counters).  The ranks are cut into
+ * `slices` row ranges of about equal edges (0 = the partition's p; at most
+ * 1024, and at most n); the columns of one range form one contiguous slice.
+ * Fewer, larger slices mean fewer pieces and fewer table rebuilds, but a
+ * budget must hold at least two of them.  The in-edge index is re-sorted by
+ * (tail range, head, tail) into pinned host memory and cut into pieces of at
+ * most 2^21 in-edges of one range pair (tail range i, head range j); each
+ * piece's work items are built here, once.  A run keeps a
  * cache of column slices on the device, as many as device_budget allows
  * (at least two), evicting the least recently used slice that the current
  * pieces do not need; it counts the pieces head-block group by head-block
@@ -235,7 +238,7 @@ int pgb_blocks_offload(pgb_blocks* b, void* stream);
  * Needs about 36 bytes per edge of device memory while it builds the index.
  * Synchronises `stream`.  Errors: PGB_E_INVAL, PGB_E_STATE, PGB_E_NOMEM,
  * PGB_E_CUDA. */
-int pgb_blocks_offload_columns(pgb_blocks* b, void* stream);
+int pgb_blocks_offload_columns(pgb_blocks* b, uint32_t slices, void* stream);
 
 /* After pgb_blocks_offload_columns: the smallest device_budget whose column
  * cache holds `slices` slices (capped at p) for runs with the given

@@ -270,7 +270,9 @@ struct ColPlan {
     VItem* h_items = nullptr;            // every piece's work items, pinned
     uint64_t nitems = 0;
     std::vector<ColPiece> pieces;
-    std::vector<uint32_t> slice_lo, slice_len;  // per row block: first column (a multiple of 8), length
+    uint32_t pc = 0;                            // row ranges (slices) of the columns
+    std::vector<uint32_t> cuts;                 // pc + 1 rank cuts of those ranges
+    std::vector<uint32_t> slice_lo, slice_len;  // per row range: first column (a multiple of 8), length
     ~ColPlan() {
         if (h_col) cudaFreeHost(h_col);
         if (h_bx) cudaFreeHost(h_bx);
@@ -359,21 +361,41 @@ __global__ void k_gather_u32(const uint32_t* __restrict__ src, const uint64_t* _
     if (t < k) out[t] = src[at[t]];
 }
 
-static std::shared_ptr<ColPlan> build_col_plan(pgb_blocks* b, cudaStream_t s) {
+// Cuts of `pc` row ranges with about equal edges: cut[t] = least rank r with
+// rowptr[r] * pc >= t * m (cut[pc] = n).
+__global__ void k_col_cuts(const uint32_t* __restrict__ rowptr, uint32_t n, uint64_t m, uint32_t pc,
+                           uint32_t* __restrict__ cuts, uint32_t* __restrict__ pos) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > pc) return;
+    uint32_t lo = 0, hi = n;
+    if (t == pc) {
+        lo = n;
+    } else {
+        while (lo < hi) {
+            const uint32_t mid = lo + (hi - lo) / 2;
+            if ((uint64_t)rowptr[mid] * pc < (uint64_t)t * m) lo = mid + 1; else hi = mid;
+        }
+    }
+    cuts[t] = lo;
+    pos[t] = rowptr[lo];
+}
+
+static std::shared_ptr<ColPlan> build_col_plan(pgb_blocks* b, uint32_t pc, cudaStream_t s) {
     auto P = std::make_shared<ColPlan>();
     const uint64_t m = b->m;
-    const uint32_t p = b->p, n = b->n;
-    // column slices per row block
+    const uint32_t n = b->n;
+    const uint32_t p = pc;
+    P->pc = pc;
+    // the row ranges of the slices and their column spans
+    DevBuf<uint32_t> dcuts(p + 1, s);
     {
-        std::vector<uint64_t> at(p + 1);
-        for (uint32_t i = 0; i <= p; ++i) at[i] = b->cuts[i];
-        DevBuf<uint64_t> dat(p + 1, s);
         DevBuf<uint32_t> dpos(p + 1, s);
-        PGB_CUDA(cudaMemcpyAsync(dat.ptr, at.data(), (p + 1) * 8, cudaMemcpyHostToDevice, s));
-        k_gather_u32<<<1, 1024, 0, s>>>(b->rowptr.ptr, dat.ptr, p + 1, dpos.ptr);
-        PGB_CHECK_LAUNCH("k_gather_u32");
+        k_col_cuts<<<(p + 1 + 255) / 256, 256, 0, s>>>(b->rowptr.ptr, n, m, p, dcuts.ptr, dpos.ptr);
+        PGB_CHECK_LAUNCH("k_col_cuts");
         std::vector<uint32_t> pos(p + 1);
+        P->cuts.resize(p + 1);
         PGB_CUDA(cudaMemcpyAsync(pos.data(), dpos.ptr, (p + 1) * 4, cudaMemcpyDeviceToHost, s));
+        PGB_CUDA(cudaMemcpyAsync(P->cuts.data(), dcuts.ptr, (p + 1) * 4, cudaMemcpyDeviceToHost, s));
         PGB_CUDA(cudaStreamSynchronize(s));
         P->slice_lo.resize(p);
         P->slice_len.resize(p);
@@ -400,7 +422,7 @@ static std::shared_ptr<ColPlan> build_col_plan(pgb_blocks* b, cudaStream_t s) {
     k_gather_tails<<<grid_for(m), 256, 0, s>>>(b->xr.ptr, m, b->rowidx.ptr, itail.ptr);
     PGB_CHECK_LAUNCH("k_gather_tails");
     DevBuf<uint32_t> key(m, s), key2(m, s), idx(m, s), idx2(m, s);
-    k_tail_blocks<<<grid_for(m), 256, 0, s>>>(itail.ptr, m, b->cuts_d.ptr, p, key.ptr, idx.ptr);
+    k_tail_blocks<<<grid_for(m), 256, 0, s>>>(itail.ptr, m, dcuts.ptr, p, key.ptr, idx.ptr);
     PGB_CHECK_LAUNCH("k_tail_blocks");
     cub::DoubleBuffer<uint32_t> dk(key.ptr, key2.ptr), dv(idx.ptr, idx2.ptr);
     {
@@ -418,7 +440,7 @@ static std::shared_ptr<ColPlan> build_col_plan(pgb_blocks* b, cudaStream_t s) {
                                                      bt.ptr, bh.ptr);
     PGB_CHECK_LAUNCH("k_gather_block_major");
     DevBuf<uint64_t> bounds((size_t)p * (p + 1), s);
-    k_pair_bounds<<<(p * (p + 1) + 255) / 256, 256, 0, s>>>(skey, bh.ptr, m, b->cuts_d.ptr, p, bounds.ptr);
+    k_pair_bounds<<<(p * (p + 1) + 255) / 256, 256, 0, s>>>(skey, bh.ptr, m, dcuts.ptr, p, bounds.ptr);
     PGB_CHECK_LAUNCH("k_pair_bounds");
     std::vector<uint64_t> hb((size_t)p * (p + 1));
     PGB_CUDA(cudaMemcpyAsync(hb.data(), bounds.ptr, hb.size() * 8, cudaMemcpyDeviceToHost, s));
@@ -521,7 +543,7 @@ struct ColSizes {
 static ColSizes col_sizes(const pgb_blocks* b, bool pv, uint32_t threads) {
     const ColPlan& P = *std::static_pointer_cast<ColPlan>(b->col_plan);
     ColSizes z;
-    for (uint32_t i = 0; i < b->p; ++i) z.max_slice = std::max<uint64_t>(z.max_slice, P.slice_len[i]);
+    for (uint32_t i = 0; i < P.pc; ++i) z.max_slice = std::max<uint64_t>(z.max_slice, P.slice_len[i]);
     for (const ColPiece& c : P.pieces) {
         z.max_edges = std::max(z.max_edges, c.e1 - c.e0);
         z.max_items = std::max(z.max_items, c.it1 - c.it0);
@@ -541,7 +563,7 @@ void run_column_streaming(const pgb_blocks* b, bool pv, uint32_t threads, unsign
                           DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
                           cudaEvent_t ev1, uint64_t* streamed, uint32_t* npieces_out, uint32_t* loads_out) {
     const ColPlan& P = *std::static_pointer_cast<ColPlan>(b->col_plan);
-    const uint32_t p = b->p;
+    const uint32_t p = P.pc;
     npartials = 2;
     partials.alloc(2, s);
     PGB_CUDA(cudaMemsetAsync(partials.ptr, 0, 16, s));
@@ -765,17 +787,20 @@ int pgb_blocks_cache_budget(const pgb_blocks* b, int per_vertex, uint32_t slices
         if (!b || !budget) fail(PGB_E_INVAL, "NULL argument");
         if (!b->cols_offloaded) fail(PGB_E_STATE, "the columns are not offloaded");
         const ColSizes z = col_sizes(b, per_vertex != 0, 0);
-        *budget = z.fixed + (uint64_t)std::min(slices, b->p) * z.max_slice * 4;
+        const uint32_t pc = std::static_pointer_cast<ColPlan>(b->col_plan)->pc;
+        *budget = z.fixed + (uint64_t)std::min(slices, pc) * z.max_slice * 4;
     });
 }
 
-int pgb_blocks_offload_columns(pgb_blocks* b, void* stream) {
+int pgb_blocks_offload_columns(pgb_blocks* b, uint32_t slices, void* stream) {
     return guard([&] {
         if (!b) fail(PGB_E_INVAL, "blocks is NULL");
+        if (slices > 1024) fail(PGB_E_INVAL, "slices must be at most 1024");
         if (b->cols_offloaded) return;
         if (b->offloaded) fail(PGB_E_STATE, "the in-edge index is already offloaded; offload the columns first");
         cudaStream_t s = (cudaStream_t)stream;
-        std::shared_ptr<ColPlan> P = build_col_plan(b, s);
+        const uint32_t pc = std::max<uint32_t>(1, std::min<uint32_t>(slices ? slices : b->p, std::max(b->n, 1u)));
+        std::shared_ptr<ColPlan> P = build_col_plan(b, pc, s);
         {
             std::lock_guard<std::mutex> lk(b->plan_mu);
             b->run_plans.clear();

@@ -110,7 +110,7 @@ _SIGS = {
     "pgb_tc_result_variant": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "pgb_tc_result_stream": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32),
                                             ctypes.POINTER(ctypes.c_uint32)]),
-    "pgb_blocks_offload_columns": (ctypes.c_int, [_VP, _VP]),
+    "pgb_blocks_offload_columns": (ctypes.c_int, [_VP, ctypes.c_uint32, _VP]),
     "pgb_blocks_cache_budget": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]),
     "pgb_tc_result_free": (None, [_VP]),
     "pgb_tc_count_edges": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
@@ -434,11 +434,11 @@ def pgb_tc_result_variant(r: Result) -> int:
     return int(v.value)
 
 
-def pgb_blocks_offload_columns(b: Blocks, stream=None):
-    """Move the columns and a tail-block-major in-edge index of ``b`` to pinned
-    host memory (block-cache runs)."""
+def pgb_blocks_offload_columns(b: Blocks, slices: int = 0, stream=None):
+    """Move the columns (in ``slices`` row ranges, 0 = p) and a tail-range-major
+    in-edge index of ``b`` to pinned host memory (block-cache runs)."""
     st = _stream(stream) if stream is not None else b.stream
-    _check(load().pgb_blocks_offload_columns(b, st), "pgb_blocks_offload_columns")
+    _check(load().pgb_blocks_offload_columns(b, slices, st), "pgb_blocks_offload_columns")
 
 
 def pgb_blocks_cache_budget(b: Blocks, slices: int, per_vertex: bool = True) -> int:

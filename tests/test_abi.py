@@ -48,7 +48,7 @@ def test_version_and_errors_without_gpu():
     u64, u32 = ctypes.c_uint64(), ctypes.c_uint32()
     assert lib.pgb_blocks_resident_bytes(None, 1, ctypes.byref(u64)) == pgabb.PGB_E_INVAL
     assert lib.pgb_tc_result_stream(None, ctypes.byref(u64), ctypes.byref(u32), None) == pgabb.PGB_E_INVAL
-    assert lib.pgb_blocks_offload_columns(None, None) == pgabb.PGB_E_INVAL
+    assert lib.pgb_blocks_offload_columns(None, 0, None) == pgabb.PGB_E_INVAL
     assert lib.pgb_blocks_cache_budget(None, 1, 2, ctypes.byref(u64)) == pgabb.PGB_E_INVAL
     # freeing NULL handles is a no-op
     lib.pgb_graph_free(None)

@@ -120,6 +120,27 @@ def test_heavy_heads_and_key_slices_column_tier():
             assert T == oT and np.array_equal(t, ot)
 
 
+@pytest.mark.parametrize("slices", [1, 3, 17, 100000])
+def test_slice_counts_column_tier(slices):
+    """Row ranges coarser or finer than the partition's blocks (capped at n
+    and at 1024): the same counts, fewer pieces when coarser."""
+    src, dst, n = graphgen.rmat(15, 16, 41)
+    oT, ot = _oracle(src, dst, n)
+    if slices > 1024:
+        b = _blocks(src, dst, n, 8)
+        with pytest.raises(P.PgbError) as ei:
+            P.pgb_blocks_offload_columns(b, slices)
+        assert ei.value.code == P.PGB_E_INVAL
+        return
+    b = _blocks(src, dst, n, 8)
+    P.pgb_blocks_offload_columns(b, slices)
+    T, t, _, pieces, loads = _run(b, True, P.pgb_blocks_cache_budget(b, 2))
+    assert T == oT and np.array_equal(t, ot)
+    assert pieces >= 1
+    if slices == 1:
+        assert loads == 1
+
+
 def test_empty_and_edgeless_column_tier():
     e = np.zeros(0, np.uint32)
     for n in (0, 6):
