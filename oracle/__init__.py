@@ -134,7 +134,7 @@ def clean(src, dst, n: int, lib=None) -> Graph:
                        _p(offs, ctypes.c_int64), _p(adj, ctypes.c_uint32))
     if got < 0:
         raise ValueError("vertex ID out of range" if got == -1 else "out of memory")
-    return Graph(n, offs, adj[:got].copy(), lib)
+    return Graph(n, offs, adj[:got], lib)  # a view: no second copy of a large adjacency
 
 
 def tc_node_iterator(g: Graph, per_vertex: bool = True):
