@@ -453,6 +453,7 @@ __global__ void __launch_bounds__(T, 1024 / T)
             const uint32_t total = __shfl_sync(kFullMask, incl, 31);
             const uint32_t excl = incl - nq;
             const uint32_t send = sb + sl;
+            uint32_t tally = 0, tally_own = 0;  // per-vertex runs: this lane's hits for owner tally_own
             constexpr int U = kPairSlots;
             for (uint32_t r0 = 0; r0 < total; r0 += 32 * U) {
                 uint4 qv[U], qw[U];
@@ -513,16 +514,21 @@ __global__ void __launch_bounds__(T, 1024 / T)
                     }
                     cnt += h4;
                     if (PV) {
-                        // per-in-edge tally: the lanes of one owner reduce
-                        // their hits together and the lowest adds the sum to
-                        // the owner's shared slot
-                        const unsigned same = __match_any_sync(kFullMask, own[j]);
-                        const uint32_t acc = __reduce_add_sync(same, h4);
-                        if (lane == __ffs(same) - 1 && acc) atomicAdd(&s_edge[warp][own[j]], acc);
+                        // per-in-edge tally: a lane's slots belong to
+                        // non-decreasing owners, so it sums its hits in a
+                        // register and adds them to the owner's shared slot
+                        // only when its owner changes
+                        if (own[j] != tally_own) {
+                            if (tally) atomicAdd(&s_edge[warp][tally_own], tally);
+                            tally_own = own[j];
+                            tally = 0;
+                        }
+                        tally += h4;
                     }
                 }
             }
             if (PV) {
+                if (tally) atomicAdd(&s_edge[warp][tally_own], tally);
                 __syncwarp();
                 const uint32_t c = s_edge[warp][lane];
                 if (c) {
