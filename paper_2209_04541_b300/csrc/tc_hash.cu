@@ -36,6 +36,9 @@ namespace pgb {
 namespace {
 
 constexpr uint32_t kInChunkDefault = 4096;  // in-edges per item unless the caller sets one
+// At most this many in-edges per item: a key's per-vertex counter counts at
+// most one hit per in-edge of the item and is 16 bits wide.
+constexpr uint32_t kInChunkMax = 65535;
 constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr unsigned kFullMask = 0xffffffffu;
 // Table keys per work item of a CTA shape (tables stay at most half full),
@@ -286,9 +289,10 @@ __global__ void __launch_bounds__(T, 1024 / T)
     extern __shared__ uint32_t hsm[];
     // Region A: the bitmap of a bitmap-mode item, or the keys and member
     // masks of a hash-mode item; all zero between items.  Region B (per-vertex
-    // counts only): in hash mode one counter per table slot; in bitmap mode a
-    // 16-bit running popcount per pair of bitmap words, then one counter per key,
-    // indexed by the key's rank in v's sorted list.
+    // counts only) holds 16-bit counters, two per word (a counter counts at
+    // most one hit per in-edge of the item): in hash mode one per table slot;
+    // in bitmap mode, after a 16-bit running popcount per bitmap word, one per
+    // key, indexed by the key's rank in v's sorted list.
     uint32_t* regA = hsm;
     constexpr int kHThreads = T, kHWarps = T / 32;
     constexpr uint32_t kRegionA = 32u * T;           // words
@@ -352,13 +356,13 @@ __global__ void __launch_bounds__(T, 1024 / T)
         const uint32_t L = I.slots_log2, S = 1u << L;
         uint32_t* keys = regA;
         uint32_t* masks = regA + kMaxSlots;
-        uint32_t* cnts = bitmap ? regB + kRegionA / 4 : regB;
+        uint32_t* cnts = bitmap ? regB + kRegionA / 2 : regB;  // 16-bit counter i: half i & 1 of word i >> 1
         uint16_t* pre = reinterpret_cast<uint16_t*>(regB);
         if (!bitmap)
             for (uint32_t i = tid; i < S; i += kHThreads) keys[i] = kEmpty;
         if (PV) {
             const uint32_t nc = bitmap ? re - rb : S;
-            for (uint32_t i = tid; i < nc; i += kHThreads) cnts[i] = 0;
+            for (uint32_t i = tid; i < (nc + 1) / 2; i += kHThreads) cnts[i] = 0;
         }
         __syncthreads();
         // build: a singleton's list is inserted by the whole CTA (bitmap bits,
@@ -404,7 +408,7 @@ __global__ void __launch_bounds__(T, 1024 / T)
             uint32_t run = inc - own_sum;
             for (int w = 0; w < warp; ++w) run += s_wsum[w];
             for (uint32_t w = w0; w < w0 + 32 && w < nwords; ++w) {
-                if ((w & 1) == 0) pre[w >> 1] = (uint16_t)run;
+                pre[w] = (uint16_t)run;
                 run += __popc(regA[w]);
             }
             __syncthreads();
@@ -498,18 +502,14 @@ __global__ void __launch_bounds__(T, 1024 / T)
                             const uint32_t word = regA[d >> 5];
                             hit = (word >> (d & 31)) & 1u;
                             // counter index = rank of x in v's sorted list
-                            if (PV && hit) {
-                                const uint32_t w = d >> 5;
-                                h = pre[w >> 1] + ((w & 1) ? __popc(regA[w - 1]) : 0) +
-                                    __popc(word & ((1u << (d & 31)) - 1u));
-                            }
+                            if (PV && hit) h = pre[d >> 5] + __popc(word & ((1u << (d & 31)) - 1u));
                         } else {
                             h = table_find(keys, x, L);
                             hit = h != kEmpty && (single || (masks[h] & bits[j]));
                         }
                         if (hit) {
                             ++h4;
-                            if (PV) atomicAdd(&cnts[h], 1u);
+                            if (PV) atomicAdd(&cnts[h >> 1], 1u << ((h & 1) << 4));
                         }
                     }
                     cnt += h4;
@@ -552,12 +552,12 @@ __global__ void __launch_bounds__(T, 1024 / T)
             if (bitmap) {
                 // the key of rank i is the i-th entry of v's (clipped) list
                 for (uint32_t i = tid; i < re - rb; i += kHThreads) {
-                    const uint32_t c = cnts[i];
+                    const uint32_t c = (cnts[i >> 1] >> ((i & 1) << 4)) & 0xffffu;
                     if (c) atomicAdd(G.tv + __ldg(G.col + (rb + i - G.vbase)), (unsigned long long)c);
                 }
             } else {
                 for (uint32_t i = tid; i < S; i += kHThreads) {
-                    const uint32_t c = cnts[i];
+                    const uint32_t c = (cnts[i >> 1] >> ((i & 1) << 4)) & 0xffffu;
                     if (c) atomicAdd(G.tv + keys[i], (unsigned long long)c);
                 }
             }
@@ -581,9 +581,10 @@ __global__ void __launch_bounds__(T, 1024 / T)
 
 template <bool PV, int T>
 size_t hash_smem() {
-    // region B: max(slot counters, 16-bit word prefix + per-key counters)
+    // region B: max(16-bit slot counters, 16-bit word prefix + 16-bit per-key counters)
     constexpr uint32_t kRegionA = 32u * T, kMaxSlots = kRegionA / 2, kKeyCap = kMaxSlots / 2;
-    constexpr uint32_t kRegionB = (kRegionA / 4 + kKeyCap) > kMaxSlots ? (kRegionA / 4 + kKeyCap) : kMaxSlots;
+    constexpr uint32_t kRegionB =
+        (kRegionA / 2 + kKeyCap / 2) > kMaxSlots / 2 ? (kRegionA / 2 + kKeyCap / 2) : kMaxSlots / 2;
     return (size_t)(kRegionA + (PV ? kRegionB : 0)) * sizeof(uint32_t);
 }
 
@@ -608,6 +609,7 @@ void launch_shape(const HashGraph& G, const VItem* items, uint32_t nitems, cudaS
 
 uint32_t build_hash_items_in(const ItemSpace& sp, uint32_t in_chunk, cudaStream_t s, DevBuf<VItem>& items) {
     if (in_chunk == 0) in_chunk = kInChunkDefault;
+    in_chunk = std::min(in_chunk, kInChunkMax);
     const uint32_t nwin = sp.nwin;
     if (nwin == 0) {
         items.alloc(1, s);
