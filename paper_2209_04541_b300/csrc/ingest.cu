@@ -1,55 +1,60 @@
 // Graph ingest (Section 5.1 preprocessing: undirected, duplicates removed,
 // self-loops dropped) on the device.
 //
-// Each raw pair {a, b} becomes one canonical key (min << B) | max, where B
-// is the bit width of the largest vertex ID; self-loops and invalid IDs
-// become an all-ones sentinel that sorts last.  One radix sort over the 2B
-// significant bits groups equal pairs, a unique pass keeps one of each, and
-// the degree of each vertex is counted from the unique pairs.
-#include <cub/device/device_radix_sort.cuh>
+// Each raw pair {a, b} becomes its canonical pair (min, max) of B-bit IDs,
+// B the bit width of the largest vertex ID; self-loops and invalid IDs
+// become (2^B - 1, 2^B - 1), which sorts last.  A lexicographic radix sort
+// groups equal pairs, a unique pass keeps one of each as a packed key
+// (min << B) | max, and the degree of each vertex is counted from the unique
+// pairs.
 #include <cub/device/device_select.cuh>
+#include <thrust/iterator/counting_iterator.h>
+#include <thrust/iterator/transform_iterator.h>
 
 #include "internal.cuh"
+#include "sort.cuh"
 
 namespace pgb {
 
-__global__ void k_canon_keys(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst, uint64_t m,
-                             uint32_t n, uint32_t B, uint64_t sentinel, uint64_t* __restrict__ keys,
-                             int* __restrict__ err) {
+__global__ void k_canon_pairs(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst, uint64_t m,
+                              uint32_t n, uint32_t top, uint32_t* __restrict__ lo, uint32_t* __restrict__ hi,
+                              int* __restrict__ err) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         uint32_t a = src[e], b = dst[e];
-        uint64_t k = sentinel;
+        uint32_t x = top, y = top;
         if (a >= n || b >= n) {
             atomicOr(err, 1);
         } else if (a != b) {
-            uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
-            k = ((uint64_t)lo << B) | hi;
+            x = a < b ? a : b;
+            y = a < b ? b : a;
         }
-        keys[e] = k;
+        lo[e] = x;
+        hi[e] = y;
     }
 }
 
 // Row of CSR entry e: the largest u with offs[u] <= e (offs non-decreasing).
-__global__ void k_csr_keys(const int64_t* __restrict__ offs, const uint32_t* __restrict__ cols, uint32_t n,
-                           uint64_t nnz, uint32_t B, uint64_t sentinel, uint64_t* __restrict__ keys,
-                           int* __restrict__ err) {
+__global__ void k_csr_pairs(const int64_t* __restrict__ offs, const uint32_t* __restrict__ cols, uint32_t n,
+                            uint64_t nnz, uint32_t top, uint32_t* __restrict__ lo, uint32_t* __restrict__ hi,
+                            int* __restrict__ err) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
-        uint32_t lo = 0, hi = n;  // search u in [0, n): offs[u] <= e < offs[u+1]
-        while (hi - lo > 1) {
-            uint32_t mid = lo + (hi - lo) / 2;
-            if ((uint64_t)offs[mid] <= e) lo = mid; else hi = mid;
+        uint32_t l = 0, h = n;  // search u in [0, n): offs[u] <= e < offs[u+1]
+        while (h - l > 1) {
+            uint32_t mid = l + (h - l) / 2;
+            if ((uint64_t)offs[mid] <= e) l = mid; else h = mid;
         }
-        uint32_t a = lo, b = cols[e];
-        uint64_t k = sentinel;
+        uint32_t a = l, b = cols[e];
+        uint32_t x = top, y = top;
         if (b >= n) {
             atomicOr(err, 1);
         } else if (a != b) {
-            uint32_t x = a < b ? a : b, y = a < b ? b : a;
-            k = ((uint64_t)x << B) | y;
+            x = a < b ? a : b;
+            y = a < b ? b : a;
         }
-        keys[e] = k;
+        lo[e] = x;
+        hi[e] = y;
     }
 }
 
@@ -80,9 +85,18 @@ static int grid_for(uint64_t items, int threads = 256) {
     return g < 1 ? 1 : (int)g;
 }
 
-// Sort the raw keys, keep one of each, count degrees.  `keys` holds m raw
-// keys on entry; the graph takes ownership of the buffer with the result.
-static void finish_ingest(pgb_graph* g, DevBuf<uint64_t>& keys, uint64_t m, DevBuf<int>& err, cudaStream_t s) {
+// Packed key (a << B) | b of sorted pair i, read on the fly by the unique pass.
+struct PackPair {
+    const uint32_t* a;
+    const uint32_t* b;
+    uint32_t B;
+    __host__ __device__ uint64_t operator()(uint64_t i) const { return ((uint64_t)a[i] << B) | b[i]; }
+};
+
+// Sort the raw canonical pairs, keep one of each, count degrees.  `lo` and
+// `hi` hold the m raw pairs on entry (both are consumed).
+static void finish_ingest(pgb_graph* g, DevBuf<uint32_t>& lo, DevBuf<uint32_t>& hi, uint64_t m, DevBuf<int>& err,
+                          cudaStream_t s) {
     const uint32_t B = g->id_bits;
     const int end_bit = (int)(2 * B);
     if (m == 0) {
@@ -95,20 +109,24 @@ static void finish_ingest(pgb_graph* g, DevBuf<uint64_t>& keys, uint64_t m, DevB
         if (g->n) PGB_CUDA(cudaMemsetAsync(g->deg.ptr, 0, (size_t)g->n * sizeof(uint32_t), s));
         return;
     }
-    DevBuf<uint64_t> alt(m, s);
     Scratch scratch;
-    cub::DoubleBuffer<uint64_t> db(keys.ptr, alt.ptr);
-    size_t tmp = 0;
-    PGB_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp, db, (int64_t)m, 0, end_bit, s));
-    void* t = scratch.get(tmp, s);
-    PGB_CUDA(cub::DeviceRadixSort::SortKeys(t, tmp, db, (int64_t)m, 0, end_bit, s));
-    uint64_t* sorted = db.Current();
-    uint64_t* uniq = (sorted == keys.ptr) ? alt.ptr : keys.ptr;
+    DevBuf<uint64_t> uniq;
     DevBuf<int64_t> nsel(1, s);
-    size_t tmp2 = 0;
-    PGB_CUDA(cub::DeviceSelect::Unique(nullptr, tmp2, sorted, uniq, nsel.ptr, (int64_t)m, s));
-    t = scratch.get(tmp2, s);
-    PGB_CUDA(cub::DeviceSelect::Unique(t, tmp2, sorted, uniq, nsel.ptr, (int64_t)m, s));
+    {
+        DevBuf<uint32_t> lo_alt(m, s), hi_alt(m, s);
+        uint32_t *a, *b;
+        sort_pairs_lex(lo.ptr, lo_alt.ptr, hi.ptr, hi_alt.ptr, m, (int)B, s, scratch, &a, &b);
+        // free the two scratch halves before the packed output is allocated
+        if (a == lo.ptr) lo_alt.release(); else lo.release();
+        if (b == hi.ptr) hi_alt.release(); else hi.release();
+        uniq.alloc(m, s);
+        auto packed = thrust::make_transform_iterator(thrust::make_counting_iterator<uint64_t>(0), PackPair{a, b, B});
+        size_t tmp = 0;
+        PGB_CUDA(cub::DeviceSelect::Unique(nullptr, tmp, packed, uniq.ptr, nsel.ptr, (int64_t)m, s));
+        void* t = scratch.get(tmp, s);
+        PGB_CUDA(cub::DeviceSelect::Unique(t, tmp, packed, uniq.ptr, nsel.ptr, (int64_t)m, s));
+        // the sorted halves are released here, after the unique pass on s
+    }
     int64_t nu = 0;
     int herr = 0;
     PGB_CUDA(cudaMemcpyAsync(&nu, nsel.ptr, sizeof(nu), cudaMemcpyDeviceToHost, s));
@@ -119,7 +137,7 @@ static void finish_ingest(pgb_graph* g, DevBuf<uint64_t>& keys, uint64_t m, DevB
     uint64_t mu = (uint64_t)nu;
     if (mu > 0) {
         uint64_t last = 0;
-        PGB_CUDA(cudaMemcpyAsync(&last, uniq + mu - 1, sizeof(last), cudaMemcpyDeviceToHost, s));
+        PGB_CUDA(cudaMemcpyAsync(&last, uniq.ptr + mu - 1, sizeof(last), cudaMemcpyDeviceToHost, s));
         PGB_CUDA(cudaStreamSynchronize(s));
         const uint64_t sentinel = (end_bit >= 64) ? ~0ull : ((1ull << end_bit) - 1);
         if ((last & sentinel) == sentinel) --mu;
@@ -129,14 +147,10 @@ static void finish_ingest(pgb_graph* g, DevBuf<uint64_t>& keys, uint64_t m, DevB
     g->deg.alloc(g->n, s);
     if (g->n) PGB_CUDA(cudaMemsetAsync(g->deg.ptr, 0, (size_t)g->n * sizeof(uint32_t), s));
     if (mu) {
-        k_degrees<<<grid_for(mu), 256, 0, s>>>(uniq, mu, B, g->deg.ptr);
+        k_degrees<<<grid_for(mu), 256, 0, s>>>(uniq.ptr, mu, B, g->deg.ptr);
         PGB_CHECK_LAUNCH("k_degrees");
     }
-    if (uniq == keys.ptr) {
-        g->keys = std::move(keys);
-    } else {
-        g->keys = std::move(alt);
-    }
+    g->keys = std::move(uniq);
 }
 
 static pgb_graph* new_graph(uint32_t n, cudaStream_t s) {
@@ -162,9 +176,8 @@ int pgb_graph_from_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, u
         if (m > 0 && n == 0) fail(PGB_E_INVAL, "edges given for an empty vertex set");
         cudaStream_t s = (cudaStream_t)stream;
         std::unique_ptr<pgb_graph> g(new_graph(n, s));
-        const uint32_t B = g->id_bits;
-        const uint64_t sentinel = (2 * B >= 64) ? ~0ull : ((1ull << (2 * B)) - 1);
-        DevBuf<uint64_t> keys(m, s);
+        const uint32_t top = (uint32_t)((1ull << g->id_bits) - 1);  // the (top, top) pair sorts last
+        DevBuf<uint32_t> lo(m, s), hi(m, s);
         DevBuf<int> err(1, s);
         PGB_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
         if (m > 0) {
@@ -179,10 +192,10 @@ int pgb_graph_from_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, u
                 ds = hs.ptr;
                 dd = hd.ptr;
             }
-            k_canon_keys<<<grid_for(m), 256, 0, s>>>(ds, dd, m, n, B, sentinel, keys.ptr, err.ptr);
-            PGB_CHECK_LAUNCH("k_canon_keys");
+            k_canon_pairs<<<grid_for(m), 256, 0, s>>>(ds, dd, m, n, top, lo.ptr, hi.ptr, err.ptr);
+            PGB_CHECK_LAUNCH("k_canon_pairs");
         }
-        finish_ingest(g.get(), keys, m, err, s);
+        finish_ingest(g.get(), lo, hi, m, err, s);
         live_handles_add(1);
         *out = g.release();
     });
@@ -195,8 +208,7 @@ int pgb_graph_from_csr(uint32_t n, const int64_t* offs, const uint32_t* cols, in
         if (mem != PGB_MEM_HOST && mem != PGB_MEM_DEVICE) fail(PGB_E_INVAL, "bad mem kind");
         cudaStream_t s = (cudaStream_t)stream;
         std::unique_ptr<pgb_graph> g(new_graph(n, s));
-        const uint32_t B = g->id_bits;
-        const uint64_t sentinel = (2 * B >= 64) ? ~0ull : ((1ull << (2 * B)) - 1);
+        const uint32_t top = (uint32_t)((1ull << g->id_bits) - 1);  // the (top, top) pair sorts last
         DevBuf<int64_t> hoffs;
         const int64_t* doffs = offs;
         int64_t nnz = 0;
@@ -221,7 +233,7 @@ int pgb_graph_from_csr(uint32_t n, const int64_t* offs, const uint32_t* cols, in
         PGB_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
         PGB_CUDA(cudaStreamSynchronize(s));
         if (herr) fail(PGB_E_INVAL, "CSR offsets must start at 0 and be non-decreasing");
-        DevBuf<uint64_t> keys((size_t)nnz, s);
+        DevBuf<uint32_t> lo((size_t)nnz, s), hi((size_t)nnz, s);
         if (nnz > 0) {
             const uint32_t* dcols = cols;
             DevBuf<uint32_t> hcols;
@@ -230,10 +242,10 @@ int pgb_graph_from_csr(uint32_t n, const int64_t* offs, const uint32_t* cols, in
                 PGB_CUDA(cudaMemcpyAsync(hcols.ptr, cols, (size_t)nnz * 4, cudaMemcpyHostToDevice, s));
                 dcols = hcols.ptr;
             }
-            k_csr_keys<<<grid_for(nnz), 256, 0, s>>>(doffs, dcols, n, (uint64_t)nnz, B, sentinel, keys.ptr, err.ptr);
-            PGB_CHECK_LAUNCH("k_csr_keys");
+            k_csr_pairs<<<grid_for(nnz), 256, 0, s>>>(doffs, dcols, n, (uint64_t)nnz, top, lo.ptr, hi.ptr, err.ptr);
+            PGB_CHECK_LAUNCH("k_csr_pairs");
         }
-        finish_ingest(g.get(), keys, (uint64_t)nnz, err, s);
+        finish_ingest(g.get(), lo, hi, (uint64_t)nnz, err, s);
         live_handles_add(1);
         *out = g.release();
     });

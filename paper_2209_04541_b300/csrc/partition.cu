@@ -11,7 +11,6 @@
 //               block; block (i, j) occupies [block_off[ij], block_off[ij+1])
 // Because every part is a contiguous rank range, the partial list of u in
 // block A_ik is the contiguous slice of row u with columns in [c_k, c_k+1).
-#include <cub/device/device_radix_sort.cuh>
 
 #include <algorithm>
 #include <memory>
@@ -19,6 +18,7 @@
 #include <numeric>
 
 #include "internal.cuh"
+#include "sort.cuh"
 
 namespace pgb {
 
@@ -38,28 +38,18 @@ __global__ void k_invert(const uint32_t* __restrict__ perm, uint32_t n, uint32_t
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) rank[perm[r]] = r;
 }
 
-// Oriented key of each undirected edge: (low rank << B) | high rank.
-__global__ void k_orient_keys(const uint64_t* __restrict__ keys, uint64_t m, uint32_t B,
-                              const uint32_t* __restrict__ rank, uint64_t* __restrict__ okeys) {
+// Oriented endpoints of each undirected edge: its lower rank (the row) and
+// its higher rank (the column).
+__global__ void k_orient_pairs(const uint64_t* __restrict__ keys, uint64_t m, uint32_t B,
+                               const uint32_t* __restrict__ rank, uint32_t* __restrict__ row,
+                               uint32_t* __restrict__ colv) {
     const uint64_t mask = (1ull << B) - 1;
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         uint64_t k = keys[e];
         uint32_t ra = rank[(uint32_t)(k >> B)], rb = rank[(uint32_t)(k & mask)];
-        uint32_t lo = ra < rb ? ra : rb, hi = ra < rb ? rb : ra;
-        okeys[e] = ((uint64_t)lo << B) | hi;
-    }
-}
-
-// Unpack sorted oriented keys into COO rows and CSR columns.
-__global__ void k_unpack_csr(const uint64_t* __restrict__ okeys, uint64_t m, uint32_t B,
-                             uint32_t* __restrict__ rowidx, uint32_t* __restrict__ col) {
-    const uint64_t mask = (1ull << B) - 1;
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-        uint64_t k = okeys[e];
-        rowidx[e] = (uint32_t)(k >> B);
-        col[e] = (uint32_t)(k & mask);
+        row[e] = ra < rb ? ra : rb;
+        colv[e] = ra < rb ? rb : ra;
     }
 }
 
@@ -204,19 +194,6 @@ __global__ void k_wedges(const uint32_t* __restrict__ colptr, const uint32_t* __
     }
 }
 
-template <class K, class V>
-static void sort_pairs(K* keys, K* keys_alt, V* vals, V* vals_alt, uint64_t count, int end_bit, cudaStream_t s,
-                       Scratch& scratch, K** keys_out, V** vals_out) {
-    cub::DoubleBuffer<K> dk(keys, keys_alt);
-    cub::DoubleBuffer<V> dv(vals, vals_alt);
-    size_t tmp = 0;
-    PGB_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, dk, dv, (int64_t)count, 0, end_bit, s));
-    void* t = scratch.get(tmp, s);
-    PGB_CUDA(cub::DeviceRadixSort::SortPairs(t, tmp, dk, dv, (int64_t)count, 0, end_bit, s));
-    *keys_out = dk.Current();
-    *vals_out = dv.Current();
-}
-
 // Section 3.6 block-list composition with the Section 4.4 default weight
 // (edges in the block-list) and decreasing order; ties by (i, j, k).
 static std::vector<pgb_triple> make_queue(uint32_t p, const std::vector<uint64_t>& be) {
@@ -260,7 +237,7 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
         PGB_CHECK_LAUNCH("k_invert");
     }
 
-    // --- orientation: sort (low rank, high rank) keys
+    // --- orientation: sort (low rank, high rank) pairs
     b->rowptr.alloc((size_t)n + 1, s);
     // 8 spare entries: the counting kernels read rows with aligned 32-byte
     // loads, whose last load may extend up to 7 entries past the last edge
@@ -268,16 +245,16 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
     PGB_CUDA(cudaMemsetAsync(b->col.ptr + m, 0, 32, s));
     b->rowidx.alloc(m, s);
     if (m > 0) {
-        DevBuf<uint64_t> ok(m, s), oalt(m, s);
-        k_orient_keys<<<grid_for(m), 256, 0, s>>>(g->keys.ptr, m, B, rank.ptr, ok.ptr);
-        PGB_CHECK_LAUNCH("k_orient_keys");
-        cub::DoubleBuffer<uint64_t> db(ok.ptr, oalt.ptr);
-        size_t tmp = 0;
-        PGB_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp, db, (int64_t)m, 0, (int)(2 * B), s));
-        void* t = scratch.get(tmp, s);
-        PGB_CUDA(cub::DeviceRadixSort::SortKeys(t, tmp, db, (int64_t)m, 0, (int)(2 * B), s));
-        k_unpack_csr<<<grid_for(m), 256, 0, s>>>(db.Current(), m, B, b->rowidx.ptr, b->col.ptr);
-        PGB_CHECK_LAUNCH("k_unpack_csr");
+        // rows and columns are sorted in two extra arrays plus rowidx and
+        // col themselves; the result is copied over when it lands in the
+        // extra pair
+        DevBuf<uint32_t> ra(m, s), ca(m, s);
+        k_orient_pairs<<<grid_for(m), 256, 0, s>>>(g->keys.ptr, m, B, rank.ptr, ra.ptr, ca.ptr);
+        PGB_CHECK_LAUNCH("k_orient_pairs");
+        uint32_t *ro, *co;
+        sort_pairs_lex(ra.ptr, b->rowidx.ptr, ca.ptr, b->col.ptr, m, (int)B, s, scratch, &ro, &co);
+        if (ro != b->rowidx.ptr) PGB_CUDA(cudaMemcpyAsync(b->rowidx.ptr, ro, m * 4, cudaMemcpyDeviceToDevice, s));
+        if (co != b->col.ptr) PGB_CUDA(cudaMemcpyAsync(b->col.ptr, co, m * 4, cudaMemcpyDeviceToDevice, s));
         k_offsets_from_sorted<<<grid_for((uint64_t)n + 1), 256, 0, s>>>(b->rowidx.ptr, m, n, b->rowptr.ptr);
         PGB_CHECK_LAUNCH("k_offsets_from_sorted");
     } else {
