@@ -118,8 +118,10 @@ typedef struct pgb_blocks pgb_blocks;
 typedef struct pgb_tc_result pgb_tc_result;
 
 /* ------------------------------------------------------------- allocator */
-/* Device allocator hooks.  alloc returns device memory usable on `stream`
- * (NULL on failure); free releases memory obtained from alloc.  Set before
+/* Device allocator hooks.  alloc returns device memory usable on `stream`,
+ * aligned to 256 bytes as cudaMalloc's is (NULL on failure; a misaligned
+ * block is freed again and the call fails with PGB_E_INVAL); free releases
+ * memory obtained from alloc.  Set before
  * any handle exists; passing NULLs restores the default (cudaMallocAsync /
  * cudaFreeAsync).  Returns PGB_E_STATE while handles are alive. */
 typedef void* (*pgb_alloc_fn)(size_t bytes, void* stream, void* ctx);

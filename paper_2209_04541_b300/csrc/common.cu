@@ -42,6 +42,11 @@ void* dev_alloc(size_t bytes, cudaStream_t s, bool* native) {
         *native = false;
         p = g_alloc(bytes, s, g_ctx);
         if (!p) fail(PGB_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+        if (reinterpret_cast<uintptr_t>(p) & 255) {
+            // kernels read rows with aligned 16- and 32-byte loads
+            g_free(p, bytes, s, g_ctx);
+            fail(PGB_E_INVAL, "the allocator hook returned memory not aligned to 256 bytes");
+        }
         return p;
     }
     *native = true;

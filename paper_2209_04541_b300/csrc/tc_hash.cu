@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(T, 1024 / T)
             }
             // The lists of the batch, cut into aligned 8-entry pairs of quads,
             // form one sequence that the lanes share: each lane takes
-            // kPairSlots pairs per step with two 16-byte loads each, so many
+            // kPairSlots pairs per step with one 32-byte load each, so many
             // loads per lane are in flight across in-edge boundaries, and the
             // owner lookup is paid once per 8 entries.
             const uint32_t qa = sb >> 3;
@@ -478,9 +478,13 @@ __global__ void __launch_bounds__(T, 1024 / T)
                     own[j] = o;
                     qb[j] = 8 * ((lo_[j] >> 3) + (f - o_ex));
                     if (f < total) {
-                        const uint4* a = reinterpret_cast<const uint4*>(G.colu + (qb[j] - G.ubase));
-                        qv[j] = __ldg(a);
-                        qw[j] = __ldg(a + 1);
+                        // one 256-bit read-only load per pair (32-byte aligned:
+                        // qb and ubase are multiples of 8, colu is checked at launch)
+                        const uint32_t* a = G.colu + (qb[j] - G.ubase);
+                        asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                            : "=r"(qv[j].x), "=r"(qv[j].y), "=r"(qv[j].z), "=r"(qv[j].w), "=r"(qw[j].x),
+                              "=r"(qw[j].y), "=r"(qw[j].z), "=r"(qw[j].w)
+                            : "l"(a));
                     } else {
                         qv[j] = qw[j] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
                     }
@@ -662,6 +666,9 @@ int hash_grid(bool pv, int threads) {
 
 void launch_hash(const HashGraph& G, const VItem* items, uint32_t nitems, bool pv, cudaStream_t s,
                  unsigned int* cursor, unsigned long long* partials, int grid, int threads) {
+    // the pair loads read 32 aligned bytes at colu + (8k - ubase)
+    if ((reinterpret_cast<uintptr_t>(G.colu) & 31) || (G.ubase & 7))
+        fail(PGB_E_INVAL, "tail column view is not 32-byte aligned");
     PGB_CUDA(cudaMemsetAsync(cursor, 0, 4, s));
     if (threads == 256) {
         if (pv) launch_shape<true, 256>(G, items, nitems, s, cursor, partials, grid);
