@@ -494,10 +494,15 @@ __global__ void __launch_bounds__(T, 1024 / T)
                 for (int j = 0; j < U; ++j) {
                     const uint32_t xv[8] = {qv[j].x, qv[j].y, qv[j].z, qv[j].w, qw[j].x, qw[j].y, qw[j].z, qw[j].w};
                     uint32_t h4 = 0;
+                    // entries of the pair inside the owner's range [lo, hi)
+                    // as an 8-bit mask (qb > lo - 8 for every slot; a slot
+                    // past the batch has hi = 0 and an empty mask)
+                    const uint32_t va = lo_[j] > qb[j] ? lo_[j] - qb[j] : 0u;
+                    const uint32_t vb = hi_[j] < qb[j] + 8 ? min(qb[j] + 8 - hi_[j], 8u) : 0u;
+                    const uint32_t vm = (0xFFu << va) & (0xFFu >> vb);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        const uint32_t p = qb[j] + i;
-                        if (p < lo_[j] || p >= hi_[j]) continue;
+                        if (!((vm >> i) & 1u)) continue;
                         const uint32_t x = xv[i];
                         bool hit;
                         uint32_t h = 0;
