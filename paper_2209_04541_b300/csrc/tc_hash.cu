@@ -57,8 +57,10 @@ __device__ __forceinline__ uint32_t hslot(uint32_t x, uint32_t log2s) { return (
 
 __device__ __forceinline__ uint32_t ceil_log2(uint32_t x) { return x <= 1 ? 0 : 32 - __clz(x - 1); }
 
-__device__ __forceinline__ uint32_t slots_for(uint32_t keys) {
-    uint32_t l = ceil_log2(2 * keys);
+// Table slots (log2) of an item with `keys` keys: at most a quarter full
+// where the capacity (2 * keycap slots) allows, else at most half full.
+__device__ __forceinline__ uint32_t slots_for(uint32_t keys, uint32_t keycap) {
+    uint32_t l = min(ceil_log2(4 * keys), ceil_log2(2 * keycap));
     return l < 6 ? 6 : l;
 }
 
@@ -212,7 +214,7 @@ __device__ __forceinline__ VItem group_item(const ItemSpace& sp, uint32_t v0, ui
     it.in_end = sp.colptr[v0 + nv - sp.cbase];
     it.lo = 0;
     it.hi = sp.n;
-    it.slots_log2 = (uint16_t)slots_for(keys);
+    it.slots_log2 = (uint16_t)slots_for(keys, sp.keycap);
     it.clip = 0;
     it.mask = mask;
     return it;
@@ -269,7 +271,7 @@ __global__ void k_items_emit(const ItemSpace sp, uint32_t in_chunk, const uint32
                     it.hi = n;
                     it.clip = 0;
                 }
-                it.slots_log2 = (uint16_t)slots_for(min(kc, W.dp - kk * kc));
+                it.slots_log2 = (uint16_t)slots_for(min(kc, W.dp - kk * kc), kc);
                 it.mask = 1u;
                 items[out++] = it;
             }
