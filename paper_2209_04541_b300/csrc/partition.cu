@@ -147,12 +147,8 @@ __global__ void k_block_ids(const uint32_t* __restrict__ rowidx, const uint32_t*
         uint32_t b = part_of(cuts, p, rowidx[e]) * p + part_of(cuts, p, col[e]);
         if (bid) bid[e] = b;
         if (!hist) continue;
-        // neighbouring lanes hold neighbouring edges, mostly of one block:
-        // one atomic per group of lanes with equal block ids
-        const unsigned same = __match_any_sync(__activemask(), b);
-        if ((threadIdx.x & 31) != (unsigned)(__ffs(same) - 1)) continue;
-        if (use_smem) atomicAdd(&h[b], (unsigned)__popc(same));
-        else atomicAdd(&hist[b], (unsigned long long)__popc(same));
+        if (use_smem) atomicAdd(&h[b], 1u);
+        else atomicAdd(&hist[b], 1ull);
     }
     if (use_smem && hist) {
         __syncthreads();
