@@ -275,7 +275,8 @@ typedef struct {
                               PGB_E_BUDGET.  Ignored for resident blocks. */
     uint32_t chunk_edges;  /* PERSISTENT: binary-search variant: edges per
                               dequeued chunk; hash variant: in-edges per work
-                              item (0 = 4,096; larger than 65,535 counts as
+                              item (0 = 16,384 for resident blocks, 4,096 for
+                              offloaded ones; larger than 65,535 counts as
                               65,535) */
     uint32_t hash_threads; /* hash variant: threads per CTA, 128 (8 CTAs per
                               SM, bitmaps over up to 131,072 ranks) or 256 (4

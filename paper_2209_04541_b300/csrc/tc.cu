@@ -475,7 +475,7 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
     } else if (variant == PGB_VAR_HASH) {
         // middle-vertex hash variant (tc_hash.cu)
         P->threads = o.hash_threads ? (int)o.hash_threads : hash_threads(b->n);
-        P->nitems = build_hash_items(b, o.chunk_edges, P->threads, s, P->items);
+        P->nitems = build_hash_items(b, o.chunk_edges ? o.chunk_edges : kResidentInChunk, P->threads, s, P->items);
         if (P->nitems) {
             P->H = resident_hash_graph(b, P->tv.ptr);
             P->cursor.alloc(1, s);
