@@ -484,7 +484,7 @@ def main(argv=None):
     ap.add_argument("--variant", choices=["auto", "bsearch", "merge", "hash"], default="auto")
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--per-vertex", type=int, default=1)
-    ap.add_argument("--hash-threads", type=int, default=0, choices=[0, 128, 256],
+    ap.add_argument("--hash-threads", type=int, default=0, choices=[0, 128, 256, 512],
                     help="CTA shape of the hash kernel (0 = autotuned)")
     ap.add_argument("--p", type=int, default=0, help="override the workload's p")
     ap.add_argument("--no-e2e", action="store_true")
