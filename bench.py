@@ -59,6 +59,10 @@ WORKLOADS = {
                   desc="random geometric graph, n=2^22, average degree about 6; p=32"),
     "er22": dict(kind="erp", n=1 << 22, m=32 << 22, p=32, seed=1,
                  desc="Erdos-Renyi, n=2^22, 2^27 uniform pairs (average degree about 64); p=32"),
+    "rmat25": dict(kind="rmat", scale=25, ef=16, p=64, seed=1,
+                   desc="R-MAT scale 25, edge factor 16 (a,b,c,d = .57,.19,.19,.05), seeded relabel; p=64"),
+    "rmat26": dict(kind="rmat", scale=26, ef=16, p=64, seed=1,
+                   desc="R-MAT scale 26, edge factor 16 (a,b,c,d = .57,.19,.19,.05), seeded relabel; p=64"),
     "rmat27": dict(kind="rmat", scale=27, ef=16, p=64, seed=1,
                    desc="R-MAT scale 27, edge factor 16 (a,b,c,d = .57,.19,.19,.05), seeded relabel; p=64"),
 }

@@ -279,10 +279,10 @@ typedef struct {
                               offloaded ones; larger than 65,535 counts as
                               65,535) */
     uint32_t hash_threads; /* hash variant: threads per CTA, 128 (8 CTAs per
-                              SM, bitmaps over up to 131,072 ranks) or 256 (4
-                              per SM, 262,144 ranks); 0 = autotuned: 256 for
-                              graphs of at least 2^24 vertices, 128 always
-                              for column-offloaded blocks */
+                              SM, bitmaps over up to 131,072 ranks), 256 (4
+                              per SM, 262,144 ranks) or 512 (2 per SM,
+                              524,288 ranks); 0 = autotuned by vertex count
+                              (128 always for column-offloaded blocks) */
     uint32_t reserved[6];
 } pgb_tc_opts;
 

@@ -711,8 +711,8 @@ int pgb_tc_run(const pgb_blocks* b, const pgb_tc_opts* opts, void* stream, pgb_t
         if (o.mode == PGB_MODE_PLAIN && o.variant == PGB_VAR_HASH)
             fail(PGB_E_INVAL, "PLAIN mode runs the edge-wise variants (binary search, merge) only");
         if (o.order != PGB_ORDER_WEIGHT && o.order != PGB_ORDER_LOCALITY) fail(PGB_E_INVAL, "bad order");
-        if (o.hash_threads != 0 && o.hash_threads != 128 && o.hash_threads != 256)
-            fail(PGB_E_INVAL, "hash_threads must be 0, 128 or 256");
+        if (o.hash_threads != 0 && o.hash_threads != 128 && o.hash_threads != 256 && o.hash_threads != 512)
+            fail(PGB_E_INVAL, "hash_threads must be 0, 128, 256 or 512");
         if (b->offloaded && (o.mode != PGB_MODE_PERSISTENT || o.variant == PGB_VAR_BSEARCH ||
                              o.variant == PGB_VAR_MERGE))
             fail(PGB_E_STATE, "offloaded blocks run in PERSISTENT mode with the hash variant only");

@@ -46,11 +46,14 @@ constexpr unsigned kFullMask = 0xffffffffu;
 constexpr uint32_t key_capacity(int threads) { return 32u * threads / 4; }
 constexpr uint32_t bitmap_range(int threads) { return 32u * 32u * threads; }
 
-// Graphs with at least this many vertices run the 256-thread shape: its
-// wider bitmaps and larger tables serve more of the top-ranked middle
-// vertices (measured on R-MAT kernels: 256 threads is 10% faster at scale 24
-// and 27% at scale 27; 128 threads is 9% faster at scale 23 and 31% at 22).
+// Graphs with at least this many vertices run the 256-thread shape, and
+// with at least kWidestShapeVertices the 512-thread one: their wider bitmaps
+// and larger tables serve more of the top-ranked middle vertices (measured on
+// R-MAT kernels: 256 threads is 10% faster than 128 at scale 24, 128 is 9%
+// faster at scale 23; 512 is 11% faster than 256 at scale 26 and 23% at 27,
+// 256 is 9% faster at scale 25 and 33% at 24).
 constexpr uint32_t kWideShapeVertices = 1u << 24;
+constexpr uint32_t kWidestShapeVertices = 1u << 26;
 constexpr int kPairSlots = 3;          // 32-byte loads (8 entries) per lane issued together
 
 __device__ __forceinline__ uint32_t hslot(uint32_t x, uint32_t log2s) { return (x * 0x9E3779B1u) >> (32 - log2s); }
@@ -279,11 +282,12 @@ __global__ void k_items_emit(const ItemSpace sp, uint32_t in_chunk, const uint32
     }
 }
 
-// Two CTA shapes: T = 128 threads (8 CTAs per SM, a 16 KB region A: bitmaps
-// over up to 131,072 ranks) and T = 256 (4 CTAs per SM, 32 KB: 262,144
-// ranks).  Region A holds the bitmap or the table keys and masks (half of it
-// each: up to 2,048 or 4,096 slots, so 1,024 or 2,048 keys per item); thread
-// t owns words [32t, 32t + 32) of it in the bitmap prefix scan.
+// Three CTA shapes: T = 128 threads (8 CTAs per SM, a 16 KB region A:
+// bitmaps over up to 131,072 ranks), T = 256 (4 CTAs per SM, 32 KB: 262,144
+// ranks) and T = 512 (2 CTAs per SM, 64 KB: 524,288 ranks).  Region A holds
+// the bitmap or the table keys and masks (half of it each: 16T slots, so 8T
+// keys per item); thread t owns words [32t, 32t + 32) of it in the bitmap
+// prefix scan.
 template <bool PV, int T>
 __global__ void __launch_bounds__(T, 1024 / T)
     k_tc_hash(const HashGraph G, const VItem* __restrict__ items,
@@ -669,9 +673,10 @@ HashGraph resident_hash_graph(const pgb_blocks* b, unsigned long long* tv) {
     return G;
 }
 
-int hash_threads(uint32_t n) { return n >= kWideShapeVertices ? 256 : 128; }
+int hash_threads(uint32_t n) { return n >= kWidestShapeVertices ? 512 : n >= kWideShapeVertices ? 256 : 128; }
 
 int hash_grid(bool pv, int threads) {
+    if (threads == 512) return pv ? grid_of<true, 512>() : grid_of<false, 512>();
     if (threads == 256) return pv ? grid_of<true, 256>() : grid_of<false, 256>();
     return pv ? grid_of<true, 128>() : grid_of<false, 128>();
 }
@@ -682,7 +687,10 @@ void launch_hash(const HashGraph& G, const VItem* items, uint32_t nitems, bool p
     if ((reinterpret_cast<uintptr_t>(G.colu) & 31) || (G.ubase & 7))
         fail(PGB_E_INVAL, "tail column view is not 32-byte aligned");
     PGB_CUDA(cudaMemsetAsync(cursor, 0, 4, s));
-    if (threads == 256) {
+    if (threads == 512) {
+        if (pv) launch_shape<true, 512>(G, items, nitems, s, cursor, partials, grid);
+        else launch_shape<false, 512>(G, items, nitems, s, cursor, partials, grid);
+    } else if (threads == 256) {
         if (pv) launch_shape<true, 256>(G, items, nitems, s, cursor, partials, grid);
         else launch_shape<false, 256>(G, items, nitems, s, cursor, partials, grid);
     } else {

@@ -115,7 +115,7 @@ def test_heavy_heads_and_key_slices_column_tier():
     for p in (1, 4, 9):
         b = _blocks(src, dst, n, p)
         P.pgb_blocks_offload_columns(b)
-        for threads in (128, 256):
+        for threads in (128, 256, 512):
             T, t, _, _, _ = _run(b, True, P.pgb_blocks_cache_budget(b, 2), threads)
             assert T == oT and np.array_equal(t, ot)
 

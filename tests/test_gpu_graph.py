@@ -24,6 +24,7 @@ SETTINGS = [
     dict(mode=P.PGB_MODE_PERSISTENT, variant=P.PGB_VAR_MERGE),
     dict(mode=P.PGB_MODE_PERSISTENT, variant=P.PGB_VAR_HASH),
     dict(mode=P.PGB_MODE_PERSISTENT, variant=P.PGB_VAR_HASH, hash_threads=256),
+    dict(mode=P.PGB_MODE_PERSISTENT, variant=P.PGB_VAR_HASH, hash_threads=512),
     dict(mode=P.PGB_MODE_PERSISTENT, variant=P.PGB_VAR_AUTO, per_vertex=0),
 ]
 

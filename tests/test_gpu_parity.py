@@ -7,6 +7,8 @@ CSR, cuts, block sizes, queue).  Sizes span many 32-edge warp steps and
 ragged tails; edge cases cover empty inputs, self-loops only, p = 1, p = n,
 empty parts and both cut rules.
 """
+from math import comb
+
 import numpy as np
 import pytest
 
@@ -250,10 +252,10 @@ def test_hash_splits_heavy_middle_vertices():
                 assert np.array_equal(gt, want_t)
 
 
-@pytest.mark.parametrize("threads", [128, 256])
+@pytest.mark.parametrize("threads", [128, 256, 512])
 def test_hash_cta_shapes(threads):
-    """Both CTA shapes of the hash kernel (the autotuner picks 256 threads
-    only for graphs of 2^26+ vertices, so they are forced here)."""
+    """Every CTA shape of the hash kernel (the autotuner picks the wider
+    shapes only for graphs of many vertices, so they are forced here)."""
     for path in golden_files():
         src, dst, n, T, t = load_golden(path)
         for p in sorted({1, 2, n}):
@@ -274,6 +276,13 @@ def test_hash_cta_shapes(threads):
         assert gT == oT
         if pv:
             assert np.array_equal(gt, ot)
+    # K_2600: 2,599 keys per list, more than one table of the two smaller
+    # shapes holds (key slices) and within one of the 512-thread shape
+    k = 2600
+    a, b = np.triu_indices(k, 1)
+    gT, gt, _, _, _ = gpu_count(a.astype(np.uint32), b.astype(np.uint32), k, 3, variant=P.PGB_VAR_HASH,
+                                hash_threads=threads)
+    assert gT == comb(k, 3) and np.all(gt == comb(k - 1, 2))
     with pytest.raises(P.PgbError) as ei:
         gpu_count(src, dst, n, 8, variant=P.PGB_VAR_HASH, hash_threads=192)
     assert ei.value.code == P.PGB_E_INVAL

@@ -69,7 +69,7 @@ def test_rmat_streamed_matches_oracle_and_resident(per_vertex):
         assert np.array_equal(t1, ot)
 
 
-@pytest.mark.parametrize("threads", [128, 256])
+@pytest.mark.parametrize("threads", [128, 256, 512])
 def test_tiny_slots_many_chunks(threads):
     """Slots of 4096 in-edges, the largest work item: hundreds of chunks."""
     src, dst, n = graphgen.rmat(14, 16, 5)
