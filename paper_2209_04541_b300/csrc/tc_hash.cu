@@ -422,18 +422,21 @@ __global__ void __launch_bounds__(T, 1024 / T)
         if (tid == 0) prefetch();
         const uint32_t vmask = s_vmask;
         // probe: warps take batches of 32 in-edges from a shared counter (so a
-        // warp with short lists takes more batches).  Batch b is strided
-        // across the item (lane l takes in-edge b + l * nb), so the lanes of a
-        // warp hold tails from all over the item rather than 32 neighbouring
-        // ones (measured 2.6% faster at R-MAT scale 24, 4.5% without
-        // per-vertex counts).
+        // warp with short lists takes more batches).  In the 256- and
+        // 512-thread shapes batch b is strided across the item (lane l takes
+        // in-edge b + l * nb), so the lanes of a warp hold tails from all over
+        // the item rather than 32 neighbouring ones (measured 2.6% faster at
+        // R-MAT scale 24 with 256 threads, 3.5% at scale 27 with 512); the
+        // 128-thread shape keeps 32 consecutive in-edges per batch (strided
+        // was 3.4% slower at scale 23).
+        constexpr bool kStrided = T >= 256;
         const uint32_t nb = (I.in_end - I.in_begin + 31) >> 5;
         for (;;) {
             uint32_t b = 0;
             if (lane == 0) b = atomicAdd(&s_next, 1u);
             b = __shfl_sync(kFullMask, b, 0);
             if (b >= nb) break;
-            const uint32_t idx = I.in_begin + b + lane * nb;
+            const uint32_t idx = kStrided ? I.in_begin + b + lane * nb : I.in_begin + b * 32 + lane;
             uint32_t sb = 0, sl = 0, vbit = 0, e = 0;
             if (idx < I.in_end) {
                 const unsigned long long r = __ldg(G.xr + idx);
