@@ -20,11 +20,17 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   orient           pinned: each undirected edge exactly once, upward, sorted.
   cuts             pinned: closed form on hand-made prefix sums, monotone,
                    endpoints; uniform rule equals floor(t n / p).
-  block_edges      pinned: sums to |E+|, zero below the diagonal, p = 1.
+  block_edges      pinned: hand-derived p x p matrices on a 6-vertex graph
+                   (both cut rules, empty parts, a vertex on a cut), a dense
+                   brute force from the definition of the parts, sums to
+                   |E+|, zero below the diagonal.
   triples          pinned: brute-force enumeration count p(p+1)(p+2)/6 for
                    dense blocks, weight order.
-  tc_forward       pinned: equals node_iterator and brute force; triple
-                   counts sum to T and are invariant in total under p, rule.
+  tc_forward       pinned: equals node_iterator and brute force; per-triple
+                   counts equal a dense brute force that places each
+                   triangle by the definition of the parts, and
+                   hand-derived values on a 6-vertex graph.
+  tc_forward_mt    pinned: equals tc_forward (total and every t[x]).
 """
 from __future__ import annotations
 
@@ -38,22 +44,28 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_MT = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_mt = None
 
 CUT_NNZ = 0
 CUT_UNIFORM = 1
 
 
-def build(force: bool = False, out: str | None = None, defines=()) -> str:
-    """Compile the oracle with gcc (single-threaded, -O2)."""
-    target = out or _LIB
+def build(force: bool = False, out: str | None = None, defines=(), openmp: bool = False,
+          src: str | None = None) -> str:
+    """Compile the oracle with gcc (-O2): single-threaded, or with OpenMP
+    (``openmp``), which only adds ``or_tc_forward_mt``.  ``src`` compiles
+    another copy of the source (the tests' planted-mistake checks)."""
+    target = out or (_LIB_MT if openmp else _LIB)
+    source = src or _SRC
     if (not force and out is None and os.path.exists(target)
-            and os.path.getmtime(target) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(target) >= os.path.getmtime(source)):
         return target
     tmp = target + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11"] + [f"-D{d}" for d in defines]
-    cmd += ["-o", tmp, _SRC]
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11"] + (["-fopenmp"] if openmp else [])
+    cmd += [f"-D{d}" for d in defines] + ["-o", tmp, source]
     subprocess.run(cmd, check=True)
     os.replace(tmp, target)
     return target
@@ -85,6 +97,11 @@ def _bind(lib):
     lib.or_tc_forward.restype = ctypes.c_uint64
     lib.or_alg_bytes.argtypes = [ctypes.c_uint32, i64p, u32p]
     lib.or_alg_bytes.restype = ctypes.c_uint64
+    if hasattr(lib, "or_tc_forward_mt"):
+        lib.or_tc_forward_mt.argtypes = [ctypes.c_uint32, i64p, u32p, u64p, ctypes.c_int, ctypes.c_uint32]
+        lib.or_tc_forward_mt.restype = ctypes.c_uint64
+        lib.or_num_threads.argtypes = []
+        lib.or_num_threads.restype = ctypes.c_int
     return lib
 
 
@@ -98,6 +115,21 @@ def load(path: str | None = None):
             build()
             _lib = _bind(ctypes.CDLL(_LIB))
     return _lib
+
+
+def load_mt():
+    """The OpenMP build (same source compiled with -fopenmp)."""
+    global _lib_mt
+    with _lock:
+        if _lib_mt is None:
+            build(openmp=True)
+            _lib_mt = _bind(ctypes.CDLL(_LIB_MT))
+    return _lib_mt
+
+
+def num_threads() -> int:
+    """Threads the OpenMP build uses by default."""
+    return int(load_mt().or_num_threads())
 
 
 def _p(a, t):
@@ -224,6 +256,25 @@ def tc_forward(o: Oriented, p: int | None = None, c=None, per_vertex: bool = Tru
         t_orig = np.zeros(n, dtype=np.uint64)
         t_orig[o.perm] = t[:n]
     return int(tot), t_orig, (tc.reshape(p, p, p) if tc is not None else None)
+
+
+def tc_forward_mt(o: Oriented, per_vertex: bool = True, threads: int = 0, stride: int = 1):
+    """(T, t_orig or None): the forward count with its rows shared among
+    OpenMP threads (``threads`` <= 0: OpenMP's default).  With ``stride``
+    1 the counts equal ``tc_forward``'s; a larger stride counts only rows
+    0, stride, 2 stride, ... (a timing sample)."""
+    lib = load_mt()
+    n = o.n
+    t = np.zeros(max(n, 1), dtype=np.uint64) if per_vertex else None
+    tot = lib.or_tc_forward_mt(n, _p(o.rowptr, ctypes.c_int64), _p(o.col, ctypes.c_uint32),
+                               _p(t, ctypes.c_uint64) if per_vertex else None, int(threads), int(stride))
+    if tot == (1 << 64) - 1:
+        raise MemoryError("per-thread counters")
+    t_orig = None
+    if per_vertex:
+        t_orig = np.zeros(n, dtype=np.uint64)
+        t_orig[o.perm] = t[:n]
+    return int(tot), t_orig
 
 
 def alg_bytes(o: Oriented) -> int:

@@ -30,6 +30,11 @@
  *                         for each oriented edge (u,v), count common
  *                         out-neighbours; per-vertex and per-triple counts.
  *   or_tc_vertex_sample   or_tc_vertex over a list of vertices.
+ *   or_tc_forward_mt      or_tc_forward with its rows shared among OpenMP
+ *                         threads (only in the -fopenmp build); same counts.
+ *
+ * The plain build (no -fopenmp) is single-threaded and is the reference;
+ * the OpenMP build differs only in or_tc_forward_mt.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -296,17 +301,14 @@ int64_t or_triples(uint32_t p, const uint64_t* be, uint32_t* ijk, uint64_t* weig
 /* ------------------------------------------------------ forward count */
 
 /*
- * Over the oriented graph (rank space): for each oriented edge (u, v),
- * every common out-neighbour w of u and v closes the triangle u < v < w,
- * found exactly once.  Optional outputs (each may be NULL; callers zero
- * them): t_rank[x] per-vertex counts in rank space; tc[(i*p + j)*p + k]
- * per block triple, where i, j, k are the parts of u, v, w (needs p, cuts).
- * Returns the triangle count.
+ * Rows [u0, u1) of the forward count below: for each oriented edge (u, v)
+ * with u in the range, every common out-neighbour w of u and v closes the
+ * triangle u < v < w.
  */
-uint64_t or_tc_forward(uint32_t n, const int64_t* rowptr, const uint32_t* col,
-                       uint64_t* t_rank, uint32_t p, const uint32_t* cuts, uint64_t* tc) {
+static uint64_t forward_rows(uint32_t u0, uint32_t u1, const int64_t* rowptr, const uint32_t* col,
+                             uint64_t* t_rank, uint32_t p, const uint32_t* cuts, uint64_t* tc) {
     uint64_t total = 0;
-    for (uint32_t u = 0; u < n; ++u) {
+    for (uint32_t u = u0; u < u1; ++u) {
         uint32_t i = tc ? part_of(p, cuts, u) : 0;
         for (int64_t e = rowptr[u]; e < rowptr[u + 1]; ++e) {
             uint32_t v = col[e];
@@ -328,6 +330,61 @@ uint64_t or_tc_forward(uint32_t n, const int64_t* rowptr, const uint32_t* col,
     }
     return total;
 }
+
+/*
+ * Over the oriented graph (rank space): for each oriented edge (u, v),
+ * every common out-neighbour w of u and v closes the triangle u < v < w,
+ * found exactly once.  Optional outputs (each may be NULL; callers zero
+ * them): t_rank[x] per-vertex counts in rank space; tc[(i*p + j)*p + k]
+ * per block triple, where i, j, k are the parts of u, v, w (needs p, cuts).
+ * Returns the triangle count.
+ */
+uint64_t or_tc_forward(uint32_t n, const int64_t* rowptr, const uint32_t* col,
+                       uint64_t* t_rank, uint32_t p, const uint32_t* cuts, uint64_t* tc) {
+    return forward_rows(0, n, rowptr, col, t_rank, p, cuts, tc);
+}
+
+#ifdef _OPENMP
+#include <omp.h>
+/*
+ * The same forward count with its rows shared among OpenMP threads (only
+ * in the build compiled with -fopenmp).  Rows u = 0, stride, 2 stride, ...
+ * are counted (stride 1: every row, the whole count; a larger stride counts
+ * a sample of the rows, for timing).  Each thread counts its rows into a
+ * private t array of n entries; the arrays are added into t_rank at the
+ * end, so with stride 1 the result equals or_tc_forward's.  threads <= 0
+ * uses OpenMP's default.  Returns the triangle count of the counted rows,
+ * or UINT64_MAX if a private array cannot be allocated.
+ */
+uint64_t or_tc_forward_mt(uint32_t n, const int64_t* rowptr, const uint32_t* col, uint64_t* t_rank,
+                          int threads, uint32_t stride) {
+    int nt = threads > 0 ? threads : omp_get_max_threads();
+    int64_t step = stride ? (int64_t)stride : 1;
+    uint64_t** priv = (uint64_t**)calloc((size_t)nt, sizeof(uint64_t*));
+    if (!priv) return UINT64_MAX;
+    int fail = 0;
+    if (t_rank)
+        for (int k = 0; k < nt; ++k)
+            if (!(priv[k] = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t)))) fail = 1;
+    uint64_t total = 0;
+    if (!fail) {
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 64) reduction(+ : total)
+        for (int64_t u = 0; u < (int64_t)n; u += step)
+            total += forward_rows((uint32_t)u, (uint32_t)u + 1, rowptr, col,
+                                  t_rank ? priv[omp_get_thread_num()] : NULL, 0, NULL, NULL);
+        if (t_rank) {
+#pragma omp parallel for num_threads(nt) schedule(static)
+            for (int64_t v = 0; v < (int64_t)n; ++v)
+                for (int k = 0; k < nt; ++k) t_rank[v] += priv[k][v];
+        }
+    }
+    for (int k = 0; k < nt; ++k) free(priv[k]);
+    free(priv);
+    return fail ? UINT64_MAX : total;
+}
+
+int or_num_threads(void) { return omp_get_max_threads(); }
+#endif
 
 /* 4*|E+| + 4*sum_v indeg(v)*outdeg(v) + 8*(n+1): the bytes of the oriented
  * CSR that the edge-wise intersection reads when nothing is reused. */

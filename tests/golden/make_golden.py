@@ -2,17 +2,21 @@
 """Write expected values for full-size parity tests, using only the oracle.
 
 For each large synthetic workload this script generates the raw edge list
-(seeded, ``graphgen``), cleans it and counts with the oracle (plain C,
-single-threaded): the exact triangle total by the oracle's forward count,
-and t[x] for a seeded sample of vertices by the oracle's one-vertex count
-(the number of edges among the neighbours of x).  The sample holds the
-highest-degree vertices plus uniformly drawn ones.  Nothing here touches the
-CUDA library.
+(seeded, ``graphgen``), cleans it and counts with the oracle (plain C):
+- the exact triangle total T and the per-vertex counts t[x] of every vertex
+  by the oracle's forward count (its OpenMP build, whose counts equal the
+  single-threaded build's, a pinned property); t is stored as the SHA-256
+  of its n uint64 values, little-endian, in original vertex ID order;
+- t[x] for a seeded sample of vertices by the oracle's one-vertex count (the
+  number of edges among the neighbours of x), an independent second route.
+The sample holds the highest-degree vertices plus uniformly drawn ones.
+Nothing here touches the CUDA library.
 
-    python tests/golden/make_golden.py rmat20 rmat24 rmat27
+    python tests/golden/make_golden.py rmat20 rmat24 grid4096 rmat27
 
 writes ``tests/golden/full_<name>.txt``.
 """
+import hashlib
 import os
 import sys
 import time
@@ -27,13 +31,33 @@ import graphgen  # noqa: E402
 import oracle  # noqa: E402
 
 WORKLOADS = {
-    "rmat20": dict(scale=20, ef=16, seed=1),
-    "rmat24": dict(scale=24, ef=16, seed=1),
-    # too large for the oracle's total (hours single-threaded) and for its
-    # one-vertex count on the hubs: a sample of vertices of degree >= 2 and
-    # of degree-quantile vertices below the top 0.01%
-    "rmat27": dict(scale=27, ef=16, seed=1, sample_only=True),
+    "rmat20": dict(kind="rmat", scale=20, ef=16, seed=1),
+    "rmat24": dict(kind="rmat", scale=24, ef=16, seed=1),
+    # the one-vertex count on the hubs of scale 27 takes too long: its sample
+    # holds vertices of degree >= 2 and degree-quantile vertices below the
+    # top 0.01%
+    "rmat27": dict(kind="rmat", scale=27, ef=16, seed=1, hub_sample=False),
+    "grid4096": dict(kind="grid", side=4096, pct=1.0, seed=1),
 }
+
+
+def digest(t) -> str:
+    """SHA-256 of per-vertex counts as n uint64 little-endian values."""
+    return hashlib.sha256(np.ascontiguousarray(t, dtype="<u8").tobytes()).hexdigest()
+
+
+def generate(w):
+    if w["kind"] == "grid":
+        return graphgen.grid_plus_percent(w["side"], w["pct"], w["seed"])
+    return graphgen.rmat(w["scale"], w["ef"], w["seed"])
+
+
+def describe(w):
+    if w["kind"] == "grid":
+        return [f"# {w['side']}x{w['side']} 4-neighbour grid + {w['pct']}% uniform random extra edges, "
+                f"seed {w['seed']} (graphgen.grid_plus_percent).\n"]
+    return [f"# R-MAT scale {w['scale']}, edge factor {w['ef']}, a,b,c = .57,.19,.19, seed {w['seed']},\n",
+            "# seeded relabel (graphgen.rmat).\n"]
 N_TOP = 8
 N_RANDOM = 192
 
@@ -41,37 +65,40 @@ N_RANDOM = 192
 def make(name):
     w = WORKLOADS[name]
     t0 = time.time()
-    src, dst, n = graphgen.rmat(w["scale"], w["ef"], w["seed"])
+    src, dst, n = generate(w)
     g = oracle.clean(src, dst, n)
     del src, dst
     deg = g.degree()
     rng = np.random.default_rng(12345)
-    if w.get("sample_only"):
-        T = None
+    if not w.get("hub_sample", True):
         order = np.argsort(deg, kind="stable")
         live = np.flatnonzero(deg >= 2)
         quant = order[(np.array([0.9, 0.99, 0.999, 0.9995, 0.9999]) * n).astype(np.int64)]
         xs = np.unique(np.concatenate([quant, rng.choice(live, size=N_RANDOM, replace=False)])).astype(np.uint32)
     else:
-        o = oracle.orient(g)
-        T, _, _ = oracle.tc_forward(o, per_vertex=False)
-        del o
         top = np.argsort(-deg, kind="stable")[:N_TOP]
         rand = rng.choice(n, size=N_RANDOM, replace=False)
         xs = np.unique(np.concatenate([top, rand])).astype(np.uint32)
     tx = oracle.tc_vertex(g, xs)
+    m = g.m
+    o = oracle.orient(g)
+    del g
+    T, t = oracle.tc_forward_mt(o, per_vertex=True)
+    del o
+    assert np.array_equal(t[xs], tx), "forward count and one-vertex count disagree"
+    assert int(t.sum(dtype=np.uint64)) == 3 * T
     path = os.path.join(HERE, f"full_{name}.txt")
     with open(path, "w") as f:
-        f.write(f"# R-MAT scale {w['scale']}, edge factor {w['ef']}, a,b,c = .57,.19,.19, seed {w['seed']},\n")
-        f.write("# seeded relabel (graphgen.rmat).  Values from the oracle only (tests/golden/make_golden.py):\n")
-        f.write("# T (when present) = oracle forward count; t[x] = oracle one-vertex count for the listed x (the\n")
-        f.write("# number of triangles containing x, PGAbB Section 3.6 definition).\n")
-        f.write(f"n {n}\nm {g.m}\n")
-        if T is not None:
-            f.write(f"T {T}\n")
+        for line in describe(w):
+            f.write(line)
+        f.write("# Values from the oracle only (tests/golden/make_golden.py): T = oracle forward count;\n")
+        f.write("# t_sha256 = SHA-256 of all n per-vertex counts (uint64 little-endian, original IDs) from the\n")
+        f.write("# same count; x lines: t[x] by the oracle's one-vertex count (the number of triangles\n")
+        f.write("# containing x, PGAbB Section 3.6 definition).\n")
+        f.write(f"n {n}\nm {m}\nT {T}\nt_sha256 {digest(t)}\n")
         for x, c in zip(xs.tolist(), tx.tolist()):
             f.write(f"x {x} {c}\n")
-    print(f"{name}: n={n} m={g.m} T={T} sample={len(xs)} in {time.time() - t0:.0f} s -> {path}")
+    print(f"{name}: n={n} m={m} T={T} sample={len(xs)} in {time.time() - t0:.0f} s -> {path}", flush=True)
 
 
 def load(name):
@@ -85,6 +112,8 @@ def load(name):
             if tag == "x":
                 out["x"].append(int(rest[0]))
                 out["t"].append(int(rest[1]))
+            elif tag == "t_sha256":
+                out[tag] = rest[0]
             else:
                 out[tag] = int(rest[0])
     out["x"] = np.array(out["x"], dtype=np.int64)

@@ -3,6 +3,7 @@ itself (hand-derived fixtures, brute force over all triples, closed forms,
 dense matrix powers, invariants).  The paper prints no triangle counts for
 any graph, so no value here comes from the paper; all come from mathematics.
 """
+import os
 from math import comb
 
 import numpy as np
@@ -354,3 +355,180 @@ def test_grid_extra_percent_count():
     gb = oracle.clean(src[:base], dst[:base], n)
     assert oracle.tc_node_iterator(gb, per_vertex=False)[0] == 0
     assert T >= 0
+
+
+# ------------------------------------------- block attribution pins
+# The p x p block sizes (Section 4.3: A_ij holds the oriented edges whose
+# tail lies in part i and head in part j) and the per-triple counts
+# (Section 3.6 block-list composition: a triangle a < b < c in rank order
+# belongs to the triple (part a, part b, part c)) are fixed here by values
+# derived by hand and by a brute force that places every edge and triangle
+# from the definition of the parts: part t = the rank range [c_t, c_t+1).
+
+# The oriented 6-vertex graph of test_cuts_closed_forms: edges 0->1, 0->2,
+# 0->3, 0->4, 2->3, 2->4, 3->4, 3->5; its triangles are 023, 024, 034, 234.
+HAND_ROWPTR = np.array([0, 4, 4, 6, 8, 8, 8], dtype=np.int64)
+HAND_COL = np.array([1, 2, 3, 4, 3, 4, 4, 5], dtype=np.uint32)
+
+# (p, rule) -> (cuts, nonzero block sizes {(i, j): count}, nonzero triple counts)
+HAND_PARTITIONS = {
+    # parts {0}, {1..5}: vertex 1 sits exactly on the cut c_1 = 1
+    (2, oracle.CUT_NNZ): ([0, 1, 6], {(0, 1): 4, (1, 1): 4}, {(0, 1, 1): 3, (1, 1, 1): 1}),
+    # parts {0}, {} (empty), {1, 2}, {3, 4, 5}: vertex 1 on the double cut c_1 = c_2 = 1
+    (4, oracle.CUT_NNZ): ([0, 1, 1, 3, 6], {(0, 2): 2, (0, 3): 2, (2, 3): 2, (3, 3): 2},
+                          {(0, 2, 3): 2, (0, 3, 3): 1, (2, 3, 3): 1}),
+    # parts {0, 1, 2}, {3, 4, 5}
+    (2, oracle.CUT_UNIFORM): ([0, 3, 6], {(0, 0): 2, (0, 1): 4, (1, 1): 2}, {(0, 0, 1): 2, (0, 1, 1): 2}),
+    # parts {0}, {1, 2}, {3}, {4, 5}
+    (4, oracle.CUT_UNIFORM): ([0, 1, 3, 4, 6], {(0, 1): 2, (0, 2): 1, (0, 3): 1, (1, 2): 1, (1, 3): 1,
+                                                (2, 3): 2},
+                              {(0, 1, 2): 1, (0, 1, 3): 1, (0, 2, 3): 1, (1, 2, 3): 1}),
+}
+
+
+def hand_attribution(lib, p, rule):
+    o = oracle.Oriented(6, np.arange(6, dtype=np.uint32), np.arange(6, dtype=np.uint32),
+                        HAND_ROWPTR, HAND_COL, lib)
+    c = oracle.cuts(o, p, rule)
+    be = oracle.block_edges(o, p, c)
+    T, t, tc = oracle.tc_forward(o, p, c, per_vertex=True)
+    return c, be, T, t, tc
+
+
+def dense_from(entries, shape):
+    out = np.zeros(shape, dtype=np.uint64)
+    for idx, v in entries.items():
+        out[idx] = v
+    return out
+
+
+@pytest.mark.parametrize("p,rule", sorted(HAND_PARTITIONS))
+def test_block_edges_and_triples_hand_derived(p, rule):
+    want_cuts, want_be, want_tc = HAND_PARTITIONS[(p, rule)]
+    c, be, T, t, tc = hand_attribution(oracle.load(), p, rule)
+    assert c.tolist() == want_cuts
+    assert np.array_equal(be, dense_from(want_be, (p, p)))
+    assert np.array_equal(tc, dense_from(want_tc, (p, p, p)))
+    assert T == 4
+    assert t.tolist() == [3, 0, 3, 3, 3, 0]  # 0: 023 024 034; 2: 023 024 234; 3: 023 034 234; 4: 024 034 234
+
+
+def part_by_definition(cuts, r):
+    """The unique t with c_t <= r < c_t+1."""
+    hits = [t for t in range(len(cuts) - 1) if cuts[t] <= r < cuts[t + 1]]
+    assert len(hits) == 1
+    return hits[0]
+
+
+def attribution_by_definition(src, dst, n, rank, cuts):
+    """Block sizes and per-triple counts from the definitions alone: every
+    undirected edge {a, b} is the oriented edge from the lower to the higher
+    rank; every triangle is placed by the parts of its three ranks in
+    ascending order."""
+    p = len(cuts) - 1
+    part = [part_by_definition(cuts, r) for r in range(n)]
+    adj = np.zeros((n, n), dtype=bool)
+    for a, b in zip(src.tolist(), dst.tolist()):
+        if a != b:
+            adj[rank[a], rank[b]] = adj[rank[b], rank[a]] = True
+    be = np.zeros((p, p), dtype=np.uint64)
+    for x in range(n):
+        for y in range(x + 1, n):
+            if adj[x, y]:
+                be[part[x], part[y]] += 1
+    tc = np.zeros((p, p, p), dtype=np.uint64)
+    for x in range(n):
+        for y in range(x + 1, n):
+            if not adj[x, y]:
+                continue
+            for z in range(y + 1, n):
+                if adj[x, z] and adj[y, z]:
+                    tc[part[x], part[y], part[z]] += 1
+    return be, tc
+
+
+def attribution_cases():
+    """(name, src, dst, n, cut list or rule) cases: random dense graphs under
+    both rules, a hub-heavy graph whose nnz cuts repeat (empty parts), and
+    hand-set cuts with empty parts and vertices exactly on cuts."""
+    cases = []
+    for seed in range(3):
+        rng = np.random.default_rng(500 + seed)
+        n = int(rng.integers(18, 34))
+        keep = rng.random((n, n)) < rng.uniform(0.25, 0.6)
+        s, d = np.nonzero(np.triu(keep, 1))
+        cases.append((f"dense{seed}", s.astype(np.uint32), d.astype(np.uint32), n))
+    # a star plus a clique: one vertex of high degree, so nnz cuts pile up
+    edges = [(0, k) for k in range(1, 20)] + complete(6)
+    s, d = edges_to_arrays(edges)
+    cases.append(("star_clique", s, d, 20))
+    return cases
+
+
+@pytest.mark.parametrize("case", attribution_cases(), ids=lambda c: c[0])
+@pytest.mark.parametrize("p", [2, 3, 4, 7])
+@pytest.mark.parametrize("rule", [oracle.CUT_NNZ, oracle.CUT_UNIFORM, "hand"])
+def test_block_attribution_brute_force(case, p, rule):
+    _, src, dst, n = case
+    o = oracle.orient(oracle.clean(src, dst, n))
+    if rule == "hand":
+        # empty parts (repeated cuts) and cuts at both ends of the rank range
+        inner = sorted(np.random.default_rng(p).choice(np.arange(0, n + 1), size=p - 1).tolist())
+        inner[0] = 0
+        c = np.array([0] + inner + [n], dtype=np.uint32)
+    else:
+        c = oracle.cuts(o, p, rule)
+    be = oracle.block_edges(o, p, c)
+    _, _, tc = oracle.tc_forward(o, p, c, per_vertex=False)
+    want_be, want_tc = attribution_by_definition(src, dst, n, o.rank, c.tolist())
+    assert np.array_equal(be, want_be)
+    assert np.array_equal(tc, want_tc)
+
+
+def test_planted_cut_boundary_mistake_is_caught(tmp_path):
+    """A copy of the oracle with the part lookup shifted by one at a cut
+    boundary (a vertex exactly on c_t+1 kept in part t) must fail the pins
+    above: the hand-derived matrices and the brute force."""
+    src_text = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    good, bad = "cuts[t + 1] <= r", "cuts[t + 1] < r"
+    assert src_text.count(good) == 1
+    mutated = tmp_path / "oracle_mutated.c"
+    mutated.write_text(src_text.replace(good, bad))
+    lib = oracle.load(oracle.build(out=str(tmp_path / "liboracle_mutated.so"), src=str(mutated)))
+    failures = 0
+    for (p, rule), (want_cuts, want_be, want_tc) in HAND_PARTITIONS.items():
+        c, be, _, _, tc = hand_attribution(lib, p, rule)
+        if not (np.array_equal(be, dense_from(want_be, (p, p)))
+                and np.array_equal(tc, dense_from(want_tc, (p, p, p)))):
+            failures += 1
+    assert failures == len(HAND_PARTITIONS), "every hand case has a vertex on a cut"
+    _, src, dst, n = attribution_cases()[0]
+    g = oracle.clean(src, dst, n, lib=lib)
+    o = oracle.orient(g)
+    c = oracle.cuts(o, 4)
+    want_be, _ = attribution_by_definition(src, dst, n, o.rank, c.tolist())
+    assert not np.array_equal(oracle.block_edges(o, 4, c), want_be)
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_forward_mt_equals_forward(threads):
+    src, dst, n = graphgen.rmat(12, 16, 9)
+    o = oracle.orient(oracle.clean(src, dst, n))
+    T, t, _ = oracle.tc_forward(o)
+    T2, t2 = oracle.tc_forward_mt(o, threads=threads)
+    assert T2 == T and np.array_equal(t2, t)
+    # a row sample counts exactly the triangles whose lowest-ranked vertex
+    # is a sampled row
+    T3, t3 = oracle.tc_forward_mt(o, threads=threads, stride=5)
+    assert int(t3.sum(dtype=np.uint64)) == 3 * T3 and 0 < T3 < T
+    assert T3 == sum(_row_count(o, u) for u in range(0, n, 5))
+
+
+def _row_count(o, u):
+    """Triangles u < v < w found from row u, by set intersection in Python."""
+    row = o.col[o.rowptr[u]:o.rowptr[u + 1]].tolist()
+    s = set(row)
+    cnt = 0
+    for v in row:
+        cnt += len(s.intersection(o.col[o.rowptr[v]:o.rowptr[v + 1]].tolist()))
+    return cnt
