@@ -13,7 +13,7 @@
  *   build the block-triple queue        (Section 3.6 block-list
  *                                        composition; Section 4.4 weights,
  *                                        decreasing order)
- *   run the device kernel per triple    (Section 3.6, Listing "tc-dev":
+ *   run the device kernel per triple    (Section 3.6, Listing 5:
  *                                        per edge of the first block,
  *                                        intersect partial lists)
  *   reduce                              (Section 3.3 reduce_dev)
@@ -80,8 +80,8 @@ extern "C" {
 #define PGB_MODE_PERSISTENT 1
 
 /* ------------------------------------------------- intersection variants */
-/* Section 3.6: "list or hashmap-based" intersection.  Every variant returns
- * the same integers; the choice only changes speed.
+/* Section 3.6 lets the intersection run over sorted lists or a hash map.
+ * Every variant returns the same integers; the choice only changes speed.
  * PGB_VAR_AUTO:    chosen by the autotuner (below).
  * PGB_VAR_BSEARCH: each element of the shorter list is binary-searched in
  *                  the longer one; work is flattened across a warp.
@@ -420,28 +420,33 @@ void pgb_server_destroy(pgb_server* s);
  * allocation, and latency-critical loops that cannot take the device-wide
  * synchronisation cudaMalloc / cudaFree may cause.  It allocates nothing:
  * no cudaMalloc, no cudaFree, no allocator callback.  Its working memory (a
- * work cursor, per-CTA partial counts and a per-vertex accumulator of
- * PGB_NOALLOC_MAX_VERTICES entries, about 8 MiB) is one fixed device array
- * inside the library, held on every GPU that loads the library until the
- * process exits.
+ * work cursor, per-CTA partial counts, a per-vertex accumulator of
+ * PGB_NOALLOC_MAX_VERTICES entries and a bitmap of as many bits, about
+ * 8.1 MiB) is one fixed device array inside the library, held on every GPU
+ * that loads the library until the process exits.
  *
  * Input: an already degree-ordered, upper-oriented graph in device memory
  * (e.g. from PGB_EXPORT_ROWPTR narrowed to uint32 and PGB_EXPORT_COL):
- *   rowptr uint32[n+1] with rowptr[0] = 0 and rowptr[n] = m; col uint32[m]
- *   with row u listing its out-neighbours, all > u, ascending;
- *   perm   uint32[n] rank -> original ID, or NULL to index output by rank.
+ *   rowptr uint32[n+1] with rowptr[0] = 0, rowptr[n] = m, non-decreasing;
+ *   col    uint32[m] with row u listing its out-neighbours, each > u and
+ *          < n, strictly ascending;
+ *   perm   uint32[n] rank -> original ID (a permutation of 0..n-1), or NULL
+ *          to index output by rank (perm is only read when per_vertex is
+ *          not NULL).
  * Output (device memory, written, not accumulated): total uint64[1];
  *   per_vertex uint64[n] or NULL.
  * Counts equal those of pgb_tc_run on the same graph.
- * The call returns after the work on `stream` has finished.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress) for
- * that device; make that first call before any stream capture begins.
- * Every call on a device shares the one array and clears what it needs at
- * the start, so calls whose work overlaps on the GPU (other streams or
- * threads) race and give wrong counts: serialise them.
- * Errors: PGB_E_INVAL (n > PGB_NOALLOC_MAX_VERTICES, NULL pointers,
- * malformed offsets, columns or perm, detected on the device),
- * PGB_E_OVERFLOW (m >= 2^32), PGB_E_CUDA. */
+ * The call checks every rule above on the device (before it returns, with
+ * reads that stay inside the arrays) and fails with PGB_E_INVAL naming the
+ * rule that was broken; outputs are then undefined.  It returns after its
+ * work on `stream` has finished.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) for that device; make that
+ * first call before any stream capture begins.  Every call on a device
+ * shares the one array and clears what it needs at the start, so calls
+ * whose work overlaps on the GPU (other streams or threads) race and give
+ * wrong counts: serialise them.
+ * Errors: PGB_E_INVAL (n > PGB_NOALLOC_MAX_VERTICES, NULL pointers, a
+ * broken input rule), PGB_E_OVERFLOW (m >= 2^32), PGB_E_CUDA. */
 #define PGB_NOALLOC_MAX_VERTICES (1u << 20)
 int pgb_tc_count_oriented_noalloc(uint32_t n, uint64_t m, const uint32_t* rowptr, const uint32_t* col,
                                   const uint32_t* perm, unsigned long long* total,

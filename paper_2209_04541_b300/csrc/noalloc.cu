@@ -32,17 +32,25 @@ constexpr int kMaxDevices = 64;
 struct NoAllocScratch {
     unsigned long long tv[kNoAllocMaxVertices];   // per-vertex counts by rank
     unsigned long long partials[kNoAllocMaxCtas]; // per-CTA totals
+    unsigned int seen[kNoAllocMaxVertices / 32];  // perm targets written (one bit each)
     unsigned long long cursor;                    // next edge chunk
-    unsigned int error;                           // bit 0: malformed input seen
+    unsigned int error;                           // error bits (kNaErr*)
 };
+
+// Error bits: which rule of the input contract a call's graph broke.
+constexpr unsigned kNaErrRange = 1u;     // an offset, column or perm entry out of range
+constexpr unsigned kNaErrOrder = 2u;     // offsets decreasing, or a row not strictly ascending above u
+constexpr unsigned kNaErrPerm = 4u;      // perm maps two ranks to one vertex
 
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
-// Zero what must start at zero: the first n accumulator entries, the
-// cursor and the error word (partials are overwritten, not accumulated).
+// Zero what must start at zero: the first n accumulator entries, the perm
+// bitmap's first ceil(n / 32) words, the cursor and the error word
+// (partials are overwritten, not accumulated).
 __global__ void k_na_clear(NoAllocScratch* __restrict__ s, uint32_t n) {
     uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) s->tv[i] = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (n + 31) / 32; i += stride) s->seen[i] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         s->cursor = 0;
         s->error = 0;
@@ -119,7 +127,7 @@ __global__ void __launch_bounds__(kNaThreads)
                         if (ll == 0) sl = 0;
                     }
                 }
-                if (!ok) atomicOr(&s->error, 1u);
+                if (!ok) atomicOr(&s->error, kNaErrRange);
             }
             uint32_t incl = sl;
 #pragma unroll
@@ -198,21 +206,53 @@ __global__ void k_na_reduce(const NoAllocScratch* __restrict__ s, int nparts,
 }
 
 // Per-vertex counts out of the accumulator: by original ID through perm, or
-// by rank when perm is NULL.  Out-of-range perm entries set the error bit.
+// by rank when perm is NULL.  An out-of-range perm entry, or one that names
+// a vertex another rank already took, sets an error bit and is not written.
 __global__ void k_na_scatter(NoAllocScratch* __restrict__ s, uint32_t n, const uint32_t* __restrict__ perm,
                              unsigned long long* __restrict__ out) {
     uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
         uint32_t dst = perm ? perm[r] : r;
-        if (dst < n) out[dst] = s->tv[r];
-        else atomicOr(&s->error, 1u);
+        if (dst >= n) {
+            atomicOr(&s->error, kNaErrRange);
+            continue;
+        }
+        if (perm) {
+            const unsigned bit = 1u << (dst & 31);
+            if (atomicOr(&s->seen[dst >> 5], bit) & bit) {
+                atomicOr(&s->error, kNaErrPerm);
+                continue;
+            }
+        }
+        out[dst] = s->tv[r];
     }
 }
 
 // Header checks: rowptr[0] == 0 and rowptr[n] == m.
 __global__ void k_na_check_ends(const uint32_t* __restrict__ rowptr, uint32_t n, uint32_t m,
                                 NoAllocScratch* __restrict__ s) {
-    if (rowptr[0] != 0 || rowptr[n] != m) atomicOr(&s->error, 1u);
+    if (rowptr[0] != 0 || rowptr[n] != m) atomicOr(&s->error, kNaErrRange);
+}
+
+// The ordering contract: offsets non-decreasing (one thread per row), and
+// every column above its row and strictly above the previous entry of the
+// same row (one thread per edge; with non-decreasing offsets the row found
+// by binary search is the edge's own).  Reads stay inside rowptr[0..n] and
+// col[0..m); a broken rule only sets an error bit.
+__global__ void k_na_check_order(const uint32_t* __restrict__ rowptr, const uint32_t* __restrict__ col,
+                                 uint32_t n, uint32_t m, NoAllocScratch* __restrict__ s) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    unsigned bad = 0;
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride)
+        if (__ldg(rowptr + u) > __ldg(rowptr + u + 1)) bad |= kNaErrOrder;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const uint32_t u = na_row_of(rowptr, n, e);
+        const uint32_t v = __ldg(col + e);
+        if (v >= n) bad |= kNaErrRange;
+        if (v <= u) bad |= kNaErrOrder;
+        if (e > __ldg(rowptr + u) && __ldg(col + e - 1) >= v) bad |= kNaErrOrder;
+    }
+    if (bad) atomicOr(&s->error, bad);
 }
 
 std::mutex g_na_mu;
@@ -272,6 +312,10 @@ int pgb_tc_count_oriented_noalloc(uint32_t n, uint64_t m, const uint32_t* rowptr
         if (n > 0) {
             k_na_check_ends<<<1, 1, 0, s>>>(rowptr, n, (uint32_t)m, sc);
             PGB_CHECK_LAUNCH("k_na_check_ends");
+            const uint64_t work = std::max<uint64_t>(n, m);
+            k_na_check_order<<<(uint32_t)std::min<uint64_t>((work + 255) / 256, 4096), 256, 0, s>>>(
+                rowptr, col, n, (uint32_t)m, sc);
+            PGB_CHECK_LAUNCH("k_na_check_order");
         }
         if (m > 0) {
             if (pv) k_na_count<true><<<grid, kNaThreads, 0, s>>>(n, (uint32_t)m, rowptr, col, sc);
@@ -289,7 +333,13 @@ int pgb_tc_count_oriented_noalloc(uint32_t n, uint64_t m, const uint32_t* rowptr
         unsigned int herr = 0;
         PGB_CUDA(cudaMemcpyAsync(&herr, &sc->error, sizeof(herr), cudaMemcpyDeviceToHost, s));
         PGB_CUDA(cudaStreamSynchronize(s));
-        if (herr) fail(PGB_E_INVAL, "malformed oriented graph (offsets, columns or perm out of range)");
+        if (herr) {
+            std::string why;
+            if (herr & kNaErrRange) why += " offsets, columns or perm out of range;";
+            if (herr & kNaErrOrder) why += " offsets decreasing, or a row not strictly ascending above its vertex;";
+            if (herr & kNaErrPerm) why += " perm maps two ranks to one vertex;";
+            fail(PGB_E_INVAL, "malformed oriented graph:" + why);
+        }
     });
 }
 

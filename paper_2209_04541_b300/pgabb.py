@@ -506,7 +506,16 @@ def pgb_tc_count_oriented_noalloc(n: int, m: int, rowptr, col, perm, total, per_
     None), ``total`` (uint64[1]) and ``per_vertex`` (uint64[n] or None) are
     CUDA tensors; results are written into ``total`` and ``per_vertex``.
     For callers that may not allocate device memory during the call; see
-    include/pgabb.h for the limits and the sharing rules."""
+    include/pgabb.h for the limits and the sharing rules.  Tensors shorter
+    than ``n`` and ``m`` require raise ValueError before the library is
+    called."""
+    for name, x, need in (("rowptr", rowptr, n + 1), ("col", col, m), ("perm", perm, n), ("total", total, 1),
+                          ("per_vertex", per_vertex, n)):
+        if x is None:
+            continue
+        have = x.size if isinstance(x, np.ndarray) else x.numel()
+        if have < need:
+            raise ValueError(f"{name} holds {have} entries; n = {n}, m = {m} need at least {need}")
     args = []
     for x, dt in ((rowptr, np.uint32), (col, np.uint32), (perm, np.uint32), (total, np.uint64),
                   (per_vertex, np.uint64)):

@@ -92,3 +92,23 @@ def test_server_opts_and_admission_estimate():
     st = ctypes.c_int()
     assert lib.pgb_server_poll(None, 1, ctypes.byref(st)) == pgabb.PGB_E_INVAL
     lib.pgb_server_destroy(None)
+
+
+@pytest.mark.parametrize("short", ["rowptr", "col", "perm", "total", "per_vertex"])
+def test_noalloc_binding_rejects_short_arrays_without_calling_the_library(short, monkeypatch):
+    """Arrays shorter than n and m require are refused in the binding, so a
+    wrong n or m never turns into device reads or writes past an array."""
+    import numpy as np
+
+    def no_library():
+        raise AssertionError("the library was reached")
+
+    monkeypatch.setattr(pgabb, "load", no_library)
+    n, m = 6, 8
+    sizes = {"rowptr": n + 1, "col": m, "perm": n, "total": 1, "per_vertex": n}
+    sizes[short] -= 1
+    arrs = {k: np.zeros(v, dtype=np.uint64 if k in ("total", "per_vertex") else np.uint32)
+            for k, v in sizes.items()}
+    with pytest.raises(ValueError, match=short):
+        pgabb.pgb_tc_count_oriented_noalloc(n, m, arrs["rowptr"], arrs["col"], arrs["perm"], arrs["total"],
+                                            arrs["per_vertex"])
