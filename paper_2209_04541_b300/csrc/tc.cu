@@ -1,4 +1,4 @@
-// Triangle counting over block tuples (PGAbB Section 3.6, Listing "tc-dev")
+// Triangle counting over block tuples (PGAbB Section 3.6, Listing 5)
 // and its reduction (Section 3.3 reduce_dev).
 //
 // A block tuple is (A_ij, A_i[k0..k1], A_j[k0..k1]) with the third index a

@@ -1,7 +1,8 @@
 // Middle-vertex shared-memory hash variant of the block-tuple kernel
-// (PGAbB Section 3.6: "list or hashmap-based intersection").
+// (PGAbB Section 3.6, which allows the intersection to be done over sorted
+// lists or through a hash map).
 //
-// Listing "tc-dev" loops over u, then over v in N(u), intersecting u's and
+// The TC device kernel (Section 3.6, Listing 5) loops over u, then over v in N(u), intersecting u's and
 // v's partial lists.  This variant interchanges the two outer loops: a CTA
 // takes a middle vertex v (or a group of up to 32 consecutive middle
 // vertices), puts v's partial list N+(v) ∩ [lo, hi) into a shared-memory
