@@ -13,10 +13,19 @@ partitioning are inside the timed step).
 ``e2e``:   the same through the one-call C ABI entry with pinned host
            buffers (host-to-device copy of the raw edges and device-to-host
            copy of the total and per-vertex counts inside the timed call).
-``roofline``: the counting kernel's algorithmic bytes (4|E+| + 4 sum_v
-           indeg(v) outdeg(v) + 8(n+1)) over its device time, against the
-           measured HBM copy bandwidth.
-``cpu_baseline``: the oracle (single-threaded C) on a bounded sample.
+``roofline``: the counting kernel's own algorithmic bytes over its device
+           time, against the measured HBM copy bandwidth.  For the
+           middle-vertex kernel that is 4 probes + 12 |E+| (every looked-up
+           entry of the tails' rows plus the in-edge index); for the
+           edge-wise kernels 4|E+| + 4 sum_v indeg(v) outdeg(v) + 8(n+1).
+           The second formula is also given for the middle-vertex kernel,
+           as ``edgewise_bound``: it charges a re-read of v's list per
+           in-edge, which that kernel serves from shared memory, so it is a
+           bound for the edge-wise method, not a bandwidth fraction.
+``cpu_baseline``: the oracle on the same workload: its clean, degree order
+           and orientation single-threaded in full, and its forward count
+           on a stride sample of the rows with every host core (OpenMP
+           build), scaled to the whole graph; the single-core figure beside.
 
 With ``--impl reference`` the oracle itself is the measured arm (rank 0
 only).  Under torchrun each rank runs an independent replica (the path
@@ -65,15 +74,25 @@ WORKLOADS = {
                    desc="R-MAT scale 26, edge factor 16 (a,b,c,d = .57,.19,.19,.05), seeded relabel; p=64"),
     "rmat27": dict(kind="rmat", scale=27, ef=16, p=64, seed=1,
                    desc="R-MAT scale 27, edge factor 16 (a,b,c,d = .57,.19,.19,.05), seeded relabel; p=64"),
+    "grid4096_u_rmat22": dict(kind="union", members=("grid4096", "rmat22"), p=32, seed=1,
+                              desc="disjoint union of the 4096x4096 grid + 1% and R-MAT scale 22 ef16 (the shape "
+                                   "of a serve batch: flat and skewed graphs in one partition); p=32"),
 }
 
-# CPU-baseline sample: the oracle's whole pipeline on the same generator
-# family at a size it finishes in about 20 s single-threaded.
-CPU_SAMPLE = dict(kind="rmat", scale=20, ef=16, p=16, seed=1)
+# Reference arm: the oracle's whole pipeline per step at a size it finishes
+# in about a second single-threaded.
 REF_SAMPLE = dict(kind="rmat", scale=17, ef=16, p=8, seed=1)
 
 
 def generate(w, out=None):
+    if w["kind"] == "union":
+        srcs, dsts, base = [], [], 0
+        for name in w["members"]:
+            s_, d_, n_ = generate(WORKLOADS[name])
+            srcs.append(s_ + np.uint32(base))
+            dsts.append(d_ + np.uint32(base))
+            base += n_
+        return np.concatenate(srcs), np.concatenate(dsts), base
     if w["kind"] == "rmat":
         return graphgen.rmat(w["scale"], w["ef"], w["seed"], out=out)
     if w["kind"] == "grid":
@@ -198,12 +217,50 @@ def oracle_pipeline(w):
     return time.perf_counter() - t0, g.m, T
 
 
-def cpu_baseline():
-    secs, m, _ = oracle_pipeline(CPU_SAMPLE)
-    return {"value": m / secs, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": "oracle (single-threaded C) clean+degree order+orient+partition+count with per-vertex "
-                      "counts on R-MAT scale 20 ef16 (same generator, 1/16 of the scale-24 vertices): "
-                      f"{m} unique edges in {secs:.2f} s"}
+def cpu_baseline(src, dst, n, target_s=12.0):
+    """The oracle on the benchmark's own graph (a bounded sample of the
+    work): clean + degree order + orientation in full (the oracle's
+    single-threaded C), then the forward count with per-vertex counts over
+    every stride-th row, on all host cores (OpenMP build) and on one core.
+    Rows sampled with a stride give 1/stride of the count's work in
+    expectation, so the whole count is estimated as stride x the sample's
+    time.  Returns the cpu_baseline object (value: all cores)."""
+    import oracle
+    t0 = time.perf_counter()
+    g = oracle.clean(src, dst, n)
+    o = oracle.orient(g)
+    prep_s = time.perf_counter() - t0
+    m = g.m
+    del g
+    cores = oracle.num_threads()
+
+    def timed(threads, stride):
+        t = time.perf_counter()
+        oracle.tc_forward_mt(o, per_vertex=True, threads=threads, stride=stride)
+        return time.perf_counter() - t
+
+    def sampled(threads, target):
+        # fixed cost of a count (per-thread counters, their final sum): one row
+        fixed = timed(threads, n + 1)
+        stride = 4096
+        while True:
+            dt = timed(threads, stride)
+            est = fixed + stride * max(dt - fixed, 0.0)
+            if dt - fixed >= 0.25 * target or stride == 1:
+                return stride, dt, est
+            stride = max(1, min(stride // 2, int((est - fixed) / target) or 1))
+
+    s_all, dt_all, est_all = sampled(cores, target_s)
+    s_one, dt_one, est_one = sampled(1, target_s / 2)
+    del o
+    return {"value": m / (prep_s + est_all), "unit": "edges/s", "cores": cores, "kind": "oracle",
+            "single_core_value": m / (prep_s + est_one),
+            "sample": f"oracle on the benchmark's R-MAT graph itself ({m} unique edges): clean + degree order + "
+                      f"orientation in full, single-threaded C, {prep_s:.1f} s; forward count with per-vertex "
+                      f"counts over every {s_all}th row on {cores} cores (OpenMP build) in {dt_all:.2f} s, "
+                      f"x{s_all} = {est_all:.1f} s estimated for all rows; single core: every {s_one}th row in "
+                      f"{dt_one:.2f} s, x{s_one} = {est_one:.1f} s",
+            "prep_s": prep_s, "count_s_all_cores": est_all, "count_s_single_core": est_one}
 
 
 def run_reference(args, rank, world):
@@ -311,6 +368,16 @@ def serve_bench(args):
             "batched_launches_closed_loop": st_b["batches"]}
 
 
+def serve_summary(serve):
+    """The serve figures that matter, compact, for the end of the line."""
+    if not serve or "error" in serve:
+        return serve
+    p = serve["poisson"]
+    return {"jobs": serve["jobs"], "capacity_jobs_s": serve["capacity_jobs_s"],
+            "at_0.8x_serial_capacity": {k: {"jobs_s": round(p[k]["jobs_s"], 1), "p50_ms": round(p[k]["p50_ms"], 2),
+                                            "p99_ms": round(p[k]["p99_ms"], 2)} for k in ("serial", "batched")}}
+
+
 def h2d_gbs(torch, nbytes=1 << 30, reps=5):
     """Pinned host-to-device copy bandwidth of this GPU's host link."""
     h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
@@ -329,7 +396,8 @@ def tiers_bench(args):
     """The runtime tiers on one partition each of R-MAT s24 and the grid
     (count phase only, the partition built once): launch per block triple
     versus the persistent autotuned kernel, each with and without CUDA-graph
-    replay.  Per-vertex counts on, written to a device tensor."""
+    replay, and the hybrid scheduler (host threads on the lightest parts) at
+    three cut-offs.  Per-vertex counts on, written to a device tensor."""
     import torch
     from paper_2209_04541_b300 import pgabb as P
     out = {}
@@ -345,12 +413,17 @@ def tiers_bench(args):
         tv = torch.zeros(n, dtype=torch.uint64, device="cuda")
         rows = {}
         T0 = None
-        for label, kw in (("plain", dict(mode=P.PGB_MODE_PLAIN)),
-                          ("plain+graph", dict(mode=P.PGB_MODE_PLAIN, use_graph=1)),
-                          ("persistent-auto", dict()),
-                          ("persistent-auto+graph", dict(use_graph=1))):
+        settings = [("plain", dict(mode=P.PGB_MODE_PLAIN)),
+                    ("plain+graph", dict(mode=P.PGB_MODE_PLAIN, use_graph=1)),
+                    ("persistent-auto", dict()),
+                    ("persistent-auto+graph", dict(use_graph=1))]
+        # HYBRID (host kernel on the lightest parts, under a cut-off share of
+        # the estimated work), beside the GPU-only rows, never instead of them
+        settings += [(f"hybrid-{ppm / 1e4:g}%", dict(mode=P.PGB_MODE_HYBRID, host_share_ppm=ppm))
+                     for ppm in (100, 1000, 10000)]
+        for label, kw in settings:
             o = P.pgb_tc_opts_default(**kw)
-            walls, kms = [], []
+            walls, kms, hms = [], [], []
             for i in range(2 + args.tiers_steps):
                 torch.cuda.synchronize()
                 t = time.perf_counter()
@@ -360,6 +433,7 @@ def tiers_bench(args):
                 if i >= 2:
                     walls.append(wall)
                     kms.append(P.pgb_tc_result_kernel_ms(r))
+                    hms.append(P.pgb_tc_result_hybrid(r))
                 var = P.pgb_tc_result_variant(r)
                 r.free()
                 T0 = T if T0 is None else T0
@@ -368,7 +442,12 @@ def tiers_bench(args):
             rows[label] = {"edges_s": info["m"] / wall, "wall_ms": 1e3 * wall,
                            "device_ms": statistics.median(kms),
                            "kernel": "k_tc_hash" if var == P.PGB_VAR_HASH else
-                                     ("k_tc_tuple" if "plain" in label else "k_tc_persistent")}
+                                     ("k_tc_tuple" if "plain" in label else
+                                      ("k_tc_hash+k_tc_persistent" if var == P.PGB_VAR_MIXED else "k_tc_persistent"))}
+            if label.startswith("hybrid"):
+                rows[label].update({"host_ms": statistics.median(h["host_ms"] for h in hms),
+                                    "host_parts": hms[-1]["host_parts"], "host_threads": hms[-1]["host_threads"],
+                                    "host_in_edges": hms[-1]["host_in_edges"]})
         b.free()
         del tv
         torch.cuda.empty_cache()
@@ -379,6 +458,49 @@ def tiers_bench(args):
             "workloads": out}
 
 
+def autotune_bench(args):
+    """Per-part autotuning on a graph whose parts disagree: the count phase
+    (partition built once) with the per-part choice (AUTO), with the hash
+    kernel for every part, and with the edge-wise kernel for every part.
+    Per-vertex counts on, written to a device tensor; counts must agree."""
+    import torch
+    from paper_2209_04541_b300 import pgabb as P
+    w = dict(WORKLOADS[args.autotune_workload])
+    s_np, d_np, n = generate(w)
+    stream = torch.cuda.current_stream()
+    g = P.pgb_graph_from_edges(torch.from_numpy(s_np).cuda(), torch.from_numpy(d_np).cuda(), n, stream)
+    del s_np, d_np
+    b = P.pgb_partition(g, w["p"], P.PGB_CUT_NNZ, stream)
+    g.free()
+    info = P.pgb_blocks_info(b)
+    tv = torch.zeros(n, dtype=torch.uint64, device="cuda")
+    rows, T0 = {}, None
+    names = {P.PGB_VAR_HASH: "hash", P.PGB_VAR_BSEARCH: "bsearch", P.PGB_VAR_MIXED: "mixed"}
+    for label, var in (("auto", P.PGB_VAR_AUTO), ("hash", P.PGB_VAR_HASH), ("bsearch", P.PGB_VAR_BSEARCH)):
+        o = P.pgb_tc_opts_default(variant=var)
+        kms = []
+        for i in range(2 + args.tiers_steps):
+            r = P.pgb_tc_run(b, o, stream)
+            T, _ = P.pgb_tc_result_get(r, per_vertex=tv)
+            if i >= 2:
+                kms.append(P.pgb_tc_result_kernel_ms(r))
+            used = P.pgb_tc_result_variant(r)
+            parts = P.pgb_tc_result_part_variants(r)
+            r.free()
+            T0 = T if T0 is None else T0
+            assert T == T0, "variants disagree"
+        rows[label] = {"kernel_ms": statistics.median(kms), "edges_s": info["m"] / (statistics.median(kms) / 1e3),
+                       "variant_used": names.get(used, used),
+                       "hash_parts": int((parts == P.PGB_VAR_HASH).sum()), "parts": int(len(parts))}
+    b.free()
+    del tv
+    torch.cuda.empty_cache()
+    best_single = min(rows["hash"]["kernel_ms"], rows["bsearch"]["kernel_ms"])
+    return {"metric": "count-phase kernel ms by variant choice", "workload": w["desc"], "unique_edges": info["m"],
+            "triangles": T0, "lookups_per_edge": info["probes"] / max(info["m"], 1), "choices": rows,
+            "auto_vs_best_single_choice": best_single / rows["auto"]["kernel_ms"]}
+
+
 def stream_bench(args):
     """The streaming tiers against the same graph fully resident: the in-edge
     index in pinned host memory (budget --stream-budget-gb), and the block
@@ -387,20 +509,19 @@ def stream_bench(args):
     from paper_2209_04541_b300 import pgabb as P
     w = dict(WORKLOADS[args.stream_workload])
     mraw = raw_edge_count(w)
+    hs = torch.empty(mraw, dtype=torch.uint32, pin_memory=True)
+    hd = torch.empty(mraw, dtype=torch.uint32, pin_memory=True)
+    _, _, n_raw = generate(w, out=(hs.numpy(), hd.numpy()))
 
     def build():
-        hs = torch.empty(mraw, dtype=torch.uint32, pin_memory=True)
-        hd = torch.empty(mraw, dtype=torch.uint32, pin_memory=True)
-        _, _, n = generate(w, out=(hs.numpy(), hd.numpy()))
         stream = torch.cuda.current_stream()
         t0 = time.perf_counter()
-        g = P.pgb_graph_from_edges(hs.cuda(), hd.cuda(), n, stream)
-        del hs, hd
+        g = P.pgb_graph_from_edges(hs.cuda(), hd.cuda(), n_raw, stream)
         b = P.pgb_partition(g, w["p"], P.PGB_CUT_NNZ, stream)
         g.free()
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        return b, n, time.perf_counter() - t0
+        return b, n_raw, time.perf_counter() - t0
 
     def timed(b, opts, reps):
         out = []
@@ -473,6 +594,7 @@ def stream_bench(args):
             out["cache"] = c
         b.free()
         torch.cuda.empty_cache()
+    del hs, hd
     return out
 
 
@@ -500,10 +622,13 @@ def main(argv=None):
     ap.add_argument("--no-tiers", action="store_true")
     ap.add_argument("--tiers-workloads", default="rmat24,grid4096")
     ap.add_argument("--tiers-steps", type=int, default=3)
-    ap.add_argument("--stream-workload", choices=["rmat24", "rmat22", "rmat27"], default="rmat24")
-    ap.add_argument("--stream-budget-gb", type=float, default=2.0)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune-workload", choices=sorted(WORKLOADS), default="grid4096_u_rmat22")
+    ap.add_argument("--stream-workload", choices=["rmat24", "rmat22", "rmat27"], default="rmat27",
+                    help="streamed graph (default: R-MAT s27, p=64, the out-of-core configuration)")
+    ap.add_argument("--stream-budget-gb", type=float, default=16.0, help="index tier device budget")
     ap.add_argument("--stream-steps", type=int, default=3)
-    ap.add_argument("--cache-budget-gb", type=float, default=1.0,
+    ap.add_argument("--cache-budget-gb", type=float, default=4.0,
                     help="block cache tier budget (0 = skip the tier)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
@@ -557,6 +682,9 @@ def main(argv=None):
         if not info:
             info.update(P.pgb_blocks_info(b))
             info["variant_used"] = P.pgb_tc_result_variant(r)
+            pv_ = P.pgb_tc_result_part_variants(r)
+            info["parts_by_kernel"] = {"hash": int((pv_ == P.PGB_VAR_HASH).sum()),
+                                       "edgewise": int(((pv_ == P.PGB_VAR_BSEARCH) | (pv_ == P.PGB_VAR_MERGE)).sum())}
         r.free()
         b.free()
         return T, kms
@@ -598,18 +726,34 @@ def main(argv=None):
     peak, peak_note = measured_peaks()
     if mode == P.PGB_MODE_PLAIN:
         kname = "k_tc_tuple"
+    elif info["variant_used"] == P.PGB_VAR_HASH:
+        kname = "k_tc_hash"
+    elif info["variant_used"] == P.PGB_VAR_MIXED:
+        # per-part choice: the hash kernel counts most parts (by lookups),
+        # the edge-wise kernel the flat ones; kernel_ms covers both launches
+        kname = "k_tc_hash"
     else:
-        kname = "k_tc_hash" if info["variant_used"] == P.PGB_VAR_HASH else "k_tc_persistent"
-    achieved = info["alg_bytes"] / (kernel_ms / 1e3) / 1e9
+        kname = "k_tc_persistent"
+    ew_achieved = info["alg_bytes"] / (kernel_ms / 1e3) / 1e9
+    if kname == "k_tc_hash":
+        # bytes this kernel must stream: every looked-up entry of the tails'
+        # rows (4 per probe), one 8-byte in-edge descriptor per edge, and
+        # each head's list (4 per edge)
+        kb = 4 * info["probes"] + 12 * info["m"]
+        bytes_rule = "4 probes + 12|E+| (looked-up tail-row entries, in-edge index, head lists)"
+    else:
+        kb = info["alg_bytes"]
+        bytes_rule = "4|E+| + 4 sum_v indeg(v) outdeg(v) + 8(n+1)"
+    achieved = kb / (kernel_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_note, "alg_bytes": info["alg_bytes"],
+                "frac": achieved / peak, "peak_source": peak_note, "alg_bytes": kb, "alg_bytes_rule": bytes_rule,
                 "kernel_ms": kernel_ms, "traffic": kernel_traffic(kname, args.workload)}
     if kname == "k_tc_hash":
-        # bytes this variant must stream: every looked-up entry of the tails'
-        # rows, one 8-byte in-edge descriptor per edge, and each head's list
-        kb = 4 * info["probes"] + 12 * info["m"]
-        roofline.update({"kernel_alg_bytes": kb, "kernel_achieved": kb / (kernel_ms / 1e3) / 1e9,
-                         "kernel_frac": kb / (kernel_ms / 1e3) / 1e9 / peak})
+        roofline["edgewise_bound"] = {
+            "note": "4|E+| + 4 sum_v indeg(v) outdeg(v) + 8(n+1): the edge-wise method's bytes, which re-read "
+                    "v's list per in-edge; this kernel holds that list in shared memory, so this is not a "
+                    "bandwidth fraction",
+            "alg_bytes": info["alg_bytes"], "achieved": ew_achieved, "ratio_to_peak": ew_achieved / peak}
 
     e2e = None
     if not args.no_e2e:
@@ -630,7 +774,10 @@ def main(argv=None):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        try:
+            cpu = cpu_baseline(hs.numpy(), hd.numpy(), n)
+        except Exception as exc:  # reported, not hidden
+            cpu = {"error": f"{type(exc).__name__}: {exc}"}
 
     serve = None
     del ds, dd, tv
@@ -646,6 +793,12 @@ def main(argv=None):
             tiers = tiers_bench(args)
         except Exception as exc:  # reported, not hidden
             tiers = {"error": f"{type(exc).__name__}: {exc}"}
+    autotune = None
+    if rank == 0 and not args.no_autotune:
+        try:
+            autotune = autotune_bench(args)
+        except Exception as exc:  # reported, not hidden
+            autotune = {"error": f"{type(exc).__name__}: {exc}"}
     streamed = None
     if rank == 0 and not args.no_stream:
         try:
@@ -659,6 +812,10 @@ def main(argv=None):
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                 "config": {"workload": w["desc"], "name": args.workload, "p": w["p"], "mode": args.mode,
                            "variant": args.variant, "kernel": kname,
+                           "variant_used": {P.PGB_VAR_HASH: "hash", P.PGB_VAR_BSEARCH: "bsearch",
+                                            P.PGB_VAR_MERGE: "merge", P.PGB_VAR_MIXED: "mixed (per part)"}.get(
+                                                info["variant_used"], info["variant_used"]),
+                           "parts_by_kernel": info["parts_by_kernel"],
                            "order": args.order, "per_vertex": bool(args.per_vertex), "n": n,
                            "raw_edges": mraw, "unique_edges": m_u, "triangles": T,
                            "wedges": info["wedges"], "probes": info["probes"], "triples": info["triples"],
@@ -667,7 +824,8 @@ def main(argv=None):
                                  % (8 * mraw / 1e9, 8 * m_u / 1e9)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "gpu_launches_per_step": launches / args.steps,
-                "clocks": clocks, "serve": serve, "tiers": tiers, "stream": streamed}
+                "clocks": clocks, "serve": serve, "tiers": tiers, "autotune": autotune, "stream": streamed}
+        line["serve_summary"] = serve_summary(serve)
         print(json.dumps(line), flush=True)
     if dist.is_initialized():
         dist.destroy_process_group()

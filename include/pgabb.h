@@ -72,12 +72,20 @@ extern "C" {
 /* PGB_MODE_PLAIN: one kernel launch per block triple (i, j, k), each
  *   counting the triangles u < v < w with u in V_i, v in V_j, w in V_k:
  *   the block-list (A_ij, A_ik, A_jk) of Section 3.6 exactly.
- * PGB_MODE_PERSISTENT: one persistent kernel drains a device queue of block
- *   tuples (A_ij, A_i[k0..k1], A_j[k0..k1]) whose third block is a run of
- *   consecutive column blocks (a coarser conformal cut); heavy tuples are
- *   split into edge chunks. */
+ * PGB_MODE_PERSISTENT: persistent kernels drain device queues of work: the
+ *   edge-wise kernel takes block columns (A_*j with third range [c_j, n):
+ *   the tuples (A_ij, A_i[j..p-1], A_j[j..p-1]) of every i <= j) in chunks
+ *   of edges; the hash kernel takes middle-vertex work items.
+ * PGB_MODE_HYBRID: Section 4.4's scheduler with host threads beside the GPU.
+ *   The head parts (tasks) are ordered by estimated work (lookups plus
+ *   in-edges); the host kernel takes the lightest parts while their summed
+ *   estimate stays within host_share_ppm / 10^6 of the total (the cut-off:
+ *   the host never takes a heavier part), on host_threads threads; the
+ *   device counts the other parts as in PERSISTENT mode, at the same time.
+ *   Needs resident blocks and use_graph = 0 (else PGB_E_STATE). */
 #define PGB_MODE_PLAIN      0
 #define PGB_MODE_PERSISTENT 1
+#define PGB_MODE_HYBRID     2
 
 /* ------------------------------------------------- intersection variants */
 /* Section 3.6 lets the intersection run over sorted lists or a hash map.
@@ -98,16 +106,26 @@ extern "C" {
  * PLAIN mode runs PGB_VAR_BSEARCH or PGB_VAR_MERGE (PGB_VAR_HASH gives
  * PGB_E_INVAL).
  * Autotuner (PGB_VAR_AUTO): PLAIN mode runs PGB_VAR_BSEARCH.  PERSISTENT
- * mode runs PGB_VAR_HASH when the graph averages at least 32 lookups per
- * oriented edge (probes >= 32 |E+|, see pgb_blocks_stats: long lists, skewed
- * degrees) and PGB_VAR_BSEARCH otherwise (flat graphs with short lists).
- * Within the hash form the bitmap or table, and the split of heavy middle
- * vertices into in-edge chunks and key-range slices, are chosen per work
- * item from its rank range, list length and in-degree. */
+ * mode chooses per column block j (the head part V_j): the tuples
+ * (A_ij, A_ik, A_jk) of one j count exactly the triangles whose middle
+ * vertex lies in V_j, so each part can take its own kernel.  A part runs
+ * PGB_VAR_HASH when its oriented edges average at least 32 lookups
+ * (PGB_EXPORT_PART_PROBES[j] >= 32 * sum_i |A_ij|: long lists, skewed
+ * degrees) and PGB_VAR_BSEARCH otherwise (short lists); when the parts
+ * differ, one hash launch over the hash parts' work items and one edge-wise
+ * launch over the other parts' tuples add into the same counts
+ * (PGB_VAR_MIXED).  Within the hash form the bitmap or table, and the split
+ * of heavy middle vertices into in-edge chunks and key-range slices, are
+ * chosen per work item from its rank range, list length and in-degree.
+ * PGB_VAR_MIXED is a result value only (pgb_tc_result_variant), and so is
+ * PGB_VAR_HOST (pgb_tc_result_part_variants: a part the HYBRID host kernel
+ * counted). */
 #define PGB_VAR_AUTO    0
 #define PGB_VAR_BSEARCH 1
 #define PGB_VAR_MERGE   2
 #define PGB_VAR_HASH    3
+#define PGB_VAR_MIXED   4
+#define PGB_VAR_HOST    5
 
 /* Queue order of block tuples (Section 4.4 sorts by decreasing weight). */
 #define PGB_ORDER_WEIGHT   0  /* decreasing weight (Section 4.4) */
@@ -192,7 +210,11 @@ int pgb_blocks_info(const pgb_blocks* b, pgb_blocks_stats* out);
  *   PGB_EXPORT_CUTS       uint32[p+1]
  *   PGB_EXPORT_BLOCK_EDGES uint64[p*p] |A_ij| row-major
  *   PGB_EXPORT_TRIPLES    uint32[3*T] queue (i, j, k) in order
- *   PGB_EXPORT_WEIGHTS    uint64[T]   queue weights */
+ *   PGB_EXPORT_WEIGHTS    uint64[T]   queue weights
+ *   PGB_EXPORT_PART_PROBES uint64[p]  per head part j: the sum over oriented
+ *                                     edges (u, v) with v in V_j of the
+ *                                     entries of u's row after v (the
+ *                                     autotuner's per-part statistic) */
 #define PGB_EXPORT_PERM        0
 #define PGB_EXPORT_ROWPTR      1
 #define PGB_EXPORT_COL         2
@@ -200,6 +222,7 @@ int pgb_blocks_info(const pgb_blocks* b, pgb_blocks_stats* out);
 #define PGB_EXPORT_BLOCK_EDGES 4
 #define PGB_EXPORT_TRIPLES     5
 #define PGB_EXPORT_WEIGHTS     6
+#define PGB_EXPORT_PART_PROBES 7
 int pgb_blocks_export(const pgb_blocks* b, int what, void* dst, int mem, void* stream);
 
 void pgb_blocks_free(pgb_blocks* b);
@@ -259,6 +282,28 @@ int pgb_blocks_cache_budget(const pgb_blocks* b, int per_vertex, uint32_t slices
  * Errors: PGB_E_INVAL (NULL). */
 int pgb_blocks_resident_bytes(const pgb_blocks* b, int per_vertex, uint64_t* bytes);
 
+/* --------------------------------------------------------------- cancel */
+/* A cancel token stops runs that are already on the device (the paper's
+ * scheduler controls its tasks from the host, Section 4.4; a stop request is
+ * this library's form of that control).  The token is one word of pinned
+ * host memory mapped into the device's address space.  A run given the
+ * token (pgb_tc_opts.cancel) reads it from its kernels: the persistent
+ * kernels every 64 work fetches, a plain per-triple launch at entry.  A
+ * kernel that finds it set skips the rest of its work (every CTA stops
+ * after its current work item) and marks the run, and pgb_tc_result_get
+ * then fails with PGB_E_CANCELLED.  A run that finished before it looked at
+ * the token is complete and returns its counts.  No wait on the token is
+ * unbounded: a kernel only reads it.  One token may serve many runs; set it
+ * from any thread, reset it before reusing it.  Free it only after the runs
+ * that use it have been fetched or freed.
+ * Errors: PGB_E_INVAL (NULL), PGB_E_CUDA (pinned mapped allocation). */
+typedef struct pgb_cancel pgb_cancel;
+int pgb_cancel_create(pgb_cancel** out);
+int pgb_cancel_set(pgb_cancel* c);
+int pgb_cancel_reset(pgb_cancel* c);
+int pgb_cancel_is_set(const pgb_cancel* c, int* set);
+void pgb_cancel_free(pgb_cancel* c);
+
 /* ------------------------------------------------------------------ run */
 typedef struct {
     int32_t mode;          /* PGB_MODE_* (default PGB_MODE_PERSISTENT) */
@@ -284,7 +329,12 @@ typedef struct {
                               524,288 ranks); 0 = autotuned by vertex count:
                               128 below 2^24 vertices, 256 below 2^26, else
                               512 (128 always for column-offloaded blocks) */
-    uint32_t reserved[6];
+    pgb_cancel* cancel;    /* stop token read by the run's kernels, or NULL */
+    uint32_t host_threads; /* HYBRID: host threads (0 = all hardware threads) */
+    uint32_t host_share_ppm;/* HYBRID: cut-off, the host's share of the estimated
+                              work in parts per million (0 = 1000, i.e. 0.1%;
+                              at most 10^6: everything on the host) */
+    uint32_t reserved[2];
 } pgb_tc_opts;
 
 void pgb_tc_opts_default(pgb_tc_opts* o);
@@ -297,14 +347,31 @@ int pgb_tc_run(const pgb_blocks* b, const pgb_tc_opts* opts, void* stream, pgb_t
 
 /* Wait for the run and fetch results.  total: global triangle count (may be
  * NULL).  per_vertex: n uint64 counts t[x] indexed by ORIGINAL vertex ID
- * (may be NULL; PGB_E_STATE if the run had per_vertex = 0). */
+ * (may be NULL; PGB_E_STATE if the run had per_vertex = 0).  Fails with
+ * PGB_E_CANCELLED, writing nothing, when a kernel of the run stopped early
+ * on its cancel token. */
 int pgb_tc_result_get(pgb_tc_result* r, uint64_t* total, uint64_t* per_vertex, int mem);
 
 /* PLAIN mode with per_triple = 1: counts[t] for queue entry t (T entries). */
 int pgb_tc_result_triples(pgb_tc_result* r, uint64_t* counts, int mem);
 
-/* The variant that ran (PGB_VAR_BSEARCH, PGB_VAR_MERGE or PGB_VAR_HASH). */
+/* The variant that ran (PGB_VAR_BSEARCH, PGB_VAR_MERGE, PGB_VAR_HASH, or
+ * PGB_VAR_MIXED when the autotuner chose differently for different parts). */
 int pgb_tc_result_variant(pgb_tc_result* r, int* variant);
+
+/* Per-part choice of the run: *p = parts; variants (may be NULL; p entries)
+ * gets, for each head part j, the kernel that counted the triangles whose
+ * middle vertex lies in V_j (PGB_VAR_HASH, PGB_VAR_BSEARCH, PGB_VAR_MERGE,
+ * or PGB_VAR_HOST for the host kernel of a HYBRID run).
+ * Errors: PGB_E_INVAL (NULL r or p). */
+int pgb_tc_result_part_variants(pgb_tc_result* r, uint32_t* p, int32_t* variants);
+
+/* HYBRID runs: the host kernel's wall time in milliseconds (the host copy of
+ * the graph included on the first hybrid run of a partition), the in-edges
+ * and parts it counted, and its threads; all 0 for other runs.  Any output
+ * pointer may be NULL.  Errors: PGB_E_INVAL (NULL r). */
+int pgb_tc_result_hybrid(pgb_tc_result* r, float* host_ms, uint64_t* host_in_edges, uint32_t* host_parts,
+                         uint32_t* host_threads);
 
 /* Streamed runs: host-to-device bytes copied (index slices, work items and,
  * for column-offloaded blocks, column slices), the number of chunks (pieces
@@ -403,14 +470,16 @@ int pgb_server_poll(pgb_server* s, uint64_t job_id, int* state);
 int pgb_server_wait(pgb_server* s, uint64_t job_id, double timeout_s, uint64_t* total, uint64_t* per_vertex,
                     double* latency_s);
 
-/* Cancel: a queued job is dropped at once; a job already on the device runs
- * to its end and its result is dropped (wait returns PGB_E_CANCELLED). */
+/* Cancel: a queued job is dropped at once.  A job already on the device is
+ * marked; once every job of its batch is marked (a SERIAL job is alone), the
+ * batch's counting kernels are stopped through the batch thread's cancel
+ * token.  Either way wait returns PGB_E_CANCELLED for the job. */
 int pgb_server_cancel(pgb_server* s, uint64_t job_id);
 
 int pgb_server_stats(pgb_server* s, pgb_server_info* out);
 
-/* Stop: queued jobs are cancelled, jobs on the device finish, threads and
- * streams are released. */
+/* Stop: queued jobs are cancelled, batches on the device are stopped through
+ * their cancel tokens, threads and streams are released. */
 void pgb_server_destroy(pgb_server* s);
 
 /* ------------------------------------------------- no-allocation count */

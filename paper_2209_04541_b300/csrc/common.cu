@@ -88,7 +88,53 @@ extern "C" {
 
 const char* pgb_last_error(void) { return pgb::t_last_error.c_str(); }
 
-const char* pgb_version(void) { return "pgabb-b300 0.1.0 (sm_103a)"; }
+const char* pgb_version(void) { return "pgabb-b300 0.2.0 (sm_103a)"; }
+
+int pgb_cancel_create(pgb_cancel** out) {
+    return pgb::guard([&] {
+        if (!out) pgb::fail(PGB_E_INVAL, "out is NULL");
+        std::unique_ptr<pgb_cancel> c(new pgb_cancel());
+        void* h = nullptr;
+        PGB_CUDA(cudaHostAlloc(&h, 64, cudaHostAllocMapped | cudaHostAllocPortable));
+        std::memset(h, 0, 64);
+        void* d = nullptr;
+        cudaError_t e = cudaHostGetDevicePointer(&d, h, 0);
+        if (e != cudaSuccess) {
+            cudaFreeHost(h);
+            pgb::fail(PGB_E_CUDA, std::string("cudaHostGetDevicePointer: ") + cudaGetErrorString(e));
+        }
+        c->host = static_cast<volatile uint32_t*>(h);
+        c->dev = static_cast<uint32_t*>(d);
+        *out = c.release();
+    });
+}
+
+int pgb_cancel_set(pgb_cancel* c) {
+    return pgb::guard([&] {
+        if (!c) pgb::fail(PGB_E_INVAL, "token is NULL");
+        __atomic_store_n(const_cast<uint32_t*>(c->host), 1u, __ATOMIC_SEQ_CST);
+    });
+}
+
+int pgb_cancel_reset(pgb_cancel* c) {
+    return pgb::guard([&] {
+        if (!c) pgb::fail(PGB_E_INVAL, "token is NULL");
+        __atomic_store_n(const_cast<uint32_t*>(c->host), 0u, __ATOMIC_SEQ_CST);
+    });
+}
+
+int pgb_cancel_is_set(const pgb_cancel* c, int* set) {
+    return pgb::guard([&] {
+        if (!c || !set) pgb::fail(PGB_E_INVAL, "NULL argument");
+        *set = __atomic_load_n(const_cast<const uint32_t*>(c->host), __ATOMIC_SEQ_CST) != 0;
+    });
+}
+
+void pgb_cancel_free(pgb_cancel* c) {
+    if (!c) return;
+    if (c->host) cudaFreeHost(const_cast<uint32_t*>(c->host));
+    delete c;
+}
 
 uint64_t pgb_kernel_launches(void) { return pgb::g_launches.load(); }
 

@@ -136,6 +136,33 @@ struct Scratch {
 
 int num_bits(uint64_t x);  // bits needed to represent values in [0, x]
 
+// ------------------------------------------------------------ stop requests
+
+// Per-run control block in device memory.  `stop` points at the run's
+// cancel-token word (pinned host memory mapped into the device's address
+// space) or is null; a kernel that sees the word set skips the rest of its
+// work and sets `cancelled`.
+struct RunCtl {
+    const volatile uint32_t* stop;
+    uint32_t cancelled;
+    uint32_t pad;
+};
+
+// The persistent kernels call this once every kStopCheckEvery work fetches
+// (a plain per-triple launch once at entry): a rare read of a word in host
+// memory, so that a stop request ends a run within a few work items.
+constexpr uint32_t kStopCheckEvery = 64;
+
+#ifdef __CUDACC__
+__device__ __forceinline__ bool run_stop_requested(RunCtl* c) {
+    if (!c) return false;
+    const volatile uint32_t* st = *reinterpret_cast<const volatile uint32_t* const volatile*>(&c->stop);
+    if (!st || *st == 0u) return false;
+    *reinterpret_cast<volatile uint32_t*>(&c->cancelled) = 1u;
+    return true;
+}
+#endif
+
 // ------------------------------------------------------------------ handles
 
 }  // namespace pgb
@@ -147,6 +174,13 @@ struct pgb_graph {
     pgb::DevBuf<uint64_t> keys;           // (a << id_bits) | b, a < b, sorted
     pgb::DevBuf<uint32_t> deg;            // degree per vertex
     cudaStream_t stream = nullptr;
+};
+
+// A cancel token: one word of pinned host memory, mapped into the device's
+// address space, that the host sets and the kernels read.
+struct pgb_cancel {
+    volatile uint32_t* host = nullptr;
+    uint32_t* dev = nullptr;
 };
 
 struct pgb_triple {
@@ -172,6 +206,8 @@ struct pgb_blocks {
     // captured runs (use_graph), at most four settings (tc.cu)
     mutable std::vector<std::shared_ptr<void>> run_plans;
     mutable std::mutex plan_mu;
+    // host copy of the oriented graph for the hybrid host kernel (hybrid.cu)
+    mutable std::shared_ptr<void> host_mirror;
     ~pgb_blocks() {
         if (h_xr) cudaFreeHost(h_xr);
         if (h_itail) cudaFreeHost(h_itail);
@@ -194,6 +230,8 @@ struct pgb_blocks {
     std::vector<pgb_triple> triples;    // queue order
     uint64_t wedges = 0;
     uint64_t probes = 0;  // sum over edges (u, v) of the entries of u's row after v
+    std::vector<uint64_t> part_probes;  // p: the same sum over edges whose head v lies in part j
+    std::vector<uint64_t> head_off;     // p + 1: first in-edge (index order) of each head part
     uint32_t max_outdeg = 0;
 };
 

@@ -130,31 +130,69 @@ __device__ __forceinline__ uint32_t part_of(const uint32_t* cuts, uint32_t p, ui
 
 // Block id (i * p + j) of every oriented edge (when bid is not null) and the
 // p x p block edge histogram (when hist is not null; shared-memory counters
-// when p*p fits, global otherwise).
+// when p*p fits, global otherwise).  With part_probes not null, also the
+// lookups of the middle-vertex variant per head part j: the sum over edges
+// (u, v) with v in V_j of the entries of u's row after v (shared counters).
 __global__ void k_block_ids(const uint32_t* __restrict__ rowidx, const uint32_t* __restrict__ col, uint64_t m,
                             const uint32_t* __restrict__ cuts_g, uint32_t p, uint32_t* __restrict__ bid,
-                            unsigned long long* __restrict__ hist) {
-    extern __shared__ uint32_t sm[];
-    uint32_t* cuts = sm;
-    uint32_t* h = sm + p + 1;
+                            unsigned long long* __restrict__ hist, const uint32_t* __restrict__ rowptr,
+                            unsigned long long* __restrict__ part_probes) {
+    extern __shared__ unsigned long long sm64[];
+    unsigned long long* pp_s = sm64;  // p entries when part_probes is set
+    uint32_t* cuts = reinterpret_cast<uint32_t*>(sm64 + (part_probes ? p : 0));
+    uint32_t* h = cuts + p + 1;
     const bool use_smem = (uint64_t)p * p <= 4096;
     for (uint32_t i = threadIdx.x; i <= p; i += blockDim.x) cuts[i] = cuts_g[i];
     if (use_smem)
         for (uint32_t i = threadIdx.x; i < p * p; i += blockDim.x) h[i] = 0;
+    if (part_probes)
+        for (uint32_t i = threadIdx.x; i < p; i += blockDim.x) pp_s[i] = 0;
     __syncthreads();
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-        uint32_t b = part_of(cuts, p, rowidx[e]) * p + part_of(cuts, p, col[e]);
-        if (bid) bid[e] = b;
-        if (!hist) continue;
-        if (use_smem) atomicAdd(&h[b], 1u);
-        else atomicAdd(&hist[b], 1ull);
+    for (uint64_t e0 = (uint64_t)blockIdx.x * blockDim.x; e0 < m; e0 += stride) {
+        const uint64_t e = e0 + threadIdx.x;
+        const bool live = e < m;
+        uint32_t j = 0xffffffffu, after = 0;
+        if (live) {
+            const uint32_t u = rowidx[e];
+            j = part_of(cuts, p, col[e]);
+            const uint32_t b = part_of(cuts, p, u) * p + j;
+            if (bid) bid[e] = b;
+            if (part_probes) after = rowptr[u + 1] - (uint32_t)(e + 1);
+            if (hist) {
+                if (use_smem) atomicAdd(&h[b], 1u);
+                else atomicAdd(&hist[b], 1ull);
+            }
+        }
+        if (part_probes) {
+            // a warp's edges are consecutive CSR positions, so their heads
+            // fall into few parts: one shared atomic per part and warp
+            const unsigned act = __ballot_sync(0xffffffffu, live);
+            if (live) {
+                const unsigned grp = __match_any_sync(act, j);
+                const uint32_t sum = __reduce_add_sync(grp, after);
+                // (32 of them stay below 2^32: with degree order an out-degree
+            // is at most sqrt(2 m) < 92,700 for m < 2^32)
+            if ((threadIdx.x & 31) == (unsigned)(__ffs(grp) - 1) && sum)
+                    atomicAdd(&pp_s[j], (unsigned long long)sum);
+            }
+        }
     }
+    if ((use_smem && hist) || part_probes) __syncthreads();
     if (use_smem && hist) {
-        __syncthreads();
         for (uint32_t i = threadIdx.x; i < p * p; i += blockDim.x)
             if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
     }
+    if (part_probes)
+        for (uint32_t i = threadIdx.x; i < p; i += blockDim.x)
+            if (pp_s[i]) atomicAdd(&part_probes[i], pp_s[i]);
+}
+
+// out[t] = colptr[cuts[t]] for t <= p: where each head part's in-edges start.
+__global__ void k_head_offsets(const uint32_t* __restrict__ colptr, const uint32_t* __restrict__ cuts, uint32_t p,
+                               unsigned long long* __restrict__ out) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t <= p) out[t] = colptr[cuts[t]];
 }
 
 // sum_v indeg(v) * outdeg(v) and max outdeg.
@@ -272,12 +310,13 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
     // --- block histogram (per-edge block ids are built on demand, for the
     // runs that walk edges block by block)
     const size_t pp = (size_t)p * p;
-    DevBuf<unsigned long long> hist(pp, s);
-    PGB_CUDA(cudaMemsetAsync(hist.ptr, 0, pp * 8, s));
+    // p x p histogram, the per-part lookups (p), the head parts' in-edge offsets (p + 1)
+    DevBuf<unsigned long long> hist(pp + 2 * (size_t)p + 1, s);
+    PGB_CUDA(cudaMemsetAsync(hist.ptr, 0, (pp + 2 * (size_t)p + 1) * 8, s));
     if (m > 0) {
-        size_t smem = ((size_t)p + 1) * 4 + (pp <= 4096 ? pp * 4 : 0);
+        size_t smem = (size_t)p * 8 + ((size_t)p + 1) * 4 + (pp <= 4096 ? pp * 4 : 0);
         k_block_ids<<<grid_for(m), 256, smem, s>>>(b->rowidx.ptr, b->col.ptr, m, b->cuts_d.ptr, p, nullptr,
-                                                   hist.ptr);
+                                                   hist.ptr, b->rowptr.ptr, hist.ptr + pp);
         PGB_CHECK_LAUNCH("k_block_ids");
     }
 
@@ -306,6 +345,8 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
         PGB_CHECK_LAUNCH("k_offsets_from_sorted");
         k_wedges<<<grid_for(n), 256, 0, s>>>(b->colptr.ptr, b->rowptr.ptr, n, wsum.ptr, wmax.ptr);
         PGB_CHECK_LAUNCH("k_wedges");
+        k_head_offsets<<<(p + 1 + 127) / 128, 128, 0, s>>>(b->colptr.ptr, b->cuts_d.ptr, p, hist.ptr + pp + p);
+        PGB_CHECK_LAUNCH("k_head_offsets");
     } else {
         k_fill_u32<<<grid_for((uint64_t)n + 1), 256, 0, s>>>(b->colptr.ptr, (uint64_t)n + 1, 0);
         PGB_CHECK_LAUNCH("k_fill_u32");
@@ -313,10 +354,14 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
 
     // --- one sync: cuts, histogram, stats to the host
     b->block_edges.assign(pp, 0);
+    b->part_probes.assign(p, 0);
     unsigned long long hw = 0, hp = 0;
     unsigned int hm = 0;
     PGB_CUDA(cudaMemcpyAsync(b->cuts.data(), b->cuts_d.ptr, ((size_t)p + 1) * 4, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaMemcpyAsync(b->block_edges.data(), hist.ptr, pp * 8, cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaMemcpyAsync(b->part_probes.data(), hist.ptr + pp, (size_t)p * 8, cudaMemcpyDeviceToHost, s));
+    b->head_off.assign((size_t)p + 1, 0);
+    PGB_CUDA(cudaMemcpyAsync(b->head_off.data(), hist.ptr + pp + p, ((size_t)p + 1) * 8, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaMemcpyAsync(&hw, wsum.ptr, 8, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaMemcpyAsync(&hp, wprobe.ptr, 8, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaMemcpyAsync(&hm, wmax.ptr, 4, cudaMemcpyDeviceToHost, s));
@@ -348,7 +393,7 @@ void ensure_block_edge_index(const pgb_blocks* b, cudaStream_t s) {
             DevBuf<uint32_t> bid(m, s), kalt(m, s), vals(m, s);
             size_t smem = ((size_t)p + 1) * 4 + (pp <= 4096 ? pp * 4 : 0);
             k_block_ids<<<grid_for(m), 256, smem, s>>>(b->rowidx.ptr, b->col.ptr, m, b->cuts_d.ptr, p, bid.ptr,
-                                                       nullptr);
+                                                       nullptr, nullptr, nullptr);
             PGB_CHECK_LAUNCH("k_block_ids");
             k_iota<<<grid_for(m), 256, 0, s>>>(vals.ptr, m);
             PGB_CHECK_LAUNCH("k_iota");
@@ -438,6 +483,7 @@ int pgb_blocks_export(const pgb_blocks* b, int what, void* dst, int mem, void* s
                 break;
             case PGB_EXPORT_CUTS: host_or_dev(b->cuts.data(), b->cuts.size() * 4); break;
             case PGB_EXPORT_BLOCK_EDGES: host_or_dev(b->block_edges.data(), b->block_edges.size() * 8); break;
+            case PGB_EXPORT_PART_PROBES: host_or_dev(b->part_probes.data(), b->part_probes.size() * 8); break;
             case PGB_EXPORT_TRIPLES: {
                 std::vector<uint32_t> t(3 * b->triples.size());
                 for (size_t i = 0; i < b->triples.size(); ++i) {

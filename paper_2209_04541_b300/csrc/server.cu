@@ -92,6 +92,14 @@ struct Job {
     uint64_t total = 0;
     std::vector<uint64_t> per_vertex;
     bool cancel = false;
+    std::shared_ptr<struct BatchState> batch;  // while RUNNING: the batch it is in
+};
+
+// A batch on the device: its thread's cancel token and how many of its jobs
+// are not cancelled; when that reaches zero the token stops the kernels.
+struct BatchState {
+    pgb_cancel* token = nullptr;
+    size_t live = 0;
 };
 
 // Pinned host buffers for batch results, reused by one batch thread.
@@ -136,6 +144,7 @@ struct pgb_server {
     bool paused = false;  // admission held (queued jobs wait)
     std::vector<std::thread> threads;
     std::vector<cudaStream_t> streams;  // one per batch thread, for the server's lifetime
+    std::vector<pgb_cancel*> tokens;    // one per batch thread: stops its batch's kernels
 };
 
 namespace pgb {
@@ -169,7 +178,7 @@ static void finish(pgb_server* S, const std::shared_ptr<Job>& J, int state, int 
 // file); fills each job's total and per-vertex counts, and `bad[j]` for jobs
 // with an endpoint >= n.
 static void count_batch(pgb_server* S, const std::vector<std::shared_ptr<Job>>& batch, cudaStream_t s,
-                        PinnedPool& pool, std::vector<uint32_t>& bad) {
+                        PinnedPool& pool, std::vector<uint32_t>& bad, pgb_cancel* token) {
     const uint32_t nj = (uint32_t)batch.size();
     std::vector<uint64_t> eoff(nj + 1, 0), voff(nj + 1, 0);
     for (uint32_t j = 0; j < nj; ++j) {
@@ -210,6 +219,10 @@ static void count_batch(pgb_server* S, const std::vector<std::shared_ptr<Job>>& 
     // third of the sum over its vertices
     pgb_tc_opts o;
     pgb_tc_opts_default(&o);
+    o.cancel = token;
+    int stopped = 0;
+    pgb_cancel_is_set(token, &stopped);
+    if (stopped) fail(PGB_E_CANCELLED, "every job of the batch was cancelled");
     pgb_tc_result* r = nullptr;
     rc = pgb_tc_run(b, &o, s, &r);
     if (rc != PGB_OK) fail(rc, pgb_last_error());
@@ -246,8 +259,10 @@ static void batch_loop(pgb_server* S, int idx) {
     const uint32_t cap = serial ? 1 : (S->o.max_batch_jobs ? S->o.max_batch_jobs : 256);
     const uint64_t max_edges = S->o.batch_edges ? S->o.batch_edges : kDefaultBatchEdges;
     PinnedPool pool;
+    pgb_cancel* token = S->tokens[idx];
     for (;;) {
         std::vector<std::shared_ptr<Job>> batch;
+        std::shared_ptr<BatchState> bs;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_queue.wait(lk, [&] {
@@ -256,6 +271,11 @@ static void batch_loop(pgb_server* S, int idx) {
                 return S->bytes_in_use + S->queued.front()->est <= S->o.budget_bytes;
             });
             if (S->stop) break;
+            // the token is reset under the lock, before any job of this batch
+            // can be cancelled
+            pgb_cancel_reset(token);
+            bs = std::make_shared<BatchState>();
+            bs->token = token;
             // admit in arrival order while the budget and the batch caps allow
             uint64_t edges = 0, verts = 0;
             while (!S->queued.empty() && batch.size() < cap) {
@@ -266,18 +286,22 @@ static void batch_loop(pgb_server* S, int idx) {
                 verts += J->n;
                 S->bytes_in_use += J->est;
                 J->state = PGB_JOB_RUNNING;
+                J->batch = bs;
                 batch.push_back(J);
                 S->queued.pop_front();
             }
+            bs->live = batch.size();
             ++S->n_batches;
             S->jobs_in_batches += batch.size();
         }
         std::vector<uint32_t> bad;
-        const int rc = guard([&] { count_batch(S, batch, s, pool, bad); });
+        const int rc = guard([&] { count_batch(S, batch, s, pool, bad, token); });
         const std::string msg = rc == PGB_OK ? std::string() : std::string(pgb_last_error());
         for (size_t j = 0; j < batch.size(); ++j) {
             const std::shared_ptr<Job>& J = batch[j];
-            if (rc != PGB_OK) finish(S, J, PGB_JOB_FAILED, rc, msg);
+            J->batch.reset();
+            if (rc == PGB_E_CANCELLED) finish(S, J, PGB_JOB_CANCELLED, PGB_E_CANCELLED, "");
+            else if (rc != PGB_OK) finish(S, J, PGB_JOB_FAILED, rc, msg);
             else if (bad[j]) finish(S, J, PGB_JOB_FAILED, PGB_E_INVAL, "vertex ID >= n in the job's edges");
             else if (J->cancel) finish(S, J, PGB_JOB_CANCELLED, PGB_E_CANCELLED, "");
             else finish(S, J, PGB_JOB_DONE, PGB_OK, "");
@@ -316,14 +340,25 @@ int pgb_server_create(const pgb_server_opts* opts, pgb_server** out) {
         PGB_CUDA(cudaGetDevice(&S->device));
         pgb_server* raw = S.get();
         const int nthreads = S->o.mode == PGB_SERVE_SERIAL ? 1 : (int)std::min<uint32_t>(S->o.max_inflight, 16);
+        auto release = [&] {
+            for (cudaStream_t x : S->streams) cudaStreamDestroy(x);
+            for (pgb_cancel* c : S->tokens) pgb_cancel_free(c);
+        };
         for (int i = 0; i < nthreads; ++i) {
             cudaStream_t st = nullptr;
             cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
             if (e != cudaSuccess) {
-                for (cudaStream_t x : S->streams) cudaStreamDestroy(x);
+                release();
                 fail(PGB_E_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
             }
             S->streams.push_back(st);
+            pgb_cancel* c = nullptr;
+            if (pgb_cancel_create(&c) != PGB_OK) {
+                const std::string why = pgb_last_error();
+                release();
+                fail(PGB_E_CUDA, why);
+            }
+            S->tokens.push_back(c);
         }
         for (int i = 0; i < nthreads; ++i) raw->threads.emplace_back(batch_loop, raw, i);
         live_handles_add(1);
@@ -423,6 +458,10 @@ int pgb_server_cancel(pgb_server* S, uint64_t job_id) {
         auto it = S->jobs.find(job_id);
         if (it == S->jobs.end()) fail(PGB_E_INVAL, "unknown job id");
         J = it->second;
+        if (J->state == PGB_JOB_RUNNING && J->batch && !J->cancel) {
+            // the last job of a running batch to be cancelled stops its kernels
+            if (--J->batch->live == 0) pgb_cancel_set(J->batch->token);
+        }
         J->cancel = true;
         auto q = std::find(S->queued.begin(), S->queued.end(), J);
         if (q != S->queued.end()) {
@@ -435,7 +474,8 @@ int pgb_server_cancel(pgb_server* S, uint64_t job_id) {
             ++S->n_cancelled;
             S->cv_done.notify_all();
         }
-        // a job already on the device runs to the end; its result is dropped
+        // a job already on the device: its batch stops once all its jobs
+        // are cancelled; otherwise the batch runs on and this result is dropped
     });
     return rc;
 }
@@ -466,6 +506,8 @@ void pgb_server_destroy(pgb_server* S) {
             J->err = PGB_E_CANCELLED;
         }
         S->queued.clear();
+        // batches on the device stop at their next check
+        for (pgb_cancel* c : S->tokens) pgb_cancel_set(c);
         S->cv_queue.notify_all();
         S->cv_done.notify_all();
     }
@@ -475,6 +517,7 @@ void pgb_server_destroy(pgb_server* S) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
+    for (pgb_cancel* c : S->tokens) pgb_cancel_free(c);
     delete S;
     live_handles_add(-1);
 }

@@ -152,7 +152,7 @@ static std::shared_ptr<StreamPlan> get_plan(const pgb_blocks* b, uint32_t in_chu
 void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint32_t threads, unsigned long long* tv,
                    uint64_t budget,
                    cudaStream_t s, DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
-                   cudaEvent_t ev1, uint64_t* streamed, uint32_t* nchunks_out) {
+                   cudaEvent_t ev1, uint64_t* streamed, uint32_t* nchunks_out, RunCtl* ctl) {
     npartials = 0;
     *streamed = 0;
     *nchunks_out = 0;
@@ -224,7 +224,7 @@ void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint32_t thr
             bytes += (uint64_t)ch.span * kStreamBytesPerInEdge + (uint64_t)ch.count * sizeof(VItem);
             PGB_CUDA(cudaStreamWaitEvent(ks[k], ready[k], 0));
             launch_hash(hg[k], sitems[k].ptr, ch.count, pv, ks[k], cursor.ptr + k, partials.ptr + c * grid, grid,
-                        P->threads);
+                        P->threads, ctl);
             PGB_CUDA(cudaEventRecord(freed[k], ks[k]));
         }
         PGB_CUDA(cudaEventRecord(done1, s1));
@@ -561,7 +561,8 @@ static ColSizes col_sizes(const pgb_blocks* b, bool pv, uint32_t threads) {
 void run_column_streaming(const pgb_blocks* b, bool pv, uint32_t threads, unsigned long long* tv, uint64_t budget,
                           cudaStream_t s,
                           DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
-                          cudaEvent_t ev1, uint64_t* streamed, uint32_t* npieces_out, uint32_t* loads_out) {
+                          cudaEvent_t ev1, uint64_t* streamed, uint32_t* npieces_out, uint32_t* loads_out,
+                          RunCtl* ctl) {
     const ColPlan& P = *std::static_pointer_cast<ColPlan>(b->col_plan);
     const uint32_t p = P.pc;
     npartials = 2;
@@ -731,7 +732,7 @@ void run_column_streaming(const pgb_blocks* b, bool pv, uint32_t threads, unsign
             Gr.ubase = P.slice_lo[c.i];
             if (ni) {
                 launch_hash(Gr, pit[k].ptr, (uint32_t)ni, pv, ss, cursor.ptr + k, part.ptr + (size_t)k * grid, grid,
-                            z.threads);
+                            z.threads, ctl);
                 k_add_partials<<<1, 256, 0, ss>>>(part.ptr + (size_t)k * grid, (uint32_t)grid, partials.ptr + k);
                 PGB_CHECK_LAUNCH("k_add_partials");
             }

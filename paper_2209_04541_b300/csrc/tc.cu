@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <memory>
 
+#include "hybrid.cuh"
 #include "internal.cuh"
 #include "tc_hash.cuh"
 
@@ -36,12 +37,20 @@ struct Tuple {
 };
 
 struct Graph {
+    // edge positions of a tuple's edges: bedge[idx] (block-grouped, PLAIN
+    // mode), or, when xr is set, the in-edge index's (uint32)xr[idx] - 1
+    // (grouped by head: the in-edges of a head part are one range)
     const uint32_t* __restrict__ bedge;
+    const unsigned long long* __restrict__ xr;
     const uint32_t* __restrict__ rowidx;
     const uint32_t* __restrict__ col;
     const uint32_t* __restrict__ rowptr;
     unsigned long long* __restrict__ tv;  // per-vertex counts, rank space (may be null)
 };
+
+__device__ __forceinline__ uint32_t edge_at(const Graph& G, uint32_t idx) {
+    return G.xr ? (uint32_t)__ldg(G.xr + idx) - 1u : __ldg(G.bedge + idx);
+}
 
 __device__ __forceinline__ uint32_t lower_bound(const uint32_t* __restrict__ a, uint32_t b, uint32_t e,
                                                 uint32_t x) {
@@ -64,7 +73,7 @@ __device__ __forceinline__ void warp_step(const Graph& G, uint32_t idx, bool val
                                           bool clip, unsigned long long& cnt, uint32_t* s_edge, int lane) {
     uint32_t sb = 0, sl = 0, lb = 0, ll = 0, u = 0, v = 0;
     if (valid) {
-        const uint32_t e = __ldg(G.bedge + idx);
+        const uint32_t e = edge_at(G, idx);
         u = __ldg(G.rowidx + e);
         v = __ldg(G.col + e);
         uint32_t xb = e + 1, xe = __ldg(G.rowptr + u + 1);
@@ -140,7 +149,7 @@ __device__ __forceinline__ void warp_step_merge(const Graph& G, uint32_t idx, bo
                                                 bool clip, unsigned long long& cnt, int lane) {
     uint32_t xb = 0, xe = 0, yb = 0, ye = 0, u = 0, v = 0;
     if (valid) {
-        const uint32_t e = __ldg(G.bedge + idx);
+        const uint32_t e = edge_at(G, idx);
         u = __ldg(G.rowidx + e);
         v = __ldg(G.col + e);
         xb = e + 1;
@@ -215,9 +224,18 @@ __device__ __forceinline__ void cta_reduce_store(unsigned long long cnt, unsigne
 
 // PLAIN mode: one launch per block triple; warps stride over its edges.
 template <bool PV>
-__global__ void __launch_bounds__(kThreads) k_tc_tuple(Graph G, Tuple t, unsigned long long* __restrict__ partials) {
+__global__ void __launch_bounds__(kThreads)
+    k_tc_tuple(Graph G, Tuple t, unsigned long long* __restrict__ partials, RunCtl* __restrict__ ctl) {
     __shared__ uint32_t s_edge[kWarps][32];
+    __shared__ int s_stop;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // a stop request seen at entry skips the launch (its partial is 0)
+    if (threadIdx.x == 0) s_stop = run_stop_requested(ctl) ? 1 : 0;
+    __syncthreads();
+    if (s_stop) {
+        if (threadIdx.x == 0) partials[blockIdx.x] = 0;
+        return;
+    }
     if (PV) s_edge[warp][lane] = 0;
     __syncwarp();
     unsigned long long cnt = 0;
@@ -239,7 +257,7 @@ template <bool PV>
 __global__ void __launch_bounds__(kThreads)
     k_tc_persistent(Graph G, const Tuple* __restrict__ tuples, const uint32_t* __restrict__ chunk_prefix,
                     uint32_t ntuples, uint32_t chunk, unsigned int* __restrict__ cursor,
-                    unsigned long long* __restrict__ partials) {
+                    unsigned long long* __restrict__ partials, RunCtl* __restrict__ ctl) {
     __shared__ uint32_t s_edge[kWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (PV) s_edge[warp][lane] = 0;
@@ -248,7 +266,15 @@ __global__ void __launch_bounds__(kThreads)
     unsigned long long cnt = 0;
     while (true) {
         uint32_t c = 0;
-        if (lane == 0) c = atomicAdd(cursor, 1u);
+        if (lane == 0) {
+            c = atomicAdd(cursor, 1u);
+            // every kStopCheckEvery-th chunk also reads the stop word; a stop
+            // pushes the cursor past the end for every warp
+            if (c % kStopCheckEvery == 0 && c < total_chunks && run_stop_requested(ctl)) {
+                atomicMax(cursor, total_chunks);
+                c = total_chunks;
+            }
+        }
         c = __shfl_sync(kFull, c, 0);
         if (c >= total_chunks) break;
         // tuple t: largest t with chunk_prefix[t] <= c
@@ -315,6 +341,12 @@ __global__ void k_reduce_segments(const unsigned long long* __restrict__ partial
     }
 }
 
+// t[i] += a[i] for i < n (the host kernel's per-vertex counts).
+__global__ void k_add_u64(unsigned long long* __restrict__ t, const unsigned long long* __restrict__ a, uint32_t n) {
+    uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) t[i] += a[i];
+}
+
 // Rank-space per-vertex counts to original IDs.
 __global__ void k_scatter_orig(const unsigned long long* __restrict__ tv, const uint32_t* __restrict__ perm,
                                uint32_t n, unsigned long long* __restrict__ out) {
@@ -340,13 +372,20 @@ struct pgb_tc_result {
     bool per_vertex = false;
     bool per_triple = false;
     uint64_t ntriples = 0;
-    int variant = PGB_VAR_BSEARCH;  // the variant that ran
+    int variant = PGB_VAR_BSEARCH;  // the variant that ran (PGB_VAR_MIXED: per part)
+    std::vector<int32_t> part_variant;  // p: the kernel that counted each head part
     uint64_t streamed = 0;          // host-to-device bytes of a streamed run
     uint32_t chunks = 0;            // stream chunks (or pieces) of a streamed run (0 = resident)
     uint32_t slice_loads = 0;       // column slices copied in (column-streamed runs)
     pgb::DevBuf<unsigned long long> total;
     pgb::DevBuf<unsigned long long> tv_orig;
     pgb::DevBuf<unsigned long long> triple_counts;
+    pgb::DevBuf<pgb::RunCtl> ctl;   // the run's stop word and its cancelled flag
+    // HYBRID runs: the host kernel's share
+    float host_ms = 0;
+    uint64_t host_in_edges = 0;
+    uint32_t host_parts = 0, host_threads = 0;
+    bool host_cancelled = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     ~pgb_tc_result() {
         if (ev0) cudaEventDestroy(ev0);
@@ -369,20 +408,66 @@ static Tuple make_tuple(const pgb_blocks* b, uint32_t i, uint32_t j, uint32_t k0
     return t;
 }
 
-// Autotuner (run level).  The middle-vertex hash kernel pays a fixed cost
-// per work item and wins when lists are long; the edge-wise binary-search
-// kernel wins on flat graphs with short lists.  The graph statistic that
-// separates them is the average number of lookups per oriented edge (the
-// entries of the tail's row after the head): measured on one B300 the hash
-// kernel is 5-10x faster on R-MAT (78-160 lookups per edge) and 1.6-18x
-// slower on Erdos-Renyi (19), random geometric (1.5) and grid (0.55) graphs.
+// Autotuner.  The middle-vertex hash kernel pays a fixed cost per work item
+// and wins when lists are long; the edge-wise binary-search kernel wins on
+// flat graphs with short lists.  The statistic that separates them is the
+// average number of lookups per oriented edge (the entries of the tail's row
+// after the head): measured on one B300 the hash kernel is 5-10x faster on
+// R-MAT (78-160 lookups per edge) and 1.6-18x slower on Erdos-Renyi (19),
+// random geometric (1.5) and grid (0.55) graphs.
+//
+// The choice is made per column block j (head part V_j): an oriented edge
+// (u, v) with v in V_j is the first edge of every triangle u < v < w it
+// closes, so the tuples (A_ij, A_ik, A_jk) of one j, and the hash work items
+// of the heads in V_j, count exactly the triangles whose middle vertex lies
+// in V_j.  Each part takes the kernel its own lookups per edge favour, and
+// both kernels add into the same counters.  A graph that mixes families (a
+// serve batch is a disjoint union of R-MAT, grid and geometric jobs) gets
+// the edge-wise kernel on its flat parts and the hash kernel on its skewed
+// ones.
 constexpr uint64_t kHashMinLookupsPerEdge = 32;
 
-static int choose_variant(const pgb_blocks* b, const pgb_tc_opts& o) {
-    if (o.mode == PGB_MODE_PLAIN) return o.variant == PGB_VAR_MERGE ? PGB_VAR_MERGE : PGB_VAR_BSEARCH;
-    if (b->offloaded) return PGB_VAR_HASH;  // only the hash kernel reads a streamed index
-    if (o.variant != PGB_VAR_AUTO) return o.variant;
-    return b->probes >= kHashMinLookupsPerEdge * b->m ? PGB_VAR_HASH : PGB_VAR_BSEARCH;
+// Which kernel counts a head part (the triangles whose middle vertex lies in
+// it): the edge-wise kernel, the hash kernel, or (HYBRID mode) the host.
+enum : uint8_t { kPartEdge = 0, kPartHash = 1, kPartHost = 2 };
+
+static uint64_t part_in_edges(const pgb_blocks* b, uint32_t j) {
+    return b->head_off.size() > j + 1 ? b->head_off[j + 1] - b->head_off[j] : 0;
+}
+
+// Fills kind[j] for every head part and returns the device side's variant:
+// PGB_VAR_BSEARCH, _MERGE or _HASH, or PGB_VAR_MIXED when parts with work
+// go to both device kernels.
+static int choose_variant(const pgb_blocks* b, const pgb_tc_opts& o, std::vector<uint8_t>& kind) {
+    const uint32_t p = b->p;
+    kind.assign(p, kPartEdge);
+    std::vector<uint8_t> host(p, 0);
+    if (o.mode == PGB_MODE_HYBRID) host = host_parts_by_cutoff(b, o.host_share_ppm ? o.host_share_ppm : 1000);
+    int v;
+    if (o.mode == PGB_MODE_PLAIN) v = o.variant == PGB_VAR_MERGE ? PGB_VAR_MERGE : PGB_VAR_BSEARCH;
+    else if (b->offloaded) v = PGB_VAR_HASH;  // only the hash kernel reads a streamed index
+    else v = o.variant;
+    bool hash_work = false, edge_work = false;
+    for (uint32_t j = 0; j < p; ++j) {
+        if (host[j]) {
+            kind[j] = kPartHost;
+            continue;
+        }
+        if (v == PGB_VAR_HASH) {
+            kind[j] = kPartHash;
+        } else if (v == PGB_VAR_AUTO) {
+            uint64_t edges = 0;
+            for (uint32_t i = 0; i <= j; ++i) edges += b->block_edges[(size_t)i * p + j];
+            const uint64_t probes = j < b->part_probes.size() ? b->part_probes[j] : 0;
+            kind[j] = (edges == 0 || probes >= kHashMinLookupsPerEdge * edges) ? kPartHash : kPartEdge;
+        }
+        const bool work = part_in_edges(b, j) > 0;
+        hash_work |= work && kind[j] == kPartHash;
+        edge_work |= work && kind[j] == kPartEdge;
+    }
+    if (v != PGB_VAR_AUTO) return v;
+    if (hash_work && edge_work) return PGB_VAR_MIXED;
+    return hash_work ? PGB_VAR_HASH : PGB_VAR_BSEARCH;
 }
 
 // Everything the device work of one run needs, allocated and planned before
@@ -406,21 +491,29 @@ struct RunPlan {
     DevBuf<Tuple> dt;
     DevBuf<uint32_t> dcp;
     uint32_t nt = 0, chunk = 0;
-    // PERSISTENT hash: work items
+    // PERSISTENT hash: work items (MIXED: those of the hash parts only)
     DevBuf<VItem> items;
     uint32_t nitems = 0;
     HashGraph H{};
-    DevBuf<unsigned int> cursor;
+    DevBuf<unsigned int> cursor;  // [0]: hash items, [1]: edge-wise chunks
     int grid = 0, threads = 128;
+    int hgrid = 0;                // general plans: CTAs of the hash launch (partials [0, hgrid))
+    bool general = false;         // parts split between kernels (and the host): filtered launches
+    bool host_slot = false;       // HYBRID: the last partial holds the host's total
+    std::vector<uint8_t> part_kind;
+    DevBuf<uint8_t> dpart_hash;
     const uint32_t* perm = nullptr;
-    // graph replay
+    // graph replay: the captured kernels read this plan-owned control block,
+    // which each replay refills with the run's stop word
+    DevBuf<RunCtl> ctl;
     cudaGraphExec_t exec = nullptr;
     uint64_t graph_launches = 0;  // kernel launches one replay makes
     cudaEvent_t done = nullptr;   // the last replay's outputs have been copied out
     bool used = false;
 
-    bool same(const pgb_tc_opts& o, int var) const {
-        return mode == o.mode && variant == var && order == o.order && per_vertex == (o.per_vertex != 0) &&
+    bool same(const pgb_tc_opts& o, int var, const std::vector<uint8_t>& kinds) const {
+        return mode == o.mode && variant == var && part_kind == kinds && order == o.order &&
+               per_vertex == (o.per_vertex != 0) &&
                per_triple == (o.mode == PGB_MODE_PLAIN && o.per_triple != 0) && chunk_edges == o.chunk_edges &&
                hash_threads_opt == o.hash_threads;
     }
@@ -430,8 +523,15 @@ struct RunPlan {
     }
 };
 
-static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& o, int variant, cudaStream_t s) {
+static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& o, int variant,
+                                        const std::vector<uint8_t>& part_kind, cudaStream_t s) {
     std::unique_ptr<RunPlan> P(new RunPlan());
+    P->part_kind = part_kind;
+    bool all_hash = true, any_host = false;
+    for (uint8_t k : part_kind) {
+        all_hash &= k == kPartHash;
+        any_host |= k == kPartHost;
+    }
     P->mode = o.mode;
     P->variant = variant;
     P->order = o.order;
@@ -446,9 +546,14 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
         P->tv.alloc(n, s);
         P->tv_orig.alloc(n, s);
     }
-    // the edge-wise (binary-search) kernels walk edges block by block
-    if (variant != PGB_VAR_HASH) ensure_block_edge_index(b, s);
-    P->G = Graph{b->bedge.ptr, b->rowidx.ptr, b->col.ptr, b->rowptr.ptr, P->tv.ptr};
+    // PLAIN launches walk the edges of one block A_ij (block-grouped index);
+    // the persistent edge-wise kernel walks head parts of the in-edge index
+    if (o.mode == PGB_MODE_PLAIN) {
+        ensure_block_edge_index(b, s);
+        P->G = Graph{b->bedge.ptr, nullptr, b->rowidx.ptr, b->col.ptr, b->rowptr.ptr, P->tv.ptr};
+    } else {
+        P->G = Graph{nullptr, b->xr.ptr, b->rowidx.ptr, b->col.ptr, b->rowptr.ptr, P->tv.ptr};
+    }
 
     if (o.mode == PGB_MODE_PLAIN) {
         // one launch per block triple, in queue order
@@ -472,46 +577,54 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
             PGB_CUDA(cudaMemcpyAsync(P->dseg.ptr, P->seg.data(), (T + 1) * 8, cudaMemcpyHostToDevice, s));
             P->triple_counts.alloc(T, s);
         }
-    } else if (variant == PGB_VAR_HASH) {
-        // middle-vertex hash variant (tc_hash.cu)
+    } else if (variant == PGB_VAR_HASH && all_hash) {
+        // middle-vertex hash variant over every head (tc_hash.cu)
         P->threads = o.hash_threads ? (int)o.hash_threads : hash_threads(b->n);
         P->nitems = build_hash_items(b, o.chunk_edges ? o.chunk_edges : kResidentInChunk, P->threads, s, P->items);
         if (P->nitems) {
             P->H = resident_hash_graph(b, P->tv.ptr);
-            P->cursor.alloc(1, s);
+            P->cursor.alloc(2, s);
             P->grid = hash_grid(P->per_vertex, P->threads);
             P->npartials = (uint64_t)P->grid;
             P->partials.alloc(P->npartials, s);
         }
     } else {
-        // tuples (A_ij, A_i[j..p-1], A_j[j..p-1]): one per non-empty block
-        // pair on the queue, ordered by the summed weight of its triples
+        // one tuple per head part j: the in-edges (u, v) with v in V_j, i.e.
+        // the block column A_*j with third range [c_j, n) (the tuples
+        // (A_ij, A_i[j..p-1], A_j[j..p-1]) of every i <= j), ordered by the
+        // summed weight of its triples (ORDER_LOCALITY: by j, descending)
+        // (head parts of the other kinds are left to the hash kernel or the host)
         const uint32_t p = b->p;
-        std::vector<uint64_t> w((size_t)p * p, 0);
-        for (const pgb_triple& q : b->triples) w[(size_t)q.i * p + q.j] += q.w;
+        P->general = true;
+        P->host_slot = any_host;
+        std::vector<uint64_t> w(p, 0);
+        for (const pgb_triple& q : b->triples) w[q.j] += q.w;
         std::vector<uint32_t> ids;
-        for (uint32_t ij = 0; ij < p * p; ++ij)
-            if (w[ij]) ids.push_back(ij);
-        if (o.order == PGB_ORDER_LOCALITY) {
-            std::stable_sort(ids.begin(), ids.end(), [&](uint32_t x, uint32_t y) {
-                if (x % p != y % p) return x % p > y % p;
-                return w[x] > w[y];
-            });
-        } else {
+        for (uint32_t j = 0; j < p; ++j)
+            if (w[j] && b->head_off[j + 1] > b->head_off[j] && P->part_kind[j] == kPartEdge) ids.push_back(j);
+        if (o.order == PGB_ORDER_LOCALITY)
+            std::stable_sort(ids.begin(), ids.end(), [&](uint32_t x, uint32_t y) { return x > y; });
+        else
             std::stable_sort(ids.begin(), ids.end(), [&](uint32_t x, uint32_t y) { return w[x] > w[y]; });
-        }
         const uint32_t chunk = P->chunk = o.chunk_edges ? ((o.chunk_edges + 31) / 32) * 32 : 64;
         std::vector<Tuple> tuples;
         std::vector<uint32_t> cp(1, 0);
-        for (uint32_t ij : ids) {
-            Tuple tu = make_tuple(b, ij / p, ij % p, ij % p, p - 1, variant);
+        const int tvar = variant == PGB_VAR_MERGE ? PGB_VAR_MERGE : PGB_VAR_BSEARCH;
+        for (uint32_t j : ids) {
+            Tuple tu;
+            tu.e_begin = (uint32_t)b->head_off[j];
+            tu.e_count = (uint32_t)(b->head_off[j + 1] - b->head_off[j]);
+            tu.lo = b->cuts[j];
+            tu.hi = b->n;
+            tu.clip = 0;  // every entry of both lists exceeds v >= c_j
+            tu.variant = (uint32_t)tvar;
             tuples.push_back(tu);
             cp.push_back(cp.back() + (tu.e_count + chunk - 1) / chunk);
         }
         const uint32_t nt = P->nt = (uint32_t)tuples.size();
         P->dt.alloc(std::max<uint32_t>(nt, 1), s);
         P->dcp.alloc(cp.size(), s);
-        P->cursor.alloc(1, s);
+        P->cursor.alloc(2, s);
         if (nt) PGB_CUDA(cudaMemcpyAsync(P->dt.ptr, tuples.data(), nt * sizeof(Tuple), cudaMemcpyHostToDevice, s));
         PGB_CUDA(cudaMemcpyAsync(P->dcp.ptr, cp.data(), cp.size() * 4, cudaMemcpyHostToDevice, s));
         int per_sm = 0;
@@ -521,7 +634,27 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
             PGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_persistent<false>, kThreads, 0));
         P->grid = std::max(1, per_sm) * sm_count();
         P->npartials = (uint64_t)P->grid;
+        bool hash_parts = false;
+        for (uint32_t j = 0; j < p; ++j) hash_parts |= P->part_kind[j] == kPartHash && b->head_off[j + 1] > b->head_off[j];
+        if (hash_parts) {
+            // the hash parts' items, counted by a hash launch before the
+            // edge-wise one; its per-CTA totals come first in partials
+            std::vector<uint8_t> mask(p);
+            for (uint32_t j = 0; j < p; ++j) mask[j] = P->part_kind[j] == kPartHash ? 1 : 0;
+            P->dpart_hash.alloc(p, s);
+            PGB_CUDA(cudaMemcpyAsync(P->dpart_hash.ptr, mask.data(), p, cudaMemcpyHostToDevice, s));
+            P->threads = o.hash_threads ? (int)o.hash_threads : hash_threads(b->n);
+            P->nitems = build_hash_items(b, o.chunk_edges ? o.chunk_edges : kResidentInChunk, P->threads, s,
+                                         P->items, P->dpart_hash.ptr);
+            if (P->nitems) {
+                P->H = resident_hash_graph(b, P->tv.ptr);
+                P->hgrid = hash_grid(P->per_vertex, P->threads);
+                P->npartials += (uint64_t)P->hgrid;
+            }
+        }
+        if (P->host_slot) P->npartials += 1;  // written once the host parts are counted
         P->partials.alloc(P->npartials, s);
+        if (P->host_slot) PGB_CUDA(cudaMemsetAsync(P->partials.ptr + P->npartials - 1, 0, 8, s));
     }
     // the host arrays copied above are pageable; their copies are staged
     // before the calls return, so the vectors may change afterwards
@@ -531,33 +664,54 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
 // The device work of a planned run: counters cleared, counting launches
 // (between ev0 and ev1 when given), reductions.  Makes no allocation and no
 // synchronising call, so it can be captured.
-static void enqueue(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+static void enqueue_reduce(const RunPlan& P, cudaStream_t s);
+
+// The device work of a planned run: the counting launches (between ev0 and
+// ev1 when given), then the reductions.
+static void enqueue_count(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, RunCtl* ctl);
+
+static void enqueue(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, RunCtl* ctl) {
+    enqueue_count(P, s, ev0, ev1, ctl);
+    enqueue_reduce(P, s);
+}
+
+static void enqueue_count(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, RunCtl* ctl) {
     if (P.per_vertex && P.n) PGB_CUDA(cudaMemsetAsync(P.tv.ptr, 0, (size_t)P.n * 8, s));
     if (ev0) PGB_CUDA(cudaEventRecord(ev0, s));
     if (P.mode == PGB_MODE_PLAIN) {
         const uint64_t T = P.tuples.size();
         for (uint64_t t = 0; t < T; ++t) {
             if (P.per_vertex)
-                k_tc_tuple<true><<<P.grids[t], kThreads, 0, s>>>(P.G, P.tuples[t], P.partials.ptr + P.seg[t]);
+                k_tc_tuple<true><<<P.grids[t], kThreads, 0, s>>>(P.G, P.tuples[t], P.partials.ptr + P.seg[t], ctl);
             else
-                k_tc_tuple<false><<<P.grids[t], kThreads, 0, s>>>(P.G, P.tuples[t], P.partials.ptr + P.seg[t]);
+                k_tc_tuple<false><<<P.grids[t], kThreads, 0, s>>>(P.G, P.tuples[t], P.partials.ptr + P.seg[t], ctl);
         }
         PGB_CHECK_LAUNCHES("k_tc_tuple", T);
-    } else if (P.variant == PGB_VAR_HASH) {
+    } else if (!P.general) {
         if (P.nitems)
             launch_hash(P.H, P.items.ptr, P.nitems, P.per_vertex, s, P.cursor.ptr, P.partials.ptr, P.grid,
-                        P.threads);
+                        P.threads, ctl);
     } else {
-        PGB_CUDA(cudaMemsetAsync(P.cursor.ptr, 0, 4, s));
+        // the hash parts first (their totals in partials [0, hgrid)), then
+        // the edge-wise tuples of the edge-wise parts
+        if (P.nitems && P.hgrid)
+            launch_hash(P.H, P.items.ptr, P.nitems, P.per_vertex, s, P.cursor.ptr, P.partials.ptr, P.hgrid,
+                        P.threads, ctl);
+        unsigned int* bcur = P.cursor.ptr + 1;
+        unsigned long long* bpart = P.partials.ptr + P.hgrid;
+        PGB_CUDA(cudaMemsetAsync(bcur, 0, 4, s));
         if (P.per_vertex)
-            k_tc_persistent<true><<<P.grid, kThreads, 0, s>>>(P.G, P.dt.ptr, P.dcp.ptr, P.nt, P.chunk, P.cursor.ptr,
-                                                             P.partials.ptr);
+            k_tc_persistent<true><<<P.grid, kThreads, 0, s>>>(P.G, P.dt.ptr, P.dcp.ptr, P.nt, P.chunk, bcur, bpart,
+                                                             ctl);
         else
-            k_tc_persistent<false><<<P.grid, kThreads, 0, s>>>(P.G, P.dt.ptr, P.dcp.ptr, P.nt, P.chunk,
-                                                              P.cursor.ptr, P.partials.ptr);
+            k_tc_persistent<false><<<P.grid, kThreads, 0, s>>>(P.G, P.dt.ptr, P.dcp.ptr, P.nt, P.chunk, bcur,
+                                                              bpart, ctl);
         PGB_CHECK_LAUNCH("k_tc_persistent");
     }
     if (ev1) PGB_CUDA(cudaEventRecord(ev1, s));
+}
+
+static void enqueue_reduce(const RunPlan& P, cudaStream_t s) {
     if (P.per_triple && !P.tuples.empty()) {
         k_reduce_segments<<<(unsigned)P.tuples.size(), 256, 0, s>>>(P.partials.ptr, P.dseg.ptr, P.triple_counts.ptr);
         PGB_CHECK_LAUNCH("k_reduce_segments");
@@ -583,7 +737,7 @@ static void capture(RunPlan& P) {
     int rc = guard([&] {
         begin_launch_capture(&launches);
         PGB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        int rc2 = guard([&] { enqueue(P, cs, nullptr, nullptr); });
+        int rc2 = guard([&] { enqueue(P, cs, nullptr, nullptr, P.ctl.ptr); });
         cudaError_t e = cudaStreamEndCapture(cs, &g);
         end_launch_capture();
         if (rc2 != PGB_OK) fail(rc2, pgb_last_error());
@@ -599,8 +753,14 @@ static void capture(RunPlan& P) {
 
 static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pgb_tc_result* r) {
     pgb_tc_opts o = o_in;
-    o.variant = choose_variant(b, o_in);
+    std::vector<uint8_t> part_kind;
+    o.variant = choose_variant(b, o_in, part_kind);
     r->variant = o.variant;
+    r->part_variant.resize(b->p);
+    for (uint32_t j = 0; j < b->p; ++j)
+        r->part_variant[j] = part_kind[j] == kPartHost   ? PGB_VAR_HOST
+                             : part_kind[j] == kPartHash ? PGB_VAR_HASH
+                             : (o.variant == PGB_VAR_MERGE ? PGB_VAR_MERGE : PGB_VAR_BSEARCH);
     const uint32_t n = b->n;
     r->stream = s;
     r->n = n;
@@ -609,6 +769,11 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
     r->ntriples = b->triples.size();
     PGB_CUDA(cudaEventCreate(&r->ev0));
     PGB_CUDA(cudaEventCreate(&r->ev1));
+    // the control block: the token's mapped word (or null), not cancelled;
+    // staged from the stack (a pageable copy returns once staged)
+    const RunCtl hctl{o.cancel ? o.cancel->dev : nullptr, 0u, 0u};
+    r->ctl.alloc(1, s);
+    PGB_CUDA(cudaMemcpyAsync(r->ctl.ptr, &hctl, sizeof(RunCtl), cudaMemcpyHostToDevice, s));
 
     if (b->offloaded) {
         // in-edge index in pinned host memory, streamed in chunks (stream.cu)
@@ -621,10 +786,10 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
         }
         if (b->cols_offloaded)
             run_column_streaming(b, r->per_vertex, o.hash_threads, tv.ptr, o.device_budget, s, partials, npartials,
-                                 r->ev0, r->ev1, &r->streamed, &r->chunks, &r->slice_loads);
+                                 r->ev0, r->ev1, &r->streamed, &r->chunks, &r->slice_loads, r->ctl.ptr);
         else
             run_streaming(b, o.chunk_edges, r->per_vertex, o.hash_threads, tv.ptr, o.device_budget, s, partials,
-                          npartials, r->ev0, r->ev1, &r->streamed, &r->chunks);
+                          npartials, r->ev0, r->ev1, &r->streamed, &r->chunks, r->ctl.ptr);
         if (npartials)
             k_reduce_sum<<<1, 1024, 0, s>>>(partials.ptr, npartials, r->total.ptr);
         else
@@ -640,9 +805,43 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
         }
         return;
     }
+    if (o.mode == PGB_MODE_HYBRID) {
+        // the device parts' launches are queued first; the host threads count
+        // the host parts meanwhile; their total fills the plan's last partial
+        // and their per-vertex counts are added before the reductions
+        std::unique_ptr<RunPlan> P = prepare(b, o, o.variant, part_kind, s);
+        enqueue_count(*P, s, r->ev0, r->ev1, r->ctl.ptr);
+        std::vector<uint8_t> host_mask(b->p);
+        for (uint32_t j = 0; j < b->p; ++j) host_mask[j] = part_kind[j] == kPartHost ? 1 : 0;
+        std::vector<unsigned long long> ht(r->per_vertex ? n : 0, 0);
+        const HostCountResult hr =
+            host_count_parts(b, host_mask, o.host_threads, r->per_vertex && n ? ht.data() : nullptr, o.cancel, s);
+        r->host_ms = hr.ms;
+        r->host_in_edges = hr.in_edges;
+        r->host_parts = hr.parts;
+        r->host_threads = hr.threads;
+        r->host_cancelled = hr.cancelled;
+        if (P->host_slot) {
+            const unsigned long long h_total = hr.total;
+            PGB_CUDA(cudaMemcpyAsync(P->partials.ptr + P->npartials - 1, &h_total, 8, cudaMemcpyHostToDevice, s));
+        }
+        DevBuf<unsigned long long> dht;
+        if (r->per_vertex && n && hr.parts) {
+            dht.alloc(n, s);
+            PGB_CUDA(cudaMemcpyAsync(dht.ptr, ht.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+            k_add_u64<<<std::min<uint32_t>((n + 255) / 256, 148 * 32), 256, 0, s>>>(P->tv.ptr, dht.ptr, n);
+            PGB_CHECK_LAUNCH("k_add_u64");
+        }
+        enqueue_reduce(*P, s);
+        // the host buffer is pageable: the copies above were staged before
+        // returning, so it may go out of scope
+        r->total = std::move(P->total);
+        r->tv_orig = std::move(P->tv_orig);
+        return;
+    }
     if (!o.use_graph) {
-        std::unique_ptr<RunPlan> P = prepare(b, o, o.variant, s);
-        enqueue(*P, s, r->ev0, r->ev1);
+        std::unique_ptr<RunPlan> P = prepare(b, o, o.variant, part_kind, s);
+        enqueue(*P, s, r->ev0, r->ev1, r->ctl.ptr);
         // the outputs move to the result; the rest is released in stream order
         r->total = std::move(P->total);
         r->tv_orig = std::move(P->tv_orig);
@@ -656,10 +855,11 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
     RunPlan* P = nullptr;
     for (auto& sp : b->run_plans) {
         RunPlan* q = static_cast<RunPlan*>(sp.get());
-        if (q->same(o, o.variant)) P = q;
+        if (q->same(o, o.variant, part_kind)) P = q;
     }
     if (!P) {
-        std::unique_ptr<RunPlan> fresh = prepare(b, o, o.variant, s);
+        std::unique_ptr<RunPlan> fresh = prepare(b, o, o.variant, part_kind, s);
+        fresh->ctl.alloc(1, s);
         PGB_CUDA(cudaStreamSynchronize(s));  // plan inputs in place before capture
         capture(*fresh);
         if (b->run_plans.size() >= 4) b->run_plans.erase(b->run_plans.begin());
@@ -667,12 +867,14 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
         b->run_plans.emplace_back(fresh.release(), [](void* q) { delete static_cast<RunPlan*>(q); });
     }
     if (P->used) PGB_CUDA(cudaStreamWaitEvent(s, P->done, 0));
+    PGB_CUDA(cudaMemcpyAsync(P->ctl.ptr, &hctl, sizeof(RunCtl), cudaMemcpyHostToDevice, s));
     PGB_CUDA(cudaEventRecord(r->ev0, s));
     PGB_CUDA(cudaGraphLaunch(P->exec, s));
     note_launches(P->graph_launches);
     PGB_CUDA(cudaEventRecord(r->ev1, s));
     r->total.alloc(1, s);
     PGB_CUDA(cudaMemcpyAsync(r->total.ptr, P->total.ptr, 8, cudaMemcpyDeviceToDevice, s));
+    PGB_CUDA(cudaMemcpyAsync(r->ctl.ptr, P->ctl.ptr, sizeof(RunCtl), cudaMemcpyDeviceToDevice, s));
     if (r->per_vertex) {
         r->tv_orig.alloc(n, s);
         if (n) PGB_CUDA(cudaMemcpyAsync(r->tv_orig.ptr, P->tv_orig.ptr, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
@@ -706,7 +908,11 @@ int pgb_tc_run(const pgb_blocks* b, const pgb_tc_opts* opts, void* stream, pgb_t
         if (!b || !out) fail(PGB_E_INVAL, "NULL argument");
         pgb_tc_opts o;
         if (opts) o = *opts; else pgb_tc_opts_default(&o);
-        if (o.mode != PGB_MODE_PLAIN && o.mode != PGB_MODE_PERSISTENT) fail(PGB_E_INVAL, "bad mode");
+        if (o.mode != PGB_MODE_PLAIN && o.mode != PGB_MODE_PERSISTENT && o.mode != PGB_MODE_HYBRID)
+            fail(PGB_E_INVAL, "bad mode");
+        if (o.mode == PGB_MODE_HYBRID && (b->offloaded || o.use_graph))
+            fail(PGB_E_STATE, "HYBRID runs need resident blocks and no graph replay");
+        if (o.host_share_ppm > 1000000) fail(PGB_E_INVAL, "host_share_ppm must be at most 10^6");
         if (o.variant < PGB_VAR_AUTO || o.variant > PGB_VAR_HASH) fail(PGB_E_INVAL, "bad variant");
         if (o.mode == PGB_MODE_PLAIN && o.variant == PGB_VAR_HASH)
             fail(PGB_E_INVAL, "PLAIN mode runs the edge-wise variants (binary search, merge) only");
@@ -727,6 +933,11 @@ int pgb_tc_result_get(pgb_tc_result* r, uint64_t* total, uint64_t* per_vertex, i
     return guard([&] {
         if (!r) fail(PGB_E_INVAL, "result is NULL");
         cudaStream_t s = r->stream;
+        uint32_t cancelled = 0;
+        PGB_CUDA(cudaMemcpyAsync(&cancelled, &r->ctl.ptr->cancelled, 4, cudaMemcpyDeviceToHost, s));
+        PGB_CUDA(cudaStreamSynchronize(s));
+        if (cancelled || r->host_cancelled)
+            fail(PGB_E_CANCELLED, "the run stopped early on its cancel token; its counts are incomplete");
         if (per_vertex) {
             if (!r->per_vertex) fail(PGB_E_STATE, "run was made without per-vertex counts");
             copy_out(per_vertex, r->tv_orig.ptr, (size_t)r->n * 8, mem, s);
@@ -754,6 +965,26 @@ int pgb_tc_result_variant(pgb_tc_result* r, int* variant) {
     return guard([&] {
         if (!r || !variant) fail(PGB_E_INVAL, "NULL argument");
         *variant = r->variant;
+    });
+}
+
+int pgb_tc_result_part_variants(pgb_tc_result* r, uint32_t* p, int32_t* variants) {
+    return guard([&] {
+        if (!r || !p) fail(PGB_E_INVAL, "NULL argument");
+        *p = (uint32_t)r->part_variant.size();
+        if (variants && !r->part_variant.empty())
+            std::memcpy(variants, r->part_variant.data(), r->part_variant.size() * sizeof(int32_t));
+    });
+}
+
+int pgb_tc_result_hybrid(pgb_tc_result* r, float* host_ms, uint64_t* host_in_edges, uint32_t* host_parts,
+                         uint32_t* host_threads) {
+    return guard([&] {
+        if (!r) fail(PGB_E_INVAL, "result is NULL");
+        if (host_ms) *host_ms = r->host_ms;
+        if (host_in_edges) *host_in_edges = r->host_in_edges;
+        if (host_parts) *host_parts = r->host_parts;
+        if (host_threads) *host_threads = r->host_threads;
     });
 }
 

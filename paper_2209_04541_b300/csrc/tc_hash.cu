@@ -142,12 +142,25 @@ struct WindowInfo {
     uint32_t run_len, run_mask, run_keys;  // a run starting at this lane (run_len > 0)
 };
 
+// Whether head v is counted by this kernel under the per-part filter.
+__device__ __forceinline__ bool head_selected(const ItemSpace& sp, uint32_t v) {
+    if (!sp.part_hash) return true;
+    uint32_t lo = 0, hi = sp.p;  // largest j in [0, p) with cuts[j] <= v
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(sp.cuts + mid) <= v) lo = mid; else hi = mid;
+    }
+    return __ldg(sp.part_hash + lo) != 0;
+}
+
 __device__ __forceinline__ WindowInfo window_info(const ItemSpace& sp, uint32_t w, uint32_t in_chunk, int lane) {
     WindowInfo W;
     W.v = sp.w0 + w * 32 + lane;
     W.dp = W.dm = 0;
     if (W.v < sp.n) {
-        W.dp = sp.rowptr[W.v + 1] - sp.rowptr[W.v];
+        // a head outside the filter keeps its in-edges (they lie inside any
+        // run's range) but no list, so it is never an active member
+        W.dp = head_selected(sp, W.v) ? sp.rowptr[W.v + 1] - sp.rowptr[W.v] : 0;
         W.dm = sp.colptr[W.v + 1 - sp.cbase] - sp.colptr[W.v - sp.cbase];
     }
     W.act = W.dp > 0 && W.dm > 0;
@@ -292,7 +305,8 @@ __global__ void k_items_emit(const ItemSpace sp, uint32_t in_chunk, const uint32
 template <bool PV, int T>
 __global__ void __launch_bounds__(T, 1024 / T)
     k_tc_hash(const HashGraph G, const VItem* __restrict__ items,
-              uint32_t nitems, unsigned int* __restrict__ cursor, unsigned long long* __restrict__ partials) {
+              uint32_t nitems, unsigned int* __restrict__ cursor, unsigned long long* __restrict__ partials,
+              RunCtl* __restrict__ ctl) {
     extern __shared__ uint32_t hsm[];
     // Region A: the bitmap of a bitmap-mode item, or the keys and member
     // masks of a hash-mode item; all zero between items.  Region B (per-vertex
@@ -318,8 +332,14 @@ __global__ void __launch_bounds__(T, 1024 / T)
     if (PV) s_edge[warp][lane] = 0;
     // thread 0 fetches the next item, and a singleton's row bounds, ahead
     // into the second shared slot
+    // every kStopCheckEvery-th fetch also reads the run's stop word; a stop
+    // pushes the cursor past the end, so every CTA ends after its item
     auto prefetch = [&] {
         s_itemn = atomicAdd(cursor, 1u);
+        if (s_itemn % kStopCheckEvery == 0 && s_itemn < nitems && run_stop_requested(ctl)) {
+            atomicMax(cursor, nitems);
+            s_itemn = nitems;
+        }
         if (s_itemn < nitems) {
             const VItem nx = items[s_itemn];
             s_itn = nx;
@@ -625,8 +645,8 @@ int grid_of() {
 
 template <bool PV, int T>
 void launch_shape(const HashGraph& G, const VItem* items, uint32_t nitems, cudaStream_t s, unsigned int* cursor,
-                  unsigned long long* partials, int grid) {
-    k_tc_hash<PV, T><<<grid, T, hash_smem<PV, T>(), s>>>(G, items, nitems, cursor, partials);
+                  unsigned long long* partials, int grid, RunCtl* ctl) {
+    k_tc_hash<PV, T><<<grid, T, hash_smem<PV, T>(), s>>>(G, items, nitems, cursor, partials, ctl);
 }
 
 }  // namespace
@@ -661,13 +681,18 @@ uint32_t build_hash_items_in(const ItemSpace& sp, uint32_t in_chunk, cudaStream_
 }
 
 uint32_t build_hash_items(const pgb_blocks* b, uint32_t in_chunk, int threads, cudaStream_t s,
-                          DevBuf<VItem>& items) {
+                          DevBuf<VItem>& items, const uint8_t* part_hash) {
     if (b->m == 0) {
         items.alloc(1, s);
         return 0;
     }
-    const ItemSpace sp{b->rowptr.ptr, b->colptr.ptr, b->col.ptr, 0, 0, 0, (b->n + 31) / 32, b->n,
-                       key_capacity(threads), bitmap_range(threads)};
+    ItemSpace sp{b->rowptr.ptr, b->colptr.ptr, b->col.ptr, 0, 0, 0, (b->n + 31) / 32, b->n,
+                 key_capacity(threads), bitmap_range(threads)};
+    if (part_hash) {
+        sp.part_hash = part_hash;
+        sp.cuts = b->cuts_d.ptr;
+        sp.p = b->p;
+    }
     return build_hash_items_in(sp, in_chunk, s, items);
 }
 
@@ -686,20 +711,20 @@ int hash_grid(bool pv, int threads) {
 }
 
 void launch_hash(const HashGraph& G, const VItem* items, uint32_t nitems, bool pv, cudaStream_t s,
-                 unsigned int* cursor, unsigned long long* partials, int grid, int threads) {
+                 unsigned int* cursor, unsigned long long* partials, int grid, int threads, RunCtl* ctl) {
     // the pair loads read 32 aligned bytes at colu + (8k - ubase)
     if ((reinterpret_cast<uintptr_t>(G.colu) & 31) || (G.ubase & 7))
         fail(PGB_E_INVAL, "tail column view is not 32-byte aligned");
     PGB_CUDA(cudaMemsetAsync(cursor, 0, 4, s));
     if (threads == 512) {
-        if (pv) launch_shape<true, 512>(G, items, nitems, s, cursor, partials, grid);
-        else launch_shape<false, 512>(G, items, nitems, s, cursor, partials, grid);
+        if (pv) launch_shape<true, 512>(G, items, nitems, s, cursor, partials, grid, ctl);
+        else launch_shape<false, 512>(G, items, nitems, s, cursor, partials, grid, ctl);
     } else if (threads == 256) {
-        if (pv) launch_shape<true, 256>(G, items, nitems, s, cursor, partials, grid);
-        else launch_shape<false, 256>(G, items, nitems, s, cursor, partials, grid);
+        if (pv) launch_shape<true, 256>(G, items, nitems, s, cursor, partials, grid, ctl);
+        else launch_shape<false, 256>(G, items, nitems, s, cursor, partials, grid, ctl);
     } else {
-        if (pv) launch_shape<true, 128>(G, items, nitems, s, cursor, partials, grid);
-        else launch_shape<false, 128>(G, items, nitems, s, cursor, partials, grid);
+        if (pv) launch_shape<true, 128>(G, items, nitems, s, cursor, partials, grid, ctl);
+        else launch_shape<false, 128>(G, items, nitems, s, cursor, partials, grid, ctl);
     }
     PGB_CHECK_LAUNCH("k_tc_hash");
 }

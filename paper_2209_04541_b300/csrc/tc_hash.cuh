@@ -27,6 +27,11 @@ struct ItemSpace {
     uint32_t cbase, vbase, w0, nwin, n;
     uint32_t keycap;       // table keys per item: 1024 (fits both CTA shapes) or 2048 (256 threads only)
     uint32_t bitmap_bits;  // widest range a singleton holds as a bitmap (such vertices are never grouped)
+    // optional filter: only heads v whose part j (cuts[j] <= v < cuts[j+1])
+    // has part_hash[j] != 0 get work items (null: every head)
+    const uint8_t* part_hash = nullptr;
+    const uint32_t* cuts = nullptr;
+    uint32_t p = 0;
 };
 
 // One work item of the middle-vertex kernel (built on the device).
@@ -44,8 +49,11 @@ struct VItem {
 // Work items of one partitioned graph for the hash kernel with `threads`
 // per CTA; returns their number (synchronises `s` once to learn it).
 // in_chunk: in-edges per item (0 = the default for streamed runs, 4,096).
+// part_hash (device, p bytes, may be null): only heads in parts with a
+// non-zero entry get items; the other parts' triangles are left to the
+// edge-wise kernel (per-part autotuning).
 uint32_t build_hash_items(const pgb_blocks* b, uint32_t in_chunk, int threads, cudaStream_t s,
-                          DevBuf<VItem>& items);
+                          DevBuf<VItem>& items, const uint8_t* part_hash = nullptr);
 
 // In-edges per work item of a resident run when the caller sets none: larger
 // items amortise the per-item table build and barrier (measured 0.5% faster
@@ -68,9 +76,10 @@ int hash_threads(uint32_t n);
 int hash_grid(bool pv, int threads);
 
 // One persistent launch over `nitems` work items of graph G; partials must
-// hold `grid` entries and receive one total per CTA.
+// hold `grid` entries and receive one total per CTA.  ctl (device memory,
+// may be null): the run's stop word, read every kStopCheckEvery fetches.
 void launch_hash(const HashGraph& G, const VItem* items, uint32_t nitems, bool pv, cudaStream_t s,
-                 unsigned int* cursor, unsigned long long* partials, int grid, int threads);
+                 unsigned int* cursor, unsigned long long* partials, int grid, int threads, RunCtl* ctl);
 
 // Streamed run over blocks whose in-edge index is in pinned host memory:
 // chunks of work items whose in-edges fit two device slots within `budget`
@@ -80,7 +89,7 @@ void launch_hash(const HashGraph& G, const VItem* items, uint32_t nitems, bool p
 void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint32_t threads, unsigned long long* tv,
                    uint64_t budget,
                    cudaStream_t s, DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
-                   cudaEvent_t ev1, uint64_t* streamed, uint32_t* nchunks);
+                   cudaEvent_t ev1, uint64_t* streamed, uint32_t* nchunks, RunCtl* ctl);
 
 // Run over blocks whose columns are offloaded too: pieces of block pairs
 // (tail block, head block) with their column slices in a device cache that
@@ -89,6 +98,7 @@ void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint32_t thr
 void run_column_streaming(const pgb_blocks* b, bool pv, uint32_t threads, unsigned long long* tv, uint64_t budget,
                           cudaStream_t s,
                           DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
-                          cudaEvent_t ev1, uint64_t* streamed, uint32_t* npieces, uint32_t* slice_loads);
+                          cudaEvent_t ev1, uint64_t* streamed, uint32_t* npieces, uint32_t* slice_loads,
+                          RunCtl* ctl);
 
 }  // namespace pgb

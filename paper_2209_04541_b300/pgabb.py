@@ -40,11 +40,14 @@ PGB_CUT_UNIFORM = 1
 
 PGB_MODE_PLAIN = 0
 PGB_MODE_PERSISTENT = 1
+PGB_MODE_HYBRID = 2
 
 PGB_VAR_AUTO = 0
 PGB_VAR_BSEARCH = 1
 PGB_VAR_MERGE = 2
 PGB_VAR_HASH = 3
+PGB_VAR_MIXED = 4
+PGB_VAR_HOST = 5
 
 PGB_ORDER_WEIGHT = 0
 PGB_ORDER_LOCALITY = 1
@@ -56,6 +59,7 @@ PGB_EXPORT_CUTS = 3
 PGB_EXPORT_BLOCK_EDGES = 4
 PGB_EXPORT_TRIPLES = 5
 PGB_EXPORT_WEIGHTS = 6
+PGB_EXPORT_PART_PROBES = 7
 
 HEADER = os.path.join(_build.INCLUDE, "pgabb.h")
 
@@ -70,7 +74,8 @@ class TcOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("variant", ctypes.c_int32), ("per_vertex", ctypes.c_int32),
                 ("per_triple", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("device_budget", ctypes.c_uint64), ("chunk_edges", ctypes.c_uint32),
-                ("hash_threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 6)]
+                ("hash_threads", ctypes.c_uint32), ("cancel", ctypes.c_void_p), ("host_threads", ctypes.c_uint32),
+                ("host_share_ppm", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
 
 
 class BlocksStats(ctypes.Structure):
@@ -108,6 +113,9 @@ _SIGS = {
     "pgb_tc_result_triples": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "pgb_tc_result_kernel_ms": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "pgb_tc_result_variant": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "pgb_tc_result_part_variants": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint32), _VP]),
+    "pgb_tc_result_hybrid": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64),
+                                            ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
     "pgb_tc_result_stream": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32),
                                             ctypes.POINTER(ctypes.c_uint32)]),
     "pgb_blocks_offload_columns": (ctypes.c_int, [_VP, ctypes.c_uint32, _VP]),
@@ -133,6 +141,11 @@ _SIGS = {
     "pgb_server_cancel": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "pgb_server_stats": (ctypes.c_int, [_VP, _VP]),
     "pgb_server_destroy": (None, [_VP]),
+    "pgb_cancel_create": (ctypes.c_int, [ctypes.POINTER(_VP)]),
+    "pgb_cancel_set": (ctypes.c_int, [_VP]),
+    "pgb_cancel_reset": (ctypes.c_int, [_VP]),
+    "pgb_cancel_is_set": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "pgb_cancel_free": (None, [_VP]),
 }
 
 PGB_NOALLOC_MAX_VERTICES = 1 << 20
@@ -258,6 +271,10 @@ class Blocks(_Handle):
     _free_name = "pgb_blocks_free"
 
 
+class Cancel(_Handle):
+    _free_name = "pgb_cancel_free"
+
+
 class Result(_Handle):
     _free_name = "pgb_tc_result_free"
 
@@ -357,6 +374,7 @@ def pgb_blocks_export(b: Blocks, what: int) -> np.ndarray:
         PGB_EXPORT_BLOCK_EDGES: (np.uint64, p * p),
         PGB_EXPORT_TRIPLES: (np.uint32, 3 * T),
         PGB_EXPORT_WEIGHTS: (np.uint64, T),
+        PGB_EXPORT_PART_PROBES: (np.uint64, p),
     }
     dt, cnt = spec[what]
     out = np.zeros(cnt, dtype=dt)
@@ -380,13 +398,41 @@ def pgb_blocks_offload(b: Blocks, stream=None):
 
 
 def pgb_tc_opts_default(**kw) -> TcOpts:
+    """Default run options with the given fields changed (``cancel`` takes a
+    Cancel token, which the caller keeps alive while the run is in use)."""
     o = TcOpts()
     load().pgb_tc_opts_default(ctypes.byref(o))
     for k, v in kw.items():
         if not hasattr(o, k):
             raise AttributeError(k)
+        if isinstance(v, _Handle):
+            v = v.ptr
         setattr(o, k, v)
     return o
+
+
+def pgb_cancel_create() -> Cancel:
+    out = ctypes.c_void_p()
+    _check(load().pgb_cancel_create(ctypes.byref(out)), "pgb_cancel_create")
+    return Cancel(out.value, None)
+
+
+def pgb_cancel_set(c: Cancel):
+    _check(load().pgb_cancel_set(c), "pgb_cancel_set")
+
+
+def pgb_cancel_reset(c: Cancel):
+    _check(load().pgb_cancel_reset(c), "pgb_cancel_reset")
+
+
+def pgb_cancel_is_set(c: Cancel) -> bool:
+    v = ctypes.c_int()
+    _check(load().pgb_cancel_is_set(c, ctypes.byref(v)), "pgb_cancel_is_set")
+    return bool(v.value)
+
+
+def pgb_cancel_free(c: Cancel):
+    c.free()
 
 
 def pgb_tc_run(b: Blocks, opts: TcOpts | None = None, stream=None) -> Result:
@@ -432,6 +478,25 @@ def pgb_tc_result_variant(r: Result) -> int:
     v = ctypes.c_int()
     _check(load().pgb_tc_result_variant(r, ctypes.byref(v)), "pgb_tc_result_variant")
     return int(v.value)
+
+
+def pgb_tc_result_part_variants(r: Result) -> np.ndarray:
+    """The kernel (PGB_VAR_*) that counted each head part of the run."""
+    p = ctypes.c_uint32()
+    _check(load().pgb_tc_result_part_variants(r, ctypes.byref(p), None), "pgb_tc_result_part_variants")
+    out = np.zeros(p.value, dtype=np.int32)
+    _check(load().pgb_tc_result_part_variants(r, ctypes.byref(p), out.ctypes.data if p.value else None),
+           "pgb_tc_result_part_variants")
+    return out
+
+
+def pgb_tc_result_hybrid(r: Result) -> dict:
+    """HYBRID runs: the host kernel's wall ms, in-edges, parts and threads."""
+    ms, ie, parts, th = ctypes.c_float(), ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load().pgb_tc_result_hybrid(r, ctypes.byref(ms), ctypes.byref(ie), ctypes.byref(parts), ctypes.byref(th)),
+           "pgb_tc_result_hybrid")
+    return {"host_ms": float(ms.value), "host_in_edges": int(ie.value), "host_parts": int(parts.value),
+            "host_threads": int(th.value)}
 
 
 def pgb_blocks_offload_columns(b: Blocks, slices: int = 0, stream=None):

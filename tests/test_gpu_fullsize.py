@@ -2,16 +2,19 @@
 
 Expected values come from the oracle only, written by
 ``tests/golden/make_golden.py`` into ``tests/golden/full_<name>.txt``: the
-exact triangle total and t[x] for a seeded vertex sample (the highest-degree
-vertices plus uniform draws).  The checks are bit-exact (tolerance 0):
-total, every sampled per-vertex count, and sum(t) = 3 T over all n vertices.
+exact triangle total, the SHA-256 of all n per-vertex counts (uint64
+little-endian, original vertex IDs), and t[x] for a seeded vertex sample by
+the oracle's one-vertex count.  The checks are bit-exact (tolerance 0):
+total, every per-vertex count (through the digest), every sampled count,
+and sum(t) = 3 T.
 
 R-MAT scale 20 (p = 16) runs in the plain one-launch-per-triple mode and in
-the persistent mode; R-MAT scale 24 (p = 32) runs in the launch
-configuration bench.py times (persistent, automatic variant, per-vertex);
-R-MAT scale 27 (p = 64) checks sampled per-vertex counts (the oracle's total
-at that size would take hours), resident and streamed.
+the persistent mode; R-MAT scale 24 (p = 32) and the 4096 x 4096 grid with
+1% extra edges (p = 32) run in the launch configuration bench.py times
+(persistent, automatic variant, per-vertex); R-MAT scale 27 (p = 64) runs
+resident and with the in-edge index streamed under a 16 GiB budget.
 """
+import hashlib
 import os
 import sys
 
@@ -29,9 +32,13 @@ sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "gol
 import make_golden  # noqa: E402
 
 
-def run_full(name, scale, p, mode, variant=P.PGB_VAR_AUTO, stream_budget=None):
+def digest(t):
+    return hashlib.sha256(np.ascontiguousarray(t, dtype="<u8").tobytes()).hexdigest()
+
+
+def run_full(name, p, mode, variant=P.PGB_VAR_AUTO, stream_budget=None):
     want = make_golden.load(name)
-    src, dst, n = graphgen.rmat(scale, 16, 1)
+    src, dst, n = make_golden.generate(make_golden.WORKLOADS[name])
     assert n == want["n"]
     ds = torch.from_numpy(src).cuda()
     dd = torch.from_numpy(dst).cuda()
@@ -44,9 +51,9 @@ def run_full(name, scale, p, mode, variant=P.PGB_VAR_AUTO, stream_budget=None):
     tv = torch.zeros(n, dtype=torch.uint64, device="cuda")
     r = P.pgb_tc_run(b, P.pgb_tc_opts_default(mode=mode, variant=variant))
     T, _ = P.pgb_tc_result_get(r, per_vertex=tv)
-    if "T" in want:
-        assert T == want["T"]
+    assert T == want["T"]
     t = tv.cpu().numpy()
+    assert digest(t) == want["t_sha256"], "per-vertex counts differ from the oracle's"
     assert np.array_equal(t[want["x"]], want["t"])
     assert int(t.sum(dtype=np.uint64)) == 3 * T
     if stream_budget is not None:
@@ -60,21 +67,25 @@ def run_full(name, scale, p, mode, variant=P.PGB_VAR_AUTO, stream_budget=None):
 
 @pytest.mark.parametrize("mode", [P.PGB_MODE_PLAIN, P.PGB_MODE_PERSISTENT])
 def test_rmat20_p16_full_size(mode):
-    run_full("rmat20", 20, 16, mode)
+    run_full("rmat20", 16, mode)
 
 
 def test_rmat24_p32_full_size_bench_configuration():
-    run_full("rmat24", 24, 32, P.PGB_MODE_PERSISTENT)
+    run_full("rmat24", 32, P.PGB_MODE_PERSISTENT)
 
 
 def test_rmat24_p32_full_size_bsearch_variant():
-    run_full("rmat24", 24, 32, P.PGB_MODE_PERSISTENT, P.PGB_VAR_BSEARCH)
+    run_full("rmat24", 32, P.PGB_MODE_PERSISTENT, P.PGB_VAR_BSEARCH)
 
 
-@pytest.mark.skipif(not os.path.exists(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
-                                                    "full_rmat27.txt")), reason="no oracle values for scale 27")
+@pytest.mark.parametrize("mode", [P.PGB_MODE_PLAIN, P.PGB_MODE_PERSISTENT])
+def test_grid4096_p32_full_size(mode):
+    """The 4096 x 4096 grid with 1% uniform extra edges at full size."""
+    run_full("grid4096", 32, mode)
+
+
 def test_rmat27_p64_full_size_and_streamed():
-    """R-MAT scale 27 (2.1 G edges, the 256-thread shape): the oracle's
+    """R-MAT scale 27 (2.1 G edges, the autotuned 512-thread shape): the oracle's
     sampled t[x], sum t = 3 T, and the same counts with the in-edge index
     streamed under a 16 GiB budget."""
-    run_full("rmat27", 27, 64, P.PGB_MODE_PERSISTENT, stream_budget=16 << 30)
+    run_full("rmat27", 64, P.PGB_MODE_PERSISTENT, stream_budget=16 << 30)

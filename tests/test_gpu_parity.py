@@ -329,18 +329,3 @@ def test_merge_long_balanced_lists():
                                               per_triple=True)
                 assert np.array_equal(tri, tri_b)
 
-
-def test_autotuner_choice_and_counts():
-    """AUTO picks the edge-wise kernel for a flat grid (short lists) and the
-    middle-vertex hash kernel for R-MAT (long lists); counts match either way."""
-    for (src, dst, n), want in ((graphgen.grid_plus_percent(128, 1.0, 4), P.PGB_VAR_BSEARCH),
-                                (graphgen.rmat(16, 16, 8), P.PGB_VAR_HASH)):
-        oT, ot, _ = oracle_count(src, dst, n)
-        g = P.pgb_graph_from_edges(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), n)
-        b = P.pgb_partition(g, 8)
-        info = P.pgb_blocks_info(b)
-        assert (info["probes"] >= 32 * info["m"]) == (want == P.PGB_VAR_HASH)
-        r = P.pgb_tc_run(b)
-        assert P.pgb_tc_result_variant(r) == want
-        T, t = P.pgb_tc_result_get(r)
-        assert T == oT and np.array_equal(t, ot)
