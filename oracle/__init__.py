@@ -31,6 +31,13 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
                    triangle by the definition of the parts, and
                    hand-derived values on a 6-vertex graph.
   tc_forward_mt    pinned: equals tc_forward (total and every t[x]).
+  cc_min_label     pinned: networkx connected components (a library
+                   routine), closed forms (disjoint cliques, paths,
+                   isolated vertices), relabelling.
+  pagerank         pinned: uniform ranks on regular graphs and the star's
+                   fixed point (closed forms), networkx.pagerank on graphs
+                   without isolated vertices (a library routine), sum of
+                   ranks 1 without isolated vertices, iteration limit.
 """
 from __future__ import annotations
 
@@ -97,6 +104,12 @@ def _bind(lib):
     lib.or_tc_forward.restype = ctypes.c_uint64
     lib.or_alg_bytes.argtypes = [ctypes.c_uint32, i64p, u32p]
     lib.or_alg_bytes.restype = ctypes.c_uint64
+    lib.or_cc_min_label.argtypes = [ctypes.c_uint32, i64p, u32p, u32p]
+    lib.or_cc_min_label.restype = ctypes.c_int64
+    f64p = ctypes.POINTER(ctypes.c_double)
+    lib.or_pagerank.argtypes = [ctypes.c_uint32, i64p, u32p, ctypes.c_double, ctypes.c_double, ctypes.c_int, f64p,
+                                f64p]
+    lib.or_pagerank.restype = ctypes.c_int
     if hasattr(lib, "or_tc_forward_mt"):
         lib.or_tc_forward_mt.argtypes = [ctypes.c_uint32, i64p, u32p, u64p, ctypes.c_int, ctypes.c_uint32]
         lib.or_tc_forward_mt.restype = ctypes.c_uint64
@@ -275,6 +288,26 @@ def tc_forward_mt(o: Oriented, per_vertex: bool = True, threads: int = 0, stride
         t_orig = np.zeros(n, dtype=np.uint64)
         t_orig[o.perm] = t[:n]
     return int(tot), t_orig
+
+
+def cc_min_label(g: Graph):
+    """(labels, components): label[x] = smallest vertex ID in x's component."""
+    lab = np.zeros(max(g.n, 1), dtype=np.uint32)
+    c = g.lib.or_cc_min_label(g.n, _p(g.offs, ctypes.c_int64), _p(g.adj, ctypes.c_uint32), _p(lab, ctypes.c_uint32))
+    if c < 0:
+        raise MemoryError("components queue")
+    return lab[: g.n], int(c)
+
+
+def pagerank(g: Graph, damping: float = 0.85, tol: float = 1e-4, max_iter: int = 20):
+    """(ranks float64[n], iterations, last L1 change) of the undirected graph."""
+    r = np.zeros(max(g.n, 1), dtype=np.float64)
+    err = ctypes.c_double()
+    it = g.lib.or_pagerank(g.n, _p(g.offs, ctypes.c_int64), _p(g.adj, ctypes.c_uint32), damping, tol, max_iter,
+                           _p(r, ctypes.c_double), ctypes.byref(err))
+    if it < 0:
+        raise MemoryError("rank arrays")
+    return r[: g.n], int(it), float(err.value)
 
 
 def alg_bytes(o: Oriented) -> int:

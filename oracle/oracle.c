@@ -32,10 +32,16 @@
  *   or_tc_vertex_sample   or_tc_vertex over a list of vertices.
  *   or_tc_forward_mt      or_tc_forward with its rows shared among OpenMP
  *                         threads (only in the -fopenmp build); same counts.
+ *   or_cc_min_label       Section 3.4 (Shiloach-Vishkin solves connected
+ *                         components): each vertex labelled with the
+ *                         smallest vertex ID of its component.
+ *   or_pagerank           Section 5.2.1: PageRank on the undirected graph,
+ *                         damping d, L1 error tolerance, iteration limit.
  *
  * The plain build (no -fopenmp) is single-threaded and is the reference;
  * the OpenMP build differs only in or_tc_forward_mt.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -397,4 +403,82 @@ uint64_t or_alg_bytes(uint32_t n, const int64_t* rowptr, const uint32_t* col) {
     for (uint32_t v = 0; v < n; ++v) wedge += indeg[v] * (uint64_t)(rowptr[v + 1] - rowptr[v]);
     free(indeg);
     return 4 * m + 4 * wedge + 8 * ((uint64_t)n + 1);
+}
+
+/* ------------------------------------------------ connected components */
+
+/*
+ * label[x] = the smallest vertex ID of x's connected component.  Vertices
+ * are visited in ascending ID order; each one not yet labelled starts a
+ * breadth-first search that labels everything it reaches with the start's
+ * ID (the first vertex of a component met in ascending order is its
+ * smallest).  Returns the number of components, or -2 without memory.
+ */
+int64_t or_cc_min_label(uint32_t n, const int64_t* offs, const uint32_t* adj, uint32_t* label) {
+    uint32_t* queue = (uint32_t*)malloc(((size_t)n + 1) * sizeof(uint32_t));
+    if (!queue) return -2;
+    for (uint32_t v = 0; v < n; ++v) label[v] = UINT32_MAX;
+    int64_t comps = 0;
+    for (uint32_t s = 0; s < n; ++s) {
+        if (label[s] != UINT32_MAX) continue;
+        ++comps;
+        size_t head = 0, tail = 0;
+        label[s] = s;
+        queue[tail++] = s;
+        while (head < tail) {
+            uint32_t x = queue[head++];
+            for (int64_t e = offs[x]; e < offs[x + 1]; ++e) {
+                uint32_t y = adj[e];
+                if (label[y] == UINT32_MAX) {
+                    label[y] = s;
+                    queue[tail++] = y;
+                }
+            }
+        }
+    }
+    free(queue);
+    return comps;
+}
+
+/* ------------------------------------------------------------ PageRank */
+
+/*
+ * PageRank of the undirected graph (every edge counts in both directions),
+ * in double precision:
+ *   r_0(v)     = 1 / n
+ *   r_t+1(v)   = (1 - d) / n + d * sum over neighbours u of r_t(u) / deg(u)
+ * (a vertex of degree 0 passes nothing on).  After each iteration the L1
+ * change sum_v |r_t+1(v) - r_t(v)| is compared with tol; the iteration
+ * stops at the first change below tol, or after max_iter iterations.
+ * rank gets r for the last iteration made; returns the iterations made
+ * (*err: the last change), or -2 without memory.
+ */
+int or_pagerank(uint32_t n, const int64_t* offs, const uint32_t* adj, double d, double tol, int max_iter,
+                double* rank, double* err) {
+    double* cur = (double*)malloc(((size_t)n + 1) * sizeof(double));
+    double* nxt = (double*)malloc(((size_t)n + 1) * sizeof(double));
+    if (!cur || !nxt) { free(cur); free(nxt); return -2; }
+    for (uint32_t v = 0; v < n; ++v) cur[v] = 1.0 / n;
+    int it = 0;
+    double change = 0.0;
+    while (it < max_iter) {
+        change = 0.0;
+        for (uint32_t v = 0; v < n; ++v) {
+            double sum = 0.0;
+            for (int64_t e = offs[v]; e < offs[v + 1]; ++e) {
+                uint32_t u = adj[e];
+                sum += cur[u] / (double)(offs[u + 1] - offs[u]);
+            }
+            nxt[v] = (1.0 - d) / n + d * sum;
+            change += fabs(nxt[v] - cur[v]);
+        }
+        double* t = cur; cur = nxt; nxt = t;
+        ++it;
+        if (change < tol) break;
+    }
+    for (uint32_t v = 0; v < n; ++v) rank[v] = cur[v];
+    if (err) *err = change;
+    free(cur);
+    free(nxt);
+    return it;
 }
