@@ -34,6 +34,10 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   cc_min_label     pinned: networkx connected components (a library
                    routine), closed forms (disjoint cliques, paths,
                    isolated vertices), relabelling.
+  k4_count         pinned: brute force over all 4-sets, closed forms (K_n,
+                   complete 4-partite K_abcd, tripartite and wheel graphs).
+  c4_count         pinned: brute force over all 4-tuples, closed forms
+                   (K_ab, grids, K_n, cycles, K_4 minus an edge).
   pagerank         pinned: uniform ranks on regular graphs and the star's
                    fixed point (closed forms), networkx.pagerank on graphs
                    without isolated vertices (a library routine), sum of
@@ -104,6 +108,10 @@ def _bind(lib):
     lib.or_tc_forward.restype = ctypes.c_uint64
     lib.or_alg_bytes.argtypes = [ctypes.c_uint32, i64p, u32p]
     lib.or_alg_bytes.restype = ctypes.c_uint64
+    lib.or_k4_count.argtypes = [ctypes.c_uint32, i64p, u32p]
+    lib.or_k4_count.restype = ctypes.c_uint64
+    lib.or_c4_count.argtypes = [ctypes.c_uint32, i64p, u32p]
+    lib.or_c4_count.restype = ctypes.c_uint64
     lib.or_cc_min_label.argtypes = [ctypes.c_uint32, i64p, u32p, u32p]
     lib.or_cc_min_label.restype = ctypes.c_int64
     f64p = ctypes.POINTER(ctypes.c_double)
@@ -288,6 +296,19 @@ def tc_forward_mt(o: Oriented, per_vertex: bool = True, threads: int = 0, stride
         t_orig = np.zeros(n, dtype=np.uint64)
         t_orig[o.perm] = t[:n]
     return int(tot), t_orig
+
+
+def k4_count(g: Graph) -> int:
+    """Number of 4-cliques."""
+    return int(g.lib.or_k4_count(g.n, _p(g.offs, ctypes.c_int64), _p(g.adj, ctypes.c_uint32)))
+
+
+def c4_count(g: Graph) -> int:
+    """Number of 4-cycles (butterflies on a bipartite graph)."""
+    c = int(g.lib.or_c4_count(g.n, _p(g.offs, ctypes.c_int64), _p(g.adj, ctypes.c_uint32)))
+    if c == (1 << 64) - 1:
+        raise MemoryError("pair counters")
+    return c
 
 
 def cc_min_label(g: Graph):

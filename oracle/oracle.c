@@ -37,6 +37,12 @@
  *                         smallest vertex ID of its component.
  *   or_pagerank           Section 5.2.1: PageRank on the undirected graph,
  *                         damping d, L1 error tolerance, iteration limit.
+ *   or_k4_count           Section 3.2 multi-block pattern mode, k-clique
+ *                         finding with k = 4: sets of four mutually
+ *                         adjacent vertices.
+ *   or_c4_count           Section 3.2, butterfly counting: cycles of four
+ *                         distinct vertices (on a bipartite graph, the
+ *                         butterflies).
  *
  * The plain build (no -fopenmp) is single-threaded and is the reference;
  * the OpenMP build differs only in or_tc_forward_mt.
@@ -481,4 +487,73 @@ int or_pagerank(uint32_t n, const int64_t* offs, const uint32_t* adj, double d, 
     free(cur);
     free(nxt);
     return it;
+}
+
+/* ----------------------------------------------------------- 4-cliques */
+
+/*
+ * Number of 4-cliques {u < v < w < x} (original IDs, every pair adjacent):
+ * for each edge (u, v) with u < v, the common neighbours above v, and for
+ * each such w the common neighbours of u, v and w above w.  Membership by
+ * binary search in the sorted adjacency lists.
+ */
+uint64_t or_k4_count(uint32_t n, const int64_t* offs, const uint32_t* adj) {
+    uint64_t total = 0;
+    for (uint32_t u = 0; u < n; ++u) {
+        const uint32_t* nu = adj + offs[u];
+        int64_t du = offs[u + 1] - offs[u];
+        for (int64_t i = 0; i < du; ++i) {
+            uint32_t v = nu[i];
+            if (v <= u) continue;
+            const uint32_t* nv = adj + offs[v];
+            int64_t dv = offs[v + 1] - offs[v];
+            for (int64_t j = i + 1; j < du; ++j) {
+                uint32_t w = nu[j];              /* w > v, adjacent to u */
+                if (!contains(nv, dv, w)) continue;
+                const uint32_t* nw = adj + offs[w];
+                int64_t dw = offs[w + 1] - offs[w];
+                for (int64_t k = j + 1; k < du; ++k) {
+                    uint32_t x = nu[k];          /* x > w, adjacent to u */
+                    if (contains(nv, dv, x) && contains(nw, dw, x)) ++total;
+                }
+            }
+        }
+    }
+    return total;
+}
+
+/* ------------------------------------------------------------ 4-cycles */
+
+/*
+ * Number of cycles a - w - b - y - a on four distinct vertices (as
+ * subgraphs).  A 4-cycle has two pairs of opposite vertices, and the pair
+ * {a, b} with c common neighbours closes C(c, 2) cycles; so the count is
+ * half the sum over unordered pairs a < b of C(c_ab, 2).  For each a the
+ * common-neighbour counts of every b > a are gathered in a dense array
+ * through the paths a - w - b, then cleared.  Returns UINT64_MAX without
+ * memory.
+ */
+uint64_t or_c4_count(uint32_t n, const int64_t* offs, const uint32_t* adj) {
+    uint64_t* cnt = (uint64_t*)calloc((size_t)n + 1, sizeof(uint64_t));
+    if (!cnt) return UINT64_MAX;
+    uint64_t pairs = 0;
+    for (uint32_t a = 0; a < n; ++a) {
+        for (int64_t e = offs[a]; e < offs[a + 1]; ++e) {
+            uint32_t w = adj[e];
+            for (int64_t f = offs[w]; f < offs[w + 1]; ++f)
+                if (adj[f] > a) cnt[adj[f]]++;
+        }
+        for (int64_t e = offs[a]; e < offs[a + 1]; ++e) {
+            uint32_t w = adj[e];
+            for (int64_t f = offs[w]; f < offs[w + 1]; ++f) {
+                uint32_t b = adj[f];
+                if (b > a && cnt[b]) {
+                    pairs += cnt[b] * (cnt[b] - 1) / 2;
+                    cnt[b] = 0;
+                }
+            }
+        }
+    }
+    free(cnt);
+    return pairs / 2;
 }
