@@ -392,6 +392,38 @@ def h2d_gbs(torch, nbytes=1 << 30, reps=5):
     return nbytes * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
 
 
+def bsp_rows(P, torch, b, info, n, stream, reps=3):
+    """Single-block bulk-synchronous kernels on the same partition:
+    Shiloach-Vishkin components (hook rounds until none hooks) and PageRank
+    (the paper's damping 0.85, tolerance 1e-4, at most 20 iterations),
+    outputs in device tensors, wall time per call (each call synchronises)."""
+    m = info["m"]
+    lab = torch.zeros(n, dtype=torch.uint32, device="cuda")
+    ranks = torch.zeros(n, dtype=torch.float64, device="cuda")
+    cc, pr = [], []
+    for i in range(1 + reps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, it_cc, comps = P.pgb_cc_run(b, labels=lab, stream=stream)
+        t1 = time.perf_counter()
+        _, it_pr, err = P.pgb_pagerank_run(b, ranks=ranks, stream=stream)
+        t2 = time.perf_counter()
+        if i:
+            cc.append(t1 - t)
+            pr.append(t2 - t1)
+    cc_s, pr_s = statistics.median(cc), statistics.median(pr)
+    # PageRank bytes per iteration: offsets and both neighbour lists once,
+    # one 8-byte rank/degree read per neighbour entry, two 8-byte writes per
+    # vertex (the reads are random: a bound, not the traffic)
+    pr_bytes = 16 * (n + 1) + 8 * m + 16 * m + 16 * n
+    return {"cc": {"wall_ms": 1e3 * cc_s, "hook_rounds": it_cc, "components": comps,
+                   "edges_s_per_round": m * it_cc / cc_s},
+            "pagerank": {"wall_ms": 1e3 * pr_s, "iterations": it_pr, "last_l1_change": err,
+                         "ms_per_iteration": 1e3 * pr_s / max(it_pr, 1),
+                         "bytes_per_iteration": pr_bytes,
+                         "achieved_gbs": pr_bytes * it_pr / pr_s / 1e9}}
+
+
 def tiers_bench(args):
     """The runtime tiers on one partition each of R-MAT s24 and the grid
     (count phase only, the partition built once): launch per block triple
@@ -448,11 +480,12 @@ def tiers_bench(args):
                 rows[label].update({"host_ms": statistics.median(h["host_ms"] for h in hms),
                                     "host_parts": hms[-1]["host_parts"], "host_threads": hms[-1]["host_threads"],
                                     "host_in_edges": hms[-1]["host_in_edges"]})
+        bsp = bsp_rows(P, torch, b, info, n, stream)
         b.free()
         del tv
         torch.cuda.empty_cache()
         out[name] = {"workload": w["desc"], "unique_edges": info["m"], "triples": info["triples"],
-                     "triangles": T0, "tiers": rows}
+                     "triangles": T0, "tiers": rows, "bsp": bsp}
     return {"metric": "count-phase edges/s by runtime tier", "steps": args.tiers_steps,
             "note": "device_ms: CUDA events around the counting launches (a replayed graph: the whole graph)",
             "workloads": out}

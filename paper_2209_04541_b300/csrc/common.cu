@@ -140,10 +140,10 @@ uint64_t pgb_kernel_launches(void) { return pgb::g_launches.load(); }
 
 int pgb_set_allocator(pgb_alloc_fn alloc, pgb_free_fn free_fn, void* ctx) {
     return pgb::guard([&] {
-        std::lock_guard<std::mutex> lk(pgb::g_alloc_mu);
-        if (pgb::g_live.load() != 0) pgb::fail(PGB_E_STATE, "allocator changed while handles are alive");
         if ((alloc == nullptr) != (free_fn == nullptr))
             pgb::fail(PGB_E_INVAL, "alloc and free must both be set or both be NULL");
+        std::lock_guard<std::mutex> lk(pgb::g_alloc_mu);
+        if (pgb::g_live.load() != 0) pgb::fail(PGB_E_STATE, "allocator changed while handles are alive");
         pgb::g_alloc = alloc;
         pgb::g_free = free_fn;
         pgb::g_ctx = ctx;

@@ -15,8 +15,9 @@
 // after v that also lie in v's row close a triangle u < v < w.  Both lists
 // are sorted ranks; the shorter is walked and each entry found in the
 // longer one, by a merge when the lengths are close and by a galloping
-// search when one list is much longer.  Per-vertex counts go to t[u], t[v]
-// (once per in-edge) and t[w] (once per match) with relaxed atomic adds.
+// search when one list is much longer.  Per-vertex counts are emitted as
+// (vertex, count) pairs, u and v once per in-edge with triangles and w once
+// per match, per thread; the caller adds them into the device counters.
 //
 // It reads a host mirror of the oriented graph (row offsets, columns, row
 // of each edge, in-edge offsets and ranges), copied from the device once per
@@ -90,10 +91,6 @@ inline uint64_t intersect(const uint32_t* col, uint32_t xb, uint32_t xe, uint32_
     return c;
 }
 
-inline void add_relaxed(unsigned long long* t, uint64_t v) {
-    __atomic_fetch_add(t, (unsigned long long)v, __ATOMIC_RELAXED);
-}
-
 const HostMirror& mirror_of(const pgb_blocks* b, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(b->plan_mu);
     if (!b->host_mirror) {
@@ -150,7 +147,8 @@ std::vector<uint8_t> host_parts_by_cutoff(const pgb_blocks* b, uint32_t share_pp
 }
 
 HostCountResult host_count_parts(const pgb_blocks* b, const std::vector<uint8_t>& host, uint32_t threads,
-                                 unsigned long long* t, const pgb_cancel* cancel, cudaStream_t s) {
+                                 bool per_vertex, std::vector<std::pair<uint32_t, uint32_t>>& adds,
+                                 const pgb_cancel* cancel, cudaStream_t s) {
     HostCountResult R;
     const auto t0 = std::chrono::steady_clock::now();
     // head runs of the host parts, lightest part first
@@ -177,8 +175,10 @@ HostCountResult host_count_parts(const pgb_blocks* b, const std::vector<uint8_t>
     std::atomic<uint64_t> total{0};
     std::atomic<bool> stopped{false};
     const uint32_t* col = H.col.data();
-    auto worker = [&] {
+    std::vector<std::vector<std::pair<uint32_t, uint32_t>>> local(threads);
+    auto worker = [&](uint32_t id) {
         uint64_t mine = 0;
+        std::vector<std::pair<uint32_t, uint32_t>>& out = local[id];
         for (;;) {
             if (cancel && __atomic_load_n(const_cast<const uint32_t*>(cancel->host), __ATOMIC_RELAXED)) {
                 stopped = true;
@@ -194,21 +194,27 @@ HostCountResult host_count_parts(const pgb_blocks* b, const std::vector<uint8_t>
                     const unsigned long long r = H.xr[q];
                     const uint32_t xb = (uint32_t)r, xe = (uint32_t)(r >> 32);
                     uint64_t c;
-                    if (t) c = intersect(col, xb, xe, vb, ve, [&](uint32_t w) { add_relaxed(t + w, 1); });
+                    if (per_vertex) c = intersect(col, xb, xe, vb, ve, [&](uint32_t w) { out.emplace_back(w, 1u); });
                     else c = intersect(col, xb, xe, vb, ve, [](uint32_t) {});
-                    if (c && t) add_relaxed(t + H.rowidx[xb - 1], c);
+                    if (c && per_vertex) out.emplace_back(H.rowidx[xb - 1], (uint32_t)c);
                     cv += c;
                 }
-                if (cv && t) add_relaxed(t + v, cv);
+                // (a head's total may pass 2^32: emitted in pieces of 2^31)
+                for (uint64_t left = per_vertex ? cv : 0; left;) {
+                    const uint32_t piece = (uint32_t)std::min<uint64_t>(left, 1ull << 31);
+                    out.emplace_back(v, piece);
+                    left -= piece;
+                }
                 mine += cv;
             }
         }
         total += mine;
     };
     std::vector<std::thread> pool;
-    for (uint32_t k = 1; k < threads; ++k) pool.emplace_back(worker);
-    worker();
+    for (uint32_t k = 1; k < threads; ++k) pool.emplace_back(worker, k);
+    worker(0);
     for (auto& th : pool) th.join();
+    for (auto& l : local) adds.insert(adds.end(), l.begin(), l.end());
     R.total = total.load();
     R.cancelled = stopped.load();
     R.threads = threads;

@@ -19,10 +19,13 @@ struct HostCountResult {
     bool cancelled = false; // the cancel token was seen; counts are incomplete
 };
 
-// Count the host parts on `threads` host threads (0: all hardware threads),
-// adding per-vertex counts (rank space) into t when t is not null.  Copies
-// the oriented graph to a host mirror on first use (synchronising s).
+// Count the host parts on `threads` host threads (0: all hardware threads).
+// With per_vertex, the per-vertex counts (rank space) are appended to `adds`
+// as (vertex, count) pairs (a vertex may appear more than once): the host
+// parts are the light ones, so their contributions are sparse.  Copies the
+// oriented graph to a host mirror on first use (synchronising s).
 HostCountResult host_count_parts(const pgb_blocks* b, const std::vector<uint8_t>& host, uint32_t threads,
-                                 unsigned long long* t, const pgb_cancel* cancel, cudaStream_t s);
+                                 bool per_vertex, std::vector<std::pair<uint32_t, uint32_t>>& adds,
+                                 const pgb_cancel* cancel, cudaStream_t s);
 
 }  // namespace pgb

@@ -341,10 +341,12 @@ __global__ void k_reduce_segments(const unsigned long long* __restrict__ partial
     }
 }
 
-// t[i] += a[i] for i < n (the host kernel's per-vertex counts).
-__global__ void k_add_u64(unsigned long long* __restrict__ t, const unsigned long long* __restrict__ a, uint32_t n) {
-    uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) t[i] += a[i];
+// t[pairs[2i]] += pairs[2i + 1] for i < k (the host kernel's per-vertex
+// counts, a vertex possibly in several pairs).
+__global__ void k_add_pairs(unsigned long long* __restrict__ t, const uint32_t* __restrict__ pairs, uint64_t k) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride)
+        atomicAdd(t + pairs[2 * i], (unsigned long long)pairs[2 * i + 1]);
 }
 
 // Rank-space per-vertex counts to original IDs.
@@ -486,6 +488,7 @@ struct RunPlan {
     std::vector<Tuple> tuples;
     std::vector<int> grids;
     std::vector<uint64_t> seg;
+    std::vector<uint32_t> launch_order;  // queue entries in launch order
     DevBuf<uint64_t> dseg;
     // PERSISTENT binary search: tuples drained from a device counter
     DevBuf<Tuple> dt;
@@ -572,6 +575,21 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
         }
         P->npartials = P->seg[T];
         P->partials.alloc(std::max<uint64_t>(P->npartials, 1), s);
+        // launch order: the queue's, or along the Hilbert curve of the
+        // blocks (i, j), then k; partials stay indexed by queue entry
+        P->launch_order.resize(T);
+        for (uint64_t t = 0; t < T; ++t) P->launch_order[t] = (uint32_t)t;
+        if (o.order == PGB_ORDER_HILBERT && T > 1) {
+            const std::vector<uint32_t> hb = hilbert_block_order(b->p);
+            std::vector<uint32_t> pos((size_t)b->p * b->p, 0);
+            for (size_t r = 0; r < hb.size(); ++r) pos[hb[r]] = (uint32_t)r;
+            std::stable_sort(P->launch_order.begin(), P->launch_order.end(), [&](uint32_t x, uint32_t y) {
+                const pgb_triple &a = b->triples[x], &c = b->triples[y];
+                const uint32_t pa = pos[(size_t)a.i * b->p + a.j], pc = pos[(size_t)c.i * b->p + c.j];
+                if (pa != pc) return pa < pc;
+                return a.k < c.k;
+            });
+        }
         if (P->per_triple && T > 0) {
             P->dseg.alloc(T + 1, s);
             PGB_CUDA(cudaMemcpyAsync(P->dseg.ptr, P->seg.data(), (T + 1) * 8, cudaMemcpyHostToDevice, s));
@@ -680,7 +698,8 @@ static void enqueue_count(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cud
     if (ev0) PGB_CUDA(cudaEventRecord(ev0, s));
     if (P.mode == PGB_MODE_PLAIN) {
         const uint64_t T = P.tuples.size();
-        for (uint64_t t = 0; t < T; ++t) {
+        for (uint64_t r = 0; r < T; ++r) {
+            const uint32_t t = P.launch_order[r];
             if (P.per_vertex)
                 k_tc_tuple<true><<<P.grids[t], kThreads, 0, s>>>(P.G, P.tuples[t], P.partials.ptr + P.seg[t], ctl);
             else
@@ -813,9 +832,8 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
         enqueue_count(*P, s, r->ev0, r->ev1, r->ctl.ptr);
         std::vector<uint8_t> host_mask(b->p);
         for (uint32_t j = 0; j < b->p; ++j) host_mask[j] = part_kind[j] == kPartHost ? 1 : 0;
-        std::vector<unsigned long long> ht(r->per_vertex ? n : 0, 0);
-        const HostCountResult hr =
-            host_count_parts(b, host_mask, o.host_threads, r->per_vertex && n ? ht.data() : nullptr, o.cancel, s);
+        std::vector<std::pair<uint32_t, uint32_t>> adds;
+        const HostCountResult hr = host_count_parts(b, host_mask, o.host_threads, r->per_vertex, adds, o.cancel, s);
         r->host_ms = hr.ms;
         r->host_in_edges = hr.in_edges;
         r->host_parts = hr.parts;
@@ -825,12 +843,15 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
             const unsigned long long h_total = hr.total;
             PGB_CUDA(cudaMemcpyAsync(P->partials.ptr + P->npartials - 1, &h_total, 8, cudaMemcpyHostToDevice, s));
         }
-        DevBuf<unsigned long long> dht;
-        if (r->per_vertex && n && hr.parts) {
-            dht.alloc(n, s);
-            PGB_CUDA(cudaMemcpyAsync(dht.ptr, ht.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
-            k_add_u64<<<std::min<uint32_t>((n + 255) / 256, 148 * 32), 256, 0, s>>>(P->tv.ptr, dht.ptr, n);
-            PGB_CHECK_LAUNCH("k_add_u64");
+        DevBuf<uint32_t> dadds;
+        if (r->per_vertex && !adds.empty()) {
+            // (vertex, count) pairs, staged from pageable memory
+            dadds.alloc(2 * adds.size(), s);
+            PGB_CUDA(cudaMemcpyAsync(dadds.ptr, adds.data(), adds.size() * 8, cudaMemcpyHostToDevice, s));
+            const uint64_t k = adds.size();
+            k_add_pairs<<<(unsigned)std::min<uint64_t>((k + 255) / 256, 148ull * 32), 256, 0, s>>>(P->tv.ptr,
+                                                                                                  dadds.ptr, k);
+            PGB_CHECK_LAUNCH("k_add_pairs");
         }
         enqueue_reduce(*P, s);
         // the host buffer is pageable: the copies above were staged before
@@ -916,7 +937,8 @@ int pgb_tc_run(const pgb_blocks* b, const pgb_tc_opts* opts, void* stream, pgb_t
         if (o.variant < PGB_VAR_AUTO || o.variant > PGB_VAR_HASH) fail(PGB_E_INVAL, "bad variant");
         if (o.mode == PGB_MODE_PLAIN && o.variant == PGB_VAR_HASH)
             fail(PGB_E_INVAL, "PLAIN mode runs the edge-wise variants (binary search, merge) only");
-        if (o.order != PGB_ORDER_WEIGHT && o.order != PGB_ORDER_LOCALITY) fail(PGB_E_INVAL, "bad order");
+        if (o.order != PGB_ORDER_WEIGHT && o.order != PGB_ORDER_LOCALITY && o.order != PGB_ORDER_HILBERT)
+            fail(PGB_E_INVAL, "bad order");
         if (o.hash_threads != 0 && o.hash_threads != 128 && o.hash_threads != 256 && o.hash_threads != 512)
             fail(PGB_E_INVAL, "hash_threads must be 0, 128, 256 or 512");
         if (b->offloaded && (o.mode != PGB_MODE_PERSISTENT || o.variant == PGB_VAR_BSEARCH ||
