@@ -130,6 +130,10 @@ extern "C" {
 /* Queue order of block tuples (Section 4.4 sorts by decreasing weight). */
 #define PGB_ORDER_WEIGHT   0  /* decreasing weight (Section 4.4) */
 #define PGB_ORDER_LOCALITY 1  /* by column block j, then decreasing weight */
+#define PGB_ORDER_HILBERT  2  /* PLAIN launches: by the Hilbert-curve index of
+                                 block (i, j) (Section 4.3.1 allows any
+                                 space-filling curve for the block IDs), then
+                                 k; PERSISTENT runs treat it as WEIGHT */
 
 typedef struct pgb_graph pgb_graph;
 typedef struct pgb_blocks pgb_blocks;
@@ -481,6 +485,104 @@ int pgb_server_stats(pgb_server* s, pgb_server_info* out);
 /* Stop: queued jobs are cancelled, batches on the device are stopped through
  * their cancel tokens, threads and streams are released. */
 void pgb_server_destroy(pgb_server* s);
+
+/* ------------------------------------------ block layout and storage */
+/* Section 4.3.1: blocks get integer IDs, row-major by default, or along a
+ * space-filling curve.  pgb_block_order writes the upper blocks (i <= j) of
+ * a p x p partition, p(p+1)/2 pairs (i, j) into ij, in row-major or
+ * Hilbert-curve order (cell (x = j, y = i) of the 2^k x 2^k grid with
+ * 2^k >= p).  pgb_hilbert_index is the curve itself: the position of cell
+ * (x, y) in a side x side grid (side a power of two).  Host-only; no GPU
+ * needed.  Errors: PGB_E_INVAL. */
+#define PGB_LAYOUT_ROWMAJOR 0
+#define PGB_LAYOUT_HILBERT  1
+int pgb_block_order(uint32_t p, int layout, uint32_t* ij);
+int pgb_hilbert_index(uint32_t side, uint32_t x, uint32_t y, uint64_t* d);
+
+/* Section 4.3.2: a block is a subgraph with block-local vertex IDs (rows
+ * u - c_i, columns v - c_j), stored as CSR, COO or CCOO.  Inside the library
+ * the kernels read blocks as slices of the oriented CSR; these calls
+ * materialise one block A_ij for a caller:
+ *   PGB_FMT_CSR:  a = offsets uint32[rows + 1], c = columns uint32[nnz]
+ *   PGB_FMT_COO:  a = rows uint32[nnz],         c = columns uint32[nnz]
+ *   PGB_FMT_CCOO: a = the non-empty rows uint32[nz], d = their offsets
+ *                 uint32[nz + 1], c = columns uint32[nnz]
+ * (d unused unless CCOO; rows of a row ascending, columns ascending in a
+ * row).  pgb_blocks_block_info gives the block's shape, the bytes of each
+ * format and `format`: the autotuned choice, the format with the fewest
+ * bytes for this block (CCOO when most rows are empty, COO near one edge
+ * per non-empty row, CSR otherwise; ties to CSR, then COO).  Both synchronise
+ * (block_info on the blocks' own stream).  Errors: PGB_E_INVAL (NULL, i or j
+ * >= p, bad format, NULL output for a non-empty block), PGB_E_STATE (columns
+ * offloaded), PGB_E_NOMEM, PGB_E_CUDA. */
+#define PGB_FMT_CSR  0
+#define PGB_FMT_COO  1
+#define PGB_FMT_CCOO 2
+typedef struct {
+    uint32_t rows, cols;      /* |V_i|, |V_j| */
+    uint64_t nnz;             /* |A_ij| */
+    uint32_t nonempty_rows;
+    int32_t format;           /* the autotuned storage format */
+    uint64_t bytes_csr, bytes_coo, bytes_ccoo;
+} pgb_block_info;
+int pgb_blocks_block_info(const pgb_blocks* b, uint32_t i, uint32_t j, pgb_block_info* out);
+int pgb_blocks_export_block(const pgb_blocks* b, uint32_t i, uint32_t j, int format, uint32_t* a, uint32_t* c,
+                            uint32_t* d, int mem, void* stream);
+
+/* ----------------------------------------- other multi-block patterns */
+/* Section 3.2 names k-clique finding and butterfly counting as the other
+ * multi-block pattern computations.  Both count on the degree-ordered
+ * oriented graph of `b` (resident blocks; PGB_E_STATE after
+ * pgb_blocks_offload), synchronise `stream` and write *total (exact).
+ *
+ * pgb_k4_count: 4-cliques (four mutually adjacent vertices), each found
+ *   once from its lowest edge (u, v): common out-neighbours w of u and v,
+ *   then common out-neighbours of u, v and w above w.
+ * pgb_c4_count: 4-cycles (four distinct vertices a - w - b - y - a, as
+ *   subgraphs), each counted once at its highest-ranked vertex; on a
+ *   bipartite graph these are its butterflies.  Holds up to 8 GiB of
+ *   per-CTA counter arrays (n words each) while it runs.
+ * Errors: PGB_E_INVAL (NULL), PGB_E_STATE, PGB_E_NOMEM, PGB_E_CUDA. */
+int pgb_k4_count(const pgb_blocks* b, void* stream, uint64_t* total);
+int pgb_c4_count(const pgb_blocks* b, void* stream, uint64_t* total);
+
+/* ------------------------------------ single-block bulk-synchronous runs */
+/* Section 3.2's single-block bulk-synchronous execution mode on the same
+ * block store: each block-list holds one block and every iteration visits
+ * every edge.  Both calls need resident blocks (PGB_E_STATE after
+ * pgb_blocks_offload), synchronise `stream`, and allocate their working
+ * arrays from the library allocator.
+ *
+ * pgb_cc_run: connected components by Shiloach-Vishkin (Section 3.4):
+ *   hook launches over the oriented edges (a root is hooked below the root
+ *   of smaller original ID, by compare-and-swap) alternate with link
+ *   launches (pointer jumping) until a hook launch hooks nothing.  labels
+ *   (n entries, host or device per `mem`) gets, for each ORIGINAL vertex ID,
+ *   the smallest original ID in its component; iterations and components
+ *   (both may be NULL) get the hook rounds and the number of components. */
+int pgb_cc_run(const pgb_blocks* b, void* stream, uint32_t* labels, int mem, uint32_t* iterations,
+               uint64_t* components);
+
+/* pgb_pagerank_run: PageRank (Section 5.2.1) of the undirected graph in
+ * double precision: r_0 = 1/n, r_t+1(v) = (1 - d)/n + d * sum over
+ * neighbours u of r_t(u) / deg(u) (degree-0 vertices pass nothing on);
+ * stops after the first iteration whose L1 change is below tol, or after
+ * max_iter iterations.  Each vertex pulls over its row and its in-edges (no
+ * atomics).  ranks (n entries, host or device) gets r by ORIGINAL vertex ID;
+ * iterations and last_change may be NULL.  Defaults (the paper's): damping
+ * 0.85, tol 1e-4, max_iter 20.  Errors: PGB_E_INVAL (NULL b or ranks,
+ * damping outside [0, 1], negative tol), PGB_E_STATE, PGB_E_NOMEM,
+ * PGB_E_CUDA. */
+typedef struct {
+    double damping;
+    double tol;
+    uint32_t max_iter;
+    uint32_t reserved[3];
+} pgb_pagerank_opts;
+
+void pgb_pagerank_opts_default(pgb_pagerank_opts* o);
+int pgb_pagerank_run(const pgb_blocks* b, const pgb_pagerank_opts* opts, void* stream, double* ranks, int mem,
+                     uint32_t* iterations, double* last_change);
 
 /* ------------------------------------------------- no-allocation count */
 /* The paper has no counterpart to this call.  It is for callers that must

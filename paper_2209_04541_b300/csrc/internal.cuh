@@ -242,6 +242,8 @@ void ingest_keys(pgb_graph* g, const uint32_t* src, const uint32_t* dst, uint64_
 void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, pgb_blocks* b);
 void ensure_block_edge_index(const pgb_blocks* b, cudaStream_t s);
 void copy_out(void* dst, const void* src_dev, size_t bytes, int mem, cudaStream_t s);
+// Upper block IDs (i * p + j, i <= j) along the Hilbert curve (blocks.cu).
+std::vector<uint32_t> hilbert_block_order(uint32_t p);
 // Pinned host copy of the columns after pgb_blocks_offload_columns, else null.
 const uint32_t* offloaded_columns(const pgb_blocks* b);
 

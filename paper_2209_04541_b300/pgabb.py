@@ -51,6 +51,7 @@ PGB_VAR_HOST = 5
 
 PGB_ORDER_WEIGHT = 0
 PGB_ORDER_LOCALITY = 1
+PGB_ORDER_HILBERT = 2
 
 PGB_EXPORT_PERM = 0
 PGB_EXPORT_ROWPTR = 1
@@ -60,6 +61,11 @@ PGB_EXPORT_BLOCK_EDGES = 4
 PGB_EXPORT_TRIPLES = 5
 PGB_EXPORT_WEIGHTS = 6
 PGB_EXPORT_PART_PROBES = 7
+PGB_LAYOUT_ROWMAJOR = 0
+PGB_LAYOUT_HILBERT = 1
+PGB_FMT_CSR = 0
+PGB_FMT_COO = 1
+PGB_FMT_CCOO = 2
 
 HEADER = os.path.join(_build.INCLUDE, "pgabb.h")
 
@@ -141,6 +147,19 @@ _SIGS = {
     "pgb_server_cancel": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "pgb_server_stats": (ctypes.c_int, [_VP, _VP]),
     "pgb_server_destroy": (None, [_VP]),
+    "pgb_block_order": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int, _VP]),
+    "pgb_hilbert_index": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+    "pgb_blocks_block_info": (ctypes.c_int, [_VP, ctypes.c_uint32, ctypes.c_uint32, _VP]),
+    "pgb_blocks_export_block": (ctypes.c_int, [_VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, _VP, _VP, _VP,
+                                               ctypes.c_int, _VP]),
+    "pgb_k4_count": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_uint64)]),
+    "pgb_c4_count": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_uint64)]),
+    "pgb_cc_run": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32),
+                                  ctypes.POINTER(ctypes.c_uint64)]),
+    "pgb_pagerank_opts_default": (None, [_VP]),
+    "pgb_pagerank_run": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32),
+                                        ctypes.POINTER(ctypes.c_double)]),
     "pgb_cancel_create": (ctypes.c_int, [ctypes.POINTER(_VP)]),
     "pgb_cancel_set": (ctypes.c_int, [_VP]),
     "pgb_cancel_reset": (ctypes.c_int, [_VP]),
@@ -409,6 +428,112 @@ def pgb_tc_opts_default(**kw) -> TcOpts:
             v = v.ptr
         setattr(o, k, v)
     return o
+
+
+class BlockInfo(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_uint32), ("cols", ctypes.c_uint32), ("nnz", ctypes.c_uint64),
+                ("nonempty_rows", ctypes.c_uint32), ("format", ctypes.c_int32), ("bytes_csr", ctypes.c_uint64),
+                ("bytes_coo", ctypes.c_uint64), ("bytes_ccoo", ctypes.c_uint64)]
+
+
+def pgb_block_order(p: int, layout: int = PGB_LAYOUT_ROWMAJOR) -> np.ndarray:
+    """The upper blocks (i <= j) as an array of (i, j) rows, in row-major or
+    Hilbert-curve order."""
+    out = np.zeros(p * (p + 1), dtype=np.uint32)
+    _check(load().pgb_block_order(p, layout, out.ctypes.data), "pgb_block_order")
+    return out.reshape(-1, 2)
+
+
+def pgb_hilbert_index(side: int, x: int, y: int) -> int:
+    d = ctypes.c_uint64()
+    _check(load().pgb_hilbert_index(side, x, y, ctypes.byref(d)), "pgb_hilbert_index")
+    return int(d.value)
+
+
+def pgb_blocks_block_info(b: Blocks, i: int, j: int) -> dict:
+    inf = BlockInfo()
+    _check(load().pgb_blocks_block_info(b, i, j, ctypes.byref(inf)), "pgb_blocks_block_info")
+    return {k: int(getattr(inf, k)) for k, _ in BlockInfo._fields_}
+
+
+def pgb_blocks_export_block(b: Blocks, i: int, j: int, fmt: int):
+    """Block A_ij with block-local IDs: CSR (offsets, columns), COO (rows,
+    columns) or CCOO (non-empty rows, their offsets, columns), host arrays."""
+    inf = pgb_blocks_block_info(b, i, j)
+    nnz, rows, nz = inf["nnz"], inf["rows"], inf["nonempty_rows"]
+    na = rows + 1 if fmt == PGB_FMT_CSR else (nnz if fmt == PGB_FMT_COO else nz)
+    a = np.zeros(max(na, 1), dtype=np.uint32)
+    c = np.zeros(max(nnz, 1), dtype=np.uint32)
+    d = np.zeros(nz + 1, dtype=np.uint32)
+    _check(load().pgb_blocks_export_block(b, i, j, fmt, a.ctypes.data, c.ctypes.data, d.ctypes.data, PGB_MEM_HOST,
+                                          b.stream), "pgb_blocks_export_block")
+    if fmt == PGB_FMT_CCOO:
+        return a[:nz], d, c[:nnz]
+    return a[:na], c[:nnz]
+
+
+def pgb_k4_count(b: Blocks, stream=None) -> int:
+    """Number of 4-cliques."""
+    v = ctypes.c_uint64()
+    _check(load().pgb_k4_count(b, _stream(stream) if stream is not None else b.stream, ctypes.byref(v)),
+           "pgb_k4_count")
+    return int(v.value)
+
+
+def pgb_c4_count(b: Blocks, stream=None) -> int:
+    """Number of 4-cycles (the butterflies of a bipartite graph)."""
+    v = ctypes.c_uint64()
+    _check(load().pgb_c4_count(b, _stream(stream) if stream is not None else b.stream, ctypes.byref(v)),
+           "pgb_c4_count")
+    return int(v.value)
+
+
+class PageRankOpts(ctypes.Structure):
+    _fields_ = [("damping", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 3)]
+
+
+def pgb_cc_run(b: Blocks, labels=None, stream=None):
+    """Connected components: (labels by original ID, iterations, components).
+    ``labels`` may be a uint32 device tensor of n entries to fill; else a
+    host numpy array is returned."""
+    n = pgb_blocks_info(b)["n"]
+    out = labels if labels is not None else np.zeros(n, dtype=np.uint32)
+    ptr, mem, keep = _arr(out, np.uint32)
+    it, comps = ctypes.c_uint32(), ctypes.c_uint64()
+    st = _stream(stream) if stream is not None else b.stream
+    _check(load().pgb_cc_run(b, st, ptr, mem, ctypes.byref(it), ctypes.byref(comps)), "pgb_cc_run")
+    return (keep if labels is None else labels), int(it.value), int(comps.value)
+
+
+def pgb_pagerank_opts_default(**kw) -> PageRankOpts:
+    o = PageRankOpts()
+    load().pgb_pagerank_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def pgb_pagerank_run(b: Blocks, opts: PageRankOpts | None = None, ranks=None, stream=None):
+    """PageRank: (ranks float64 by original ID, iterations, last L1 change)."""
+    n = pgb_blocks_info(b)["n"]
+    out = ranks if ranks is not None else np.zeros(n, dtype=np.float64)
+    if isinstance(out, np.ndarray):
+        if out.dtype != np.float64 or out.size < n:
+            raise ValueError("ranks must be float64 with n entries")
+        ptr, mem = out.ctypes.data, PGB_MEM_HOST
+    else:
+        import torch
+        if out.dtype != torch.float64 or out.numel() < n or not out.is_contiguous():
+            raise ValueError("ranks must be a contiguous float64 tensor with n entries")
+        ptr, mem = out.data_ptr(), (PGB_MEM_DEVICE if out.is_cuda else PGB_MEM_HOST)
+    it, err = ctypes.c_uint32(), ctypes.c_double()
+    st = _stream(stream) if stream is not None else b.stream
+    _check(load().pgb_pagerank_run(b, ctypes.byref(opts) if opts is not None else None, st, ptr, mem,
+                                   ctypes.byref(it), ctypes.byref(err)), "pgb_pagerank_run")
+    return out, int(it.value), float(err.value)
 
 
 def pgb_cancel_create() -> Cancel:

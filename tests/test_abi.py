@@ -112,3 +112,32 @@ def test_noalloc_binding_rejects_short_arrays_without_calling_the_library(short,
     with pytest.raises(ValueError, match=short):
         pgabb.pgb_tc_count_oriented_noalloc(n, m, arrs["rowptr"], arrs["col"], arrs["perm"], arrs["total"],
                                             arrs["per_vertex"])
+
+
+def test_hilbert_curve_and_block_order():
+    """Host-only layout helpers: the Hilbert curve is a bijection of the
+    grid onto [0, side^2) whose consecutive cells are neighbours, with the
+    2 x 2 curve (0,0), (0,1), (1,1), (1,0); block orders list each upper
+    block once."""
+    import numpy as np
+
+    assert [pgabb.pgb_hilbert_index(2, x, y) for x, y in ((0, 0), (0, 1), (1, 1), (1, 0))] == [0, 1, 2, 3]
+    for side in (4, 8, 64):
+        cells = {}
+        for x in range(side):
+            for y in range(side):
+                cells[pgabb.pgb_hilbert_index(side, x, y)] = (x, y)
+        assert sorted(cells) == list(range(side * side))
+        for d in range(side * side - 1):
+            (x0, y0), (x1, y1) = cells[d], cells[d + 1]
+            assert abs(x0 - x1) + abs(y0 - y1) == 1
+    for p in (1, 5, 16, 33):
+        rm = pgabb.pgb_block_order(p, pgabb.PGB_LAYOUT_ROWMAJOR)
+        hb = pgabb.pgb_block_order(p, pgabb.PGB_LAYOUT_HILBERT)
+        want = [(i, j) for i in range(p) for j in range(i, p)]
+        assert [tuple(x) for x in rm.tolist()] == want
+        assert sorted(tuple(x) for x in hb.tolist()) == want
+        keys = [pgabb.pgb_hilbert_index(1 << max(p - 1, 1).bit_length(), j, i) for i, j in hb.tolist()]
+        assert keys == sorted(keys)
+    with pytest.raises(pgabb.PgbError):
+        pgabb.pgb_hilbert_index(6, 0, 0)
