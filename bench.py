@@ -288,29 +288,28 @@ def run_reference(args, rank, world):
     return 0
 
 
+def serve_job(i: int, max_scale: int):
+    """Job i of the serving workload: the families in equal thirds, R-MAT
+    (scale uniform in [10, max_scale], edge factor uniform in [8, 32]),
+    Erdos-Renyi (n log-uniform in [2^10, 2^max_scale], average degree
+    log-uniform in [4, 64]) and random geometric graphs (n log-uniform,
+    average degree 6); seed = job index."""
+    rng = np.random.default_rng(i)
+    fam = i % 3
+    if fam == 0:
+        s = int(rng.integers(10, max_scale + 1))
+        ef = int(rng.integers(8, 33))
+        return graphgen.rmat(s, ef, i)
+    n = int(round(2.0 ** rng.uniform(10, max_scale)))
+    if fam == 1:
+        deg = 2.0 ** rng.uniform(2, 6)
+        return graphgen.er_pairs(n, max(1, int(n * deg / 2)), i)
+    return graphgen.rgg(n, None, i)
+
+
 def serve_jobs(count: int, max_scale: int):
-    """The serving workload: jobs in equal thirds of R-MAT (scale uniform in
-    [10, max_scale], edge factor uniform in [8, 32]), Erdos-Renyi (n
-    log-uniform in [2^10, 2^max_scale], average degree log-uniform in
-    [4, 64]) and random geometric graphs (n log-uniform, average degree 6);
-    seed = job index."""
-    jobs = []
-    for i in range(count):
-        rng = np.random.default_rng(i)
-        fam = i % 3
-        if fam == 0:
-            s = int(rng.integers(10, max_scale + 1))
-            ef = int(rng.integers(8, 33))
-            src, dst, n = graphgen.rmat(s, ef, i)
-        else:
-            n = int(round(2.0 ** rng.uniform(10, max_scale)))
-            if fam == 1:
-                deg = 2.0 ** rng.uniform(2, 6)
-                src, dst, n = graphgen.er_pairs(n, max(1, int(n * deg / 2)), i)
-            else:
-                src, dst, n = graphgen.rgg(n, None, i)
-        jobs.append((src, dst, n))
-    return jobs
+    """The first `count` jobs of the serving workload."""
+    return [serve_job(i, max_scale) for i in range(count)]
 
 
 def run_serve(jobs, mode, arrivals=None, **kw):
@@ -646,11 +645,14 @@ def main(argv=None):
     ap.add_argument("--hash-threads", type=int, default=0, choices=[0, 128, 256, 512],
                     help="CTA shape of the hash kernel (0 = autotuned)")
     ap.add_argument("--p", type=int, default=0, help="override the workload's p")
+    ap.add_argument("--hash-min-lookups", type=int, default=0,
+                    help="per-part autotuner threshold, lookups per edge (0 = the library's 32)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-jobs", type=int, default=1000)
-    ap.add_argument("--serve-max-scale", type=int, default=18)
+    ap.add_argument("--serve-jobs", type=int, default=10000)
+    ap.add_argument("--serve-max-scale", type=int, default=16,
+                    help="largest R-MAT scale and log2 n of the mix (the survey's 22 needs ~66 G raw edges)")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-tiers", action="store_true")
     ap.add_argument("--tiers-workloads", default="rmat24,grid4096")
@@ -701,7 +703,7 @@ def main(argv=None):
     variant = {"auto": P.PGB_VAR_AUTO, "bsearch": P.PGB_VAR_BSEARCH, "merge": P.PGB_VAR_MERGE,
                "hash": P.PGB_VAR_HASH}[args.variant]
     opts = P.pgb_tc_opts_default(mode=mode, per_vertex=args.per_vertex, chunk_edges=args.chunk, variant=variant,
-                                 hash_threads=args.hash_threads,
+                                 hash_threads=args.hash_threads, hash_min_lookups=args.hash_min_lookups,
                                  order=P.PGB_ORDER_WEIGHT if args.order == "weight" else P.PGB_ORDER_LOCALITY)
     info = {}
 

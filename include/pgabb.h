@@ -110,6 +110,7 @@ extern "C" {
  * (A_ij, A_ik, A_jk) of one j count exactly the triangles whose middle
  * vertex lies in V_j, so each part can take its own kernel.  A part runs
  * PGB_VAR_HASH when its oriented edges average at least 32 lookups
+ * (pgb_tc_opts.hash_min_lookups)
  * (PGB_EXPORT_PART_PROBES[j] >= 32 * sum_i |A_ij|: long lists, skewed
  * degrees) and PGB_VAR_BSEARCH otherwise (short lists); when the parts
  * differ, one hash launch over the hash parts' work items and one edge-wise
@@ -338,7 +339,9 @@ typedef struct {
     uint32_t host_share_ppm;/* HYBRID: cut-off, the host's share of the estimated
                               work in parts per million (0 = 1000, i.e. 0.1%;
                               at most 10^6: everything on the host) */
-    uint32_t reserved[2];
+    uint32_t hash_min_lookups; /* AUTO: a head part takes the hash kernel at
+                              this many lookups per edge or more (0 = 32) */
+    uint32_t reserved[1];
 } pgb_tc_opts;
 
 void pgb_tc_opts_default(pgb_tc_opts* o);

@@ -461,7 +461,8 @@ static int choose_variant(const pgb_blocks* b, const pgb_tc_opts& o, std::vector
             uint64_t edges = 0;
             for (uint32_t i = 0; i <= j; ++i) edges += b->block_edges[(size_t)i * p + j];
             const uint64_t probes = j < b->part_probes.size() ? b->part_probes[j] : 0;
-            kind[j] = (edges == 0 || probes >= kHashMinLookupsPerEdge * edges) ? kPartHash : kPartEdge;
+            const uint64_t thr = o.hash_min_lookups ? o.hash_min_lookups : kHashMinLookupsPerEdge;
+            kind[j] = (edges == 0 || probes >= thr * edges) ? kPartHash : kPartEdge;
         }
         const bool work = part_in_edges(b, j) > 0;
         hash_work |= work && kind[j] == kPartHash;
@@ -506,6 +507,11 @@ struct RunPlan {
     std::vector<uint8_t> part_kind;
     DevBuf<uint8_t> dpart_hash;
     const uint32_t* perm = nullptr;
+    // per-part runs with both kernels: the edge-wise launch on a side
+    // stream (forked and joined by events), so that it fills the SMs the
+    // hash launch's last CTAs leave idle
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     // graph replay: the captured kernels read this plan-owned control block,
     // which each replay refills with the run's stop word
     DevBuf<RunCtl> ctl;
@@ -523,6 +529,9 @@ struct RunPlan {
     ~RunPlan() {
         if (exec) cudaGraphExecDestroy(exec);
         if (done) cudaEventDestroy(done);
+        if (fork_ev) cudaEventDestroy(fork_ev);
+        if (join_ev) cudaEventDestroy(join_ev);
+        if (side) cudaStreamDestroy(side);
     }
 };
 
@@ -670,6 +679,11 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
                 P->npartials += (uint64_t)P->hgrid;
             }
         }
+        if (P->nitems && P->hgrid && P->nt) {
+            PGB_CUDA(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
+            PGB_CUDA(cudaEventCreateWithFlags(&P->fork_ev, cudaEventDisableTiming));
+            PGB_CUDA(cudaEventCreateWithFlags(&P->join_ev, cudaEventDisableTiming));
+        }
         if (P->host_slot) P->npartials += 1;  // written once the host parts are counted
         P->partials.alloc(P->npartials, s);
         if (P->host_slot) PGB_CUDA(cudaMemsetAsync(P->partials.ptr + P->npartials - 1, 0, 8, s));
@@ -711,21 +725,32 @@ static void enqueue_count(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cud
             launch_hash(P.H, P.items.ptr, P.nitems, P.per_vertex, s, P.cursor.ptr, P.partials.ptr, P.grid,
                         P.threads, ctl);
     } else {
-        // the hash parts first (their totals in partials [0, hgrid)), then
-        // the edge-wise tuples of the edge-wise parts
-        if (P.nitems && P.hgrid)
-            launch_hash(P.H, P.items.ptr, P.nitems, P.per_vertex, s, P.cursor.ptr, P.partials.ptr, P.hgrid,
-                        P.threads, ctl);
+        // the hash parts (their totals in partials [0, hgrid)) and the
+        // edge-wise tuples of the edge-wise parts; with both, the edge-wise
+        // launch runs on the side stream, beside the hash launch's tail
         unsigned int* bcur = P.cursor.ptr + 1;
         unsigned long long* bpart = P.partials.ptr + P.hgrid;
         PGB_CUDA(cudaMemsetAsync(bcur, 0, 4, s));
+        const bool fork = P.side != nullptr;
+        if (fork) {
+            PGB_CUDA(cudaEventRecord(P.fork_ev, s));
+            PGB_CUDA(cudaStreamWaitEvent(P.side, P.fork_ev, 0));
+        }
+        if (P.nitems && P.hgrid)
+            launch_hash(P.H, P.items.ptr, P.nitems, P.per_vertex, s, P.cursor.ptr, P.partials.ptr, P.hgrid,
+                        P.threads, ctl);
+        const cudaStream_t es = fork ? P.side : s;
         if (P.per_vertex)
-            k_tc_persistent<true><<<P.grid, kThreads, 0, s>>>(P.G, P.dt.ptr, P.dcp.ptr, P.nt, P.chunk, bcur, bpart,
-                                                             ctl);
+            k_tc_persistent<true><<<P.grid, kThreads, 0, es>>>(P.G, P.dt.ptr, P.dcp.ptr, P.nt, P.chunk, bcur, bpart,
+                                                              ctl);
         else
-            k_tc_persistent<false><<<P.grid, kThreads, 0, s>>>(P.G, P.dt.ptr, P.dcp.ptr, P.nt, P.chunk, bcur,
-                                                              bpart, ctl);
+            k_tc_persistent<false><<<P.grid, kThreads, 0, es>>>(P.G, P.dt.ptr, P.dcp.ptr, P.nt, P.chunk, bcur,
+                                                               bpart, ctl);
         PGB_CHECK_LAUNCH("k_tc_persistent");
+        if (fork) {
+            PGB_CUDA(cudaEventRecord(P.join_ev, P.side));
+            PGB_CUDA(cudaStreamWaitEvent(s, P.join_ev, 0));
+        }
     }
     if (ev1) PGB_CUDA(cudaEventRecord(ev1, s));
 }

@@ -81,7 +81,8 @@ class TcOpts(ctypes.Structure):
                 ("per_triple", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("device_budget", ctypes.c_uint64), ("chunk_edges", ctypes.c_uint32),
                 ("hash_threads", ctypes.c_uint32), ("cancel", ctypes.c_void_p), ("host_threads", ctypes.c_uint32),
-                ("host_share_ppm", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
+                ("host_share_ppm", ctypes.c_uint32), ("hash_min_lookups", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 1)]
 
 
 class BlocksStats(ctypes.Structure):

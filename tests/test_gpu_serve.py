@@ -187,3 +187,21 @@ def test_serve_without_per_vertex():
         assert P.pgb_server_wait(srv, j, 60.0)[0] == oracle.tc_node_iterator(oracle.clean(*g), False)[0]
     finally:
         P.pgb_server_destroy(srv)
+
+
+def test_serve_benchmark_mix_sample_matches_oracle():
+    """A seeded sample of the benchmark's own serving workload (10,000 jobs,
+    scales up to 16; job i seeded by i, as bench.py makes it): every sampled
+    job, counted in one batched mix, equals the oracle's counts."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    idx = sorted(np.random.default_rng(2027).choice(10000, size=24, replace=False).tolist())
+    jobs = [bench.serve_job(i, 16) for i in idx]
+    want = expected(jobs)
+    res, stats = run_server(jobs, P.PGB_SERVE_BATCHED)
+    assert stats["batches"] < len(jobs)
+    for (T, t), (gT, gt, _) in zip(want, res):
+        assert gT == T and np.array_equal(gt, t)
