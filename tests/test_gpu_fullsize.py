@@ -36,12 +36,13 @@ def digest(t):
     return hashlib.sha256(np.ascontiguousarray(t, dtype="<u8").tobytes()).hexdigest()
 
 
-def run_full(name, p, mode, variant=P.PGB_VAR_AUTO, stream_budget=None):
+def run_full(name, p, mode, variant=P.PGB_VAR_AUTO, stream_budget=None, cache_budget=None):
     want = make_golden.load(name)
     src, dst, n = make_golden.generate(make_golden.WORKLOADS[name])
     assert n == want["n"]
     ds = torch.from_numpy(src).cuda()
     dd = torch.from_numpy(dst).cuda()
+    src_keep = (src, dst) if cache_budget is not None else None
     del src, dst
     g = P.pgb_graph_from_edges(ds, dd, n)
     assert P.pgb_graph_info(g)[1] == want["m"]
@@ -63,6 +64,21 @@ def run_full(name, p, mode, variant=P.PGB_VAR_AUTO, stream_budget=None):
         T2, _ = P.pgb_tc_result_get(r, per_vertex=tv)
         assert T2 == T and P.pgb_tc_result_stream(r)[1] > 1
         assert np.array_equal(tv.cpu().numpy(), t)
+    b.free()
+    del r
+    torch.cuda.empty_cache()
+    if cache_budget is not None:
+        # a fresh partition with the columns offloaded too (block cache tier)
+        b2 = P.pgb_partition(P.pgb_graph_from_edges(torch.from_numpy(src_keep[0]).cuda(),
+                                                    torch.from_numpy(src_keep[1]).cuda(), n), p)
+        P.pgb_blocks_offload_columns(b2, cache_budget[1])
+        r = P.pgb_tc_run(b2, P.pgb_tc_opts_default(device_budget=cache_budget[0]))
+        T3, _ = P.pgb_tc_result_get(r, per_vertex=tv)
+        assert T3 == T and P.pgb_tc_result_stream(r, slice_loads=True)[2] > 0
+        assert digest(tv.cpu().numpy()) == want["t_sha256"]
+        b2.free()
+        del r
+        torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("mode", [P.PGB_MODE_PLAIN, P.PGB_MODE_PERSISTENT])
@@ -85,7 +101,8 @@ def test_grid4096_p32_full_size(mode):
 
 
 def test_rmat27_p64_full_size_and_streamed():
-    """R-MAT scale 27 (2.1 G edges, the autotuned 512-thread shape): the oracle's
-    sampled t[x], sum t = 3 T, and the same counts with the in-edge index
-    streamed under a 16 GiB budget."""
-    run_full("rmat27", 64, P.PGB_MODE_PERSISTENT, stream_budget=16 << 30)
+    """R-MAT scale 27 (2.1 G edges, the autotuned 512-thread shape): the
+    oracle's total and every per-vertex count, resident; with the columns
+    offloaded too under a 4 GiB budget (block cache tier, 45 row ranges);
+    and with the in-edge index streamed under a 16 GiB budget."""
+    run_full("rmat27", 64, P.PGB_MODE_PERSISTENT, stream_budget=16 << 30, cache_budget=(4 << 30, 45))
