@@ -352,8 +352,9 @@ void pgb_tc_opts_default(pgb_tc_opts* o);
  * PGB_E_BUDGET, PGB_E_NOMEM, PGB_E_CUDA. */
 int pgb_tc_run(const pgb_blocks* b, const pgb_tc_opts* opts, void* stream, pgb_tc_result** out);
 
-/* Wait for the run and fetch results.  total: global triangle count (may be
- * NULL).  per_vertex: n uint64 counts t[x] indexed by ORIGINAL vertex ID
+/* Wait for the run and fetch results (Section 3.3: the reduce_dev result of
+ * the kernel, n_t in Listing 5, and its per-vertex form).  total: global
+ * triangle count (may be NULL).  per_vertex: n uint64 counts t[x] indexed by ORIGINAL vertex ID
  * (may be NULL; PGB_E_STATE if the run had per_vertex = 0).  Fails with
  * PGB_E_CANCELLED, writing nothing, when a kernel of the run stopped early
  * on its cancel token. */
