@@ -61,6 +61,10 @@ __global__ void k_cc_hook(const uint32_t* __restrict__ rowidx, const uint32_t* _
         if (cu == cv) continue;
         const bool u_hi = __ldg(perm + cu) > __ldg(perm + cv);
         const uint32_t hi = u_hi ? cu : cv, lo = u_hi ? cv : cu;
+        // read first: once a root has been hooked, the other edges that would
+        // hook it skip the compare-and-swap (a root shared by many edges, such
+        // as a giant component's, is contended only until its first hook)
+        if (*reinterpret_cast<volatile uint32_t*>(C + hi) != hi) continue;
         if (atomicCAS(C + hi, hi, lo) == hi) ++mine;
     }
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
