@@ -308,17 +308,20 @@ __global__ void __launch_bounds__(T, 1024 / T)
               uint32_t nitems, unsigned int* __restrict__ cursor, unsigned long long* __restrict__ partials,
               RunCtl* __restrict__ ctl) {
     extern __shared__ uint32_t hsm[];
-    // Region A: the bitmap of a bitmap-mode item, or the keys and member
-    // masks of a hash-mode item; all zero between items.  Region B (per-vertex
-    // counts only) holds 16-bit counters, two per word (a counter counts at
-    // most one hit per in-edge of the item): in hash mode one per table slot;
-    // in bitmap mode, after a 16-bit running popcount per bitmap word, one per
-    // key, indexed by the key's rank in v's sorted list.
+    // Region A: the bitmap of a bitmap-mode item, the 16-bit rank entries of
+    // a dense-mode item (ranges of at most 2 x region A words), or the keys
+    // and member masks of a hash-mode item; all zero between items.  Region B
+    // (per-vertex counts only) holds 16-bit counters, two per word (a counter
+    // counts at most one hit per in-edge of the item): in hash mode one per
+    // table slot; in bitmap and dense mode one per key, indexed by the key's
+    // rank in v's sorted list, after (bitmap mode) a 16-bit running popcount
+    // per bitmap word.
     uint32_t* regA = hsm;
     constexpr int kHThreads = T, kHWarps = T / 32;
     constexpr uint32_t kRegionA = 32u * T;           // words
     constexpr uint32_t kBitmapBits = 32u * kRegionA;  // widest third-vertex range held as a bitmap
     constexpr uint32_t kMaxSlots = kRegionA / 2;     // table slots (keys, then member masks)
+    constexpr uint32_t kDenseRanks = 2u * kRegionA;   // widest range held as 16-bit rank entries
     uint32_t* regB = hsm + kRegionA;
     __shared__ uint32_t s_wsum[kHWarps];
     __shared__ VItem s_it, s_itn;      // current item and the next one (prefetched)
@@ -370,6 +373,11 @@ __global__ void __launch_bounds__(T, 1024 / T)
         const uint32_t rlo = I.clip ? I.lo : (single ? I.v0 + 1 : 0);
         const uint32_t rhi = I.clip ? I.hi : G.n;
         const bool bitmap = single && rhi - rlo <= kBitmapBits;
+        // a range of at most kDenseRanks ranks (the top of the degree order:
+        // most lookups at R-MAT scale) is held densely instead: one 16-bit
+        // entry per rank, the key's rank in the list plus one (0: absent),
+        // so a lookup is one shared load giving the hit and its counter
+        const bool dense = bitmap && rhi - rlo <= kDenseRanks;
         // a singleton's (clipped) list; its row bounds came with the item
         uint32_t rb = 0, re = 0;
         if (single) {
@@ -385,6 +393,7 @@ __global__ void __launch_bounds__(T, 1024 / T)
         uint32_t* masks = regA + kMaxSlots;
         uint32_t* cnts = bitmap ? regB + kRegionA / 2 : regB;  // 16-bit counter i: half i & 1 of word i >> 1
         uint16_t* pre = reinterpret_cast<uint16_t*>(regB);
+        uint16_t* dense16 = reinterpret_cast<uint16_t*>(regA);
         if (!bitmap)
             for (uint32_t i = tid; i < S; i += kHThreads) keys[i] = kEmpty;
         if (PV) {
@@ -399,7 +408,8 @@ __global__ void __launch_bounds__(T, 1024 / T)
             if (tid == 0 && rb < re) s_vmask = 1u;
             for (uint32_t q = rb + tid; q < re; q += kHThreads) {
                 const uint32_t x = __ldg(G.col + (q - G.vbase));
-                if (bitmap) atomicOr(&regA[(x - rlo) >> 5], 1u << ((x - rlo) & 31));
+                if (dense) dense16[x - rlo] = (uint16_t)(q - rb + 1);  // at most K keys: fits 16 bits
+                else if (bitmap) atomicOr(&regA[(x - rlo) >> 5], 1u << ((x - rlo) & 31));
                 else table_insert(keys, masks, x, 0u, L);
             }
         } else {
@@ -417,7 +427,7 @@ __global__ void __launch_bounds__(T, 1024 / T)
             }
         }
         __syncthreads();
-        if (PV && bitmap) {
+        if (PV && bitmap && !dense) {
             // running popcount per bitmap word: thread t owns 32 consecutive
             // words; a CTA scan of the per-thread sums gives each its base
             const uint32_t nwords = (rhi - rlo + 31) >> 5;
@@ -541,7 +551,11 @@ __global__ void __launch_bounds__(T, 1024 / T)
                         const uint32_t x = xv[i];
                         bool hit;
                         uint32_t h = 0;
-                        if (bitmap) {
+                        if (dense) {
+                            const uint32_t r1 = dense16[x - rlo];
+                            hit = r1 != 0u;
+                            h = r1 - 1u;
+                        } else if (bitmap) {
                             const uint32_t d = x - rlo;
                             const uint32_t word = regA[d >> 5];
                             hit = (word >> (d & 31)) & 1u;
@@ -608,7 +622,9 @@ __global__ void __launch_bounds__(T, 1024 / T)
             if (tid < I.nv && s_vcnt[tid]) atomicAdd(G.tv + I.v0 + tid, (unsigned long long)s_vcnt[tid]);
         }
         // leave region A all zero for the next item
-        if (bitmap) {
+        if (dense) {
+            for (uint32_t q = rb + tid; q < re; q += kHThreads) dense16[__ldg(G.col + (q - G.vbase)) - rlo] = 0;
+        } else if (bitmap) {
             for (uint32_t q = rb + tid; q < re; q += kHThreads) regA[(__ldg(G.col + (q - G.vbase)) - rlo) >> 5] = 0;
         } else {
             for (uint32_t i = tid; i < S; i += kHThreads) {
