@@ -533,6 +533,37 @@ def autotune_bench(args):
             "auto_vs_best_single_choice": best_single / rows["auto"]["kernel_ms"]}
 
 
+def pattern_bench(args):
+    """The other multi-block patterns on one partition: 4-cliques and 4-cycles
+    (wall time per call, each call synchronises), counts equal across
+    repeats."""
+    import torch
+    from paper_2209_04541_b300 import pgabb as P
+    w = dict(WORKLOADS[args.pattern_workload])
+    s_np, d_np, n = generate(w)
+    stream = torch.cuda.current_stream()
+    g = P.pgb_graph_from_edges(torch.from_numpy(s_np).cuda(), torch.from_numpy(d_np).cuda(), n, stream)
+    del s_np, d_np
+    b = P.pgb_partition(g, w["p"], P.PGB_CUT_NNZ, stream)
+    g.free()
+    info = P.pgb_blocks_info(b)
+    out = {"workload": w["desc"], "unique_edges": info["m"]}
+    for name, fn in (("k4", P.pgb_k4_count), ("c4", P.pgb_c4_count)):
+        times, vals = [], set()
+        for i in range(3):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            vals.add(fn(b, stream))
+            if i:
+                times.append(time.perf_counter() - t)
+        assert len(vals) == 1, f"{name} counts differ between calls"
+        wall = statistics.median(times)
+        out[name] = {"count": vals.pop(), "wall_ms": 1e3 * wall, "edges_s": info["m"] / wall}
+    b.free()
+    torch.cuda.empty_cache()
+    return out
+
+
 def stream_bench(args):
     """The streaming tiers against the same graph fully resident: the in-edge
     index in pinned host memory (budget --stream-budget-gb), and the block
@@ -658,6 +689,8 @@ def main(argv=None):
     ap.add_argument("--tiers-workloads", default="rmat24,grid4096")
     ap.add_argument("--tiers-steps", type=int, default=3)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-patterns", action="store_true")
+    ap.add_argument("--pattern-workload", choices=sorted(WORKLOADS), default="rmat20")
     ap.add_argument("--autotune-workload", choices=sorted(WORKLOADS), default="grid4096_u_rmat22")
     ap.add_argument("--stream-workload", choices=["rmat24", "rmat22", "rmat27"], default="rmat27",
                     help="streamed graph (default: R-MAT s27, p=64, the out-of-core configuration)")
@@ -834,6 +867,12 @@ def main(argv=None):
             autotune = autotune_bench(args)
         except Exception as exc:  # reported, not hidden
             autotune = {"error": f"{type(exc).__name__}: {exc}"}
+    patterns = None
+    if rank == 0 and not args.no_patterns:
+        try:
+            patterns = pattern_bench(args)
+        except Exception as exc:  # reported, not hidden
+            patterns = {"error": f"{type(exc).__name__}: {exc}"}
     streamed = None
     if rank == 0 and not args.no_stream:
         try:
@@ -859,7 +898,8 @@ def main(argv=None):
                                  % (8 * mraw / 1e9, 8 * m_u / 1e9)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "gpu_launches_per_step": launches / args.steps,
-                "clocks": clocks, "serve": serve, "tiers": tiers, "autotune": autotune, "stream": streamed}
+                "clocks": clocks, "serve": serve, "tiers": tiers, "autotune": autotune, "patterns": patterns,
+                "stream": streamed}
         line["serve_summary"] = serve_summary(serve)
         print(json.dumps(line), flush=True)
     if dist.is_initialized():
