@@ -683,7 +683,7 @@ def main(argv=None):
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=10000)
     ap.add_argument("--serve-max-scale", type=int, default=16,
-                    help="largest R-MAT scale and log2 n of the mix (the survey's 22 needs ~66 G raw edges)")
+                    help="largest R-MAT scale and log2 n of the mix (scales up to 22 would need about 66 G raw edges)")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-tiers", action="store_true")
     ap.add_argument("--tiers-workloads", default="rmat24,grid4096")
