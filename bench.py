@@ -289,22 +289,16 @@ def run_reference(args, rank, world):
 
 
 def serve_job(i: int, max_scale: int):
-    """Job i of the serving workload: the families in equal thirds, R-MAT
-    (scale uniform in [10, max_scale], edge factor uniform in [8, 32]),
-    Erdos-Renyi (n log-uniform in [2^10, 2^max_scale], average degree
-    log-uniform in [4, 64]) and random geometric graphs (n log-uniform,
-    average degree 6); seed = job index."""
-    rng = np.random.default_rng(i)
-    fam = i % 3
-    if fam == 0:
-        s = int(rng.integers(10, max_scale + 1))
-        ef = int(rng.integers(8, 33))
-        return graphgen.rmat(s, ef, i)
-    n = int(round(2.0 ** rng.uniform(10, max_scale)))
-    if fam == 1:
-        deg = 2.0 ** rng.uniform(2, 6)
-        return graphgen.er_pairs(n, max(1, int(n * deg / 2)), i)
-    return graphgen.rgg(n, None, i)
+    """Job i of the serving workload (graphgen.serve_spec), generated on the
+    host: (src, dst, n) numpy arrays."""
+    return graphgen.serve_job(i, max_scale)
+
+
+def serve_job_device(i: int, max_scale: int, stream=None):
+    """Job i generated on the device (the same edges as serve_job): (src,
+    dst, n) with uint32 CUDA tensors written on `stream`."""
+    from graphgen import device as gd
+    return gd.serve_job(i, max_scale, stream)
 
 
 def serve_jobs(count: int, max_scale: int):
@@ -358,12 +352,178 @@ def serve_bench(args):
                          "p99_ms": float(np.percentile(lat_ms, 99)), "launches": st["batches"]}
         sweep[f"{factor:.2f}"] = {"rate_jobs_s": rate, **res}
     return {"metric": "serve jobs/s and p50/p99 latency", "jobs": len(jobs), "raw_edges": edges,
-            "mix": f"thirds of R-MAT (scale 10-{args.serve_max_scale}, ef 8-32), ER (n 2^10-2^{args.serve_max_scale} "
+            "mix": f"thirds of R-MAT (scale 10-{args.serve_max_scale}, ef 8-32, Feistel relabelling), ER (n "
+                   f"2^10-2^{args.serve_max_scale} "
                    "log-uniform, avg degree 4-64 log-uniform), RGG (avg degree 6); seed = job index; per-vertex on",
             "capacity_jobs_s": {"serial": cap_s, "batched": cap_b},
             "poisson_rate_jobs_s": sweep["0.80"]["rate_jobs_s"],
             "poisson": {k: sweep["0.80"][k] for k in ("serial", "batched")},
             "poisson_sweep_by_fraction_of_serial_capacity": sweep,
+            "batched_launches_closed_loop": st_b["batches"]}
+
+
+def run_serve_device(count, max_scale, mode, arrivals=None, window_edges=1 << 31, lookahead=64,
+                     lookahead_edges=1 << 30):
+    """The serving workload with jobs made on the device just before they
+    are submitted (device arrays the server borrows until the job ends): a
+    producer thread generates job k on its own stream, the caller submits it
+    at its arrival offset (arrivals in seconds; None: as soon as the window
+    allows), a waiter thread collects results.  At most `window_edges` raw
+    edges are submitted and not yet finished, which bounds the device copies
+    of queued jobs; the producer runs ahead by at most `lookahead` jobs and
+    `lookahead_edges` raw edges, on a high-priority stream.  Totals only.
+    Returns (totals, latencies s, makespan s, stats, raw edges, client dict:
+    submissions later than 1 ms past their arrival, and seconds spent waiting
+    for the generator, for the window, and in submit calls)."""
+    import queue
+    import threading
+
+    import torch
+    from paper_2209_04541_b300 import pgabb as P
+    srv = P.pgb_server_create(P.pgb_server_opts_default(mode=mode, per_vertex=0))
+    gen_q = queue.Queue(maxsize=lookahead)
+    done_q = queue.Queue()
+    stop = threading.Event()
+    cond = threading.Condition()
+    state = {"out": 0, "err": None, "ahead": 0}
+    totals, lats, subs = [0] * count, [0.0] * count, [0.0] * count
+    stream = torch.cuda.Stream(priority=-1)
+
+    def producer():
+        try:
+            for i in range(count):
+                if stop.is_set():
+                    return
+                with cond:
+                    cond.wait_for(lambda: stop.is_set() or state["ahead"] <= lookahead_edges)
+                s, d, n = serve_job_device(i, max_scale, stream)
+                stream.synchronize()
+                with cond:
+                    state["ahead"] += int(s.numel())
+                gen_q.put((s, d, n))
+        except BaseException as exc:  # handed to the caller
+            gen_q.put(exc)
+
+    def waiter():
+        try:
+            for _ in range(count):
+                item = done_q.get()
+                if item is None:
+                    return
+                k, jid, m = item
+                totals[k], _, lats[k] = P.pgb_server_wait(srv, jid, 900.0)
+                with cond:
+                    state["out"] -= m
+                    cond.notify_all()
+        except BaseException as exc:
+            state["err"] = exc
+            with cond:
+                cond.notify_all()
+
+    th_p = threading.Thread(target=producer, daemon=True)
+    th_w = threading.Thread(target=waiter, daemon=True)
+    th_p.start()
+    th_w.start()
+    raw = late = 0
+    t_gen = t_win = t_sub = 0.0
+    submitted = []
+    try:
+        t0 = time.perf_counter()
+        for k in range(count):
+            ta = time.perf_counter()
+            item = gen_q.get()
+            if isinstance(item, BaseException):
+                raise item
+            s, d, n = item
+            m = int(s.numel())
+            raw += m
+            tb = time.perf_counter()
+            t_gen += tb - ta
+            if arrivals is not None:
+                delay = t0 + arrivals[k] - tb
+                if delay > 0:
+                    time.sleep(delay)
+            tc = time.perf_counter()
+            with cond:
+                cond.wait_for(lambda: state["err"] is not None or state["out"] == 0
+                              or state["out"] + m <= window_edges)
+                if state["err"] is not None:
+                    raise state["err"]
+                state["out"] += m
+            subs[k] = time.perf_counter()
+            t_win += subs[k] - tc
+            if arrivals is not None and subs[k] - (t0 + arrivals[k]) > 1e-3:
+                late += 1
+            jid = P.pgb_server_submit(srv, s, d, n, borrow=True)
+            t_sub += time.perf_counter() - subs[k]
+            submitted.append(jid)
+            done_q.put((k, jid, m))
+            del s, d, item
+            with cond:
+                state["ahead"] -= m
+                cond.notify_all()
+        th_w.join()
+        if state["err"] is not None:
+            raise state["err"]
+        span = max(subs[k] + lats[k] for k in range(count)) - t0
+        stats = P.pgb_server_stats(srv)
+    finally:
+        stop.set()
+        with cond:
+            cond.notify_all()
+        if th_w.is_alive():
+            # an error: cancel what is left so that the waiter returns
+            # before the server goes away
+            for jid in submitted:
+                try:
+                    P.pgb_server_cancel(srv, jid)
+                except Exception:
+                    pass
+            done_q.put(None)
+            th_w.join()
+        while th_p.is_alive():
+            try:
+                gen_q.get(timeout=0.1)
+            except queue.Empty:
+                pass
+        P.pgb_server_destroy(srv)
+    client = {"late_submissions": late, "generator_wait_s": round(t_gen, 3), "window_wait_s": round(t_win, 3),
+              "submit_s": round(t_sub, 3)}
+    return totals, lats, span, stats, raw, client
+
+
+def serve_bench_device(args):
+    """The serving workload at its stated size (R-MAT scales up to 22, ER and
+    RGG n up to 2^22): jobs made on the device as they are submitted, since
+    the whole mix (tens of G raw edges) fits neither host nor device memory.
+    Capacity (closed loop) and a Poisson load at 0.8x the one-at-a-time
+    capacity, for both modes; totals only."""
+    from paper_2209_04541_b300 import pgabb as P
+    J, S = args.serve_jobs, args.serve_max_scale
+    run_serve_device(24, S, P.PGB_SERVE_BATCHED)  # warm-up
+    tot_s, _, span_s, _, raw, cl_s = run_serve_device(J, S, P.PGB_SERVE_SERIAL)
+    tot_b, _, span_b, st_b, _, cl_b = run_serve_device(J, S, P.PGB_SERVE_BATCHED)
+    assert tot_s == tot_b, "serial and batched counts differ"
+    cap_s, cap_b = J / span_s, J / span_b
+    rate = 0.8 * cap_s
+    rng = np.random.default_rng(12345)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=J))
+    res = {}
+    for name, mode in (("serial", P.PGB_SERVE_SERIAL), ("batched", P.PGB_SERVE_BATCHED)):
+        tot, lat, span, st, _, client = run_serve_device(J, S, mode, arrivals)
+        assert tot == tot_s
+        lat_ms = np.array(lat) * 1e3
+        res[name] = {"jobs_s": J / span, "p50_ms": float(np.percentile(lat_ms, 50)),
+                     "p99_ms": float(np.percentile(lat_ms, 99)), "launches": st["batches"], "client": client}
+    return {"metric": "serve jobs/s and p50/p99 latency", "jobs": J, "raw_edges": raw,
+            "triangles": int(sum(tot_s)),
+            "mix": f"thirds of R-MAT (scale 10-{S}, ef 8-32, Feistel relabelling), ER (n 2^10-2^{S} log-uniform, "
+                   "avg degree 4-64 log-uniform), RGG (avg degree 6); seed = job index; generated on the device, "
+                   "submitted as borrowed device arrays; totals only",
+            "capacity_jobs_s": {"serial": cap_s, "batched": cap_b},
+            "capacity_edges_s": {"serial": raw / span_s, "batched": raw / span_b},
+            "capacity_client": {"serial": cl_s, "batched": cl_b},
+            "poisson_rate_jobs_s": rate, "poisson": res,
             "batched_launches_closed_loop": st_b["batches"]}
 
 
@@ -682,8 +842,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=10000)
-    ap.add_argument("--serve-max-scale", type=int, default=16,
-                    help="largest R-MAT scale and log2 n of the mix (scales up to 22 would need about 66 G raw edges)")
+    ap.add_argument("--serve-max-scale", type=int, default=0,
+                    help="largest R-MAT scale and log2 n of the mix (0: 16 for the host-generated mix, 22 with "
+                         "--serve-full)")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="the serving mix at its stated size (scales up to 22, device-generated); instead of the "
+                         "host-generated mix")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-tiers", action="store_true")
     ap.add_argument("--tiers-workloads", default="rmat24,grid4096")
@@ -852,7 +1016,12 @@ def main(argv=None):
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_serve:
         try:
-            serve = serve_bench(args)
+            if not args.serve_max_scale:
+                args.serve_max_scale = 22 if args.serve_full else 16
+            if args.serve_full:
+                serve = serve_bench_device(args)
+            else:
+                serve = serve_bench(args)
         except Exception as exc:  # reported, not hidden: the TC line stands on its own
             serve = {"error": f"{type(exc).__name__}: {exc}"}
     tiers = None

@@ -13,7 +13,9 @@
  *     mix(key + (c + 1) * 0x9E3779B97F4A7C15),   key = mix(seed),
  * where mix() is SplitMix64's output function.  Because each draw depends
  * only on (seed, c), the parallel generators are bit-identical for any
- * thread count.
+ * thread count.  The stream, the R-MAT edge step and the Feistel
+ * relabelling live in gg_stream.h, which the device generators
+ * (graphgen_dev.cu) include too.
  *
  * Workloads (synthetic stand-ins for the paper's real-world datasets, which
  * are not available; the paper's own synthetic graph is a Kronecker graph):
@@ -31,24 +33,7 @@
 #include <omp.h>
 #endif
 
-#define GG_GOLDEN 0x9E3779B97F4A7C15ULL
-
-static inline uint64_t gg_mix(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    return z ^ (z >> 31);
-}
-
-/* Draw number c of the stream keyed by seed. */
-static inline uint64_t gg_draw(uint64_t key, uint64_t c) {
-    return gg_mix(key + (c + 1) * GG_GOLDEN);
-}
-
-/* Uniform integer in [0, n) from the high 32 bits of a draw (Lemire's
- * multiply-shift; bias below n / 2^32). */
-static inline uint32_t gg_below(uint32_t x32, uint32_t n) {
-    return (uint32_t)(((uint64_t)x32 * (uint64_t)n) >> 32);
-}
+#include "gg_stream.h"
 
 uint64_t gg_splitmix_draw(uint64_t seed, uint64_t c) { return gg_draw(gg_mix(seed), c); }
 
@@ -71,43 +56,31 @@ static void gg_permutation(uint32_t n, uint64_t seed, uint32_t* perm) {
  * at each level one 32-bit uniform picks a quadrant with probabilities
  * (a, b, c, 1-a-b-c) (top-left, top-right, bottom-left, bottom-right),
  * setting one bit of src (row) and dst (column), most significant first.
- * No noise.  If permute != 0, both endpoints are relabelled by a seeded
- * permutation.  Duplicates and self-loops are kept.
+ * No noise.  Relabelling of both endpoints: permute = 0 none, 1 a seeded
+ * Fisher-Yates permutation (as Graph500), 2 the seeded Feistel bijection of
+ * gg_stream.h (evaluated per endpoint, so it parallelises).  Duplicates and
+ * self-loops are kept.
  */
 int gg_rmat(uint32_t scale, uint64_t m, double a, double b, double c, uint64_t seed,
             int permute, uint32_t* src, uint32_t* dst) {
     if (scale == 0 || scale > 31 || a < 0 || b < 0 || c < 0 || a + b + c > 1.0) return -1;
+    if (permute < 0 || permute > 2) return -1;
     const uint64_t key = gg_mix(seed);
-    const uint64_t ta = (uint64_t)(a * 4294967296.0);
-    const uint64_t tb = (uint64_t)((a + b) * 4294967296.0);
-    const uint64_t tc = (uint64_t)((a + b + c) * 4294967296.0);
-    const uint64_t draws_per_edge = (scale + 1) / 2;
+    uint64_t ta, tb, tc;
+    gg_rmat_thresholds(a, b, c, &ta, &tb, &tc);
+    const uint64_t fkey = gg_mix(seed ^ GG_TAG_FEISTEL);
     int64_t mm = (int64_t)m;
 #pragma omp parallel for schedule(static)
     for (int64_t e = 0; e < mm; ++e) {
-        uint32_t s = 0, d = 0;
-        uint64_t x = 0;
-        for (uint32_t lvl = 0; lvl < scale; ++lvl) {
-            uint32_t r;
-            if ((lvl & 1u) == 0) {
-                x = gg_draw(key, (uint64_t)e * draws_per_edge + lvl / 2);
-                r = (uint32_t)(x >> 32);
-            } else {
-                r = (uint32_t)x;
-            }
-            uint32_t bit = 1u << (scale - 1 - lvl);
-            if (r < ta) {
-            } else if (r < tb) {
-                d |= bit;
-            } else if (r < tc) {
-                s |= bit;
-            } else {
-                s |= bit; d |= bit;
-            }
+        uint32_t s, d;
+        gg_rmat_edge(key, scale, (uint64_t)e, ta, tb, tc, &s, &d);
+        if (permute == 2) {
+            s = gg_feistel(s, scale, fkey);
+            d = gg_feistel(d, scale, fkey);
         }
         src[e] = s; dst[e] = d;
     }
-    if (permute) {
+    if (permute == 1) {
         uint32_t n = 1u << scale;
         uint32_t* perm = (uint32_t*)malloc((size_t)n * sizeof(uint32_t));
         if (!perm) return -2;
@@ -117,6 +90,15 @@ int gg_rmat(uint32_t scale, uint64_t m, double a, double b, double c, uint64_t s
         free(perm);
     }
     return 0;
+}
+
+/* The Fisher-Yates relabelling gg_rmat applies for `seed` (permute = 1),
+ * for a device generator to apply. */
+void gg_shuffle_permutation(uint32_t n, uint64_t seed, uint32_t* perm) { gg_permutation(n, seed, perm); }
+
+/* The Feistel relabelling of x in [0, 2^bits) for seed (for checks). */
+uint32_t gg_feistel_label(uint32_t x, uint32_t bits, uint64_t seed) {
+    return gg_feistel(x, bits, gg_mix(seed ^ GG_TAG_FEISTEL));
 }
 
 /*

@@ -418,8 +418,10 @@ int pgb_tc_count_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, uin
  * Results are bit-identical to pgb_tc_run on each graph alone.  A job with
  * an endpoint >= n fails alone (PGB_E_INVAL at wait).  The server keeps its
  * own CUDA streams and threads on the device current at create; its threads
- * take device memory from the CUDA stream-ordered allocator
- * (cudaMallocAsync), not from hooks set with pgb_set_allocator. */
+ * and queued device inputs take device memory from a stream-ordered memory
+ * pool of the server's own (cudaMemPoolCreate), which keeps freed memory
+ * mapped for the next batch until pgb_server_destroy; never from hooks set
+ * with pgb_set_allocator. */
 typedef struct pgb_server pgb_server;
 
 #define PGB_SERVE_BATCHED 0
@@ -458,10 +460,27 @@ uint64_t pgb_server_job_bytes(uint64_t m, uint32_t n);
 int pgb_server_create(const pgb_server_opts* opts, pgb_server** out);
 
 /* Queue one job; src/dst (m raw pairs, IDs < n) are copied before return.
+ * Host arrays (mem = PGB_MEM_HOST) are copied into host memory; device
+ * arrays (PGB_MEM_DEVICE) into a device buffer of 8 bytes per raw edge that
+ * the job holds while queued (outside the admission budget), copied on the
+ * legacy default stream: after work the caller queued there, while writes
+ * on non-blocking streams must be complete before the call.
  * Errors: PGB_E_BUDGET (the job can never fit the budget), PGB_E_INVAL,
- * PGB_E_STATE (server shutting down).  Vertex IDs >= n make the job fail. */
+ * PGB_E_STATE (server shutting down), PGB_E_CUDA.  Vertex IDs >= n make the
+ * job fail. */
 int pgb_server_submit(pgb_server* s, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, int mem,
                       uint64_t* job_id);
+
+/* Queue one job on device arrays that the server borrows instead of
+ * copying: src/dst (m raw pairs, IDs < n, device memory of the server's
+ * device) must be fully written before the call (their producer stream
+ * synchronised) and stay valid and unchanged until pgb_server_wait for the
+ * job has returned, or the server is destroyed.  The job's batch reads them
+ * on its own stream when it starts; submit itself queues no device work, so
+ * it does not wait behind kernels already running.  Errors as
+ * pgb_server_submit. */
+int pgb_server_submit_borrowed(pgb_server* s, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n,
+                               uint64_t* job_id);
 
 /* Hold (paused != 0) or resume admission: while held, queued jobs stay
  * queued; jobs already admitted continue. */

@@ -32,8 +32,12 @@ void end_launch_capture() { t_capture_count = nullptr; }
 void live_handles_add(int d) { g_live += d; }
 
 static thread_local bool t_native_only = false;
+static thread_local cudaMemPool_t t_pool = nullptr;
 
-void use_native_allocator_in_this_thread() { t_native_only = true; }
+void use_native_allocator_in_this_thread(cudaMemPool_t pool) {
+    t_native_only = true;
+    t_pool = pool;
+}
 
 void* dev_alloc(size_t bytes, cudaStream_t s, bool* native) {
     if (bytes == 0) return nullptr;
@@ -50,7 +54,7 @@ void* dev_alloc(size_t bytes, cudaStream_t s, bool* native) {
         return p;
     }
     *native = true;
-    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    cudaError_t e = t_pool ? cudaMallocFromPoolAsync(&p, bytes, t_pool, s) : cudaMallocAsync(&p, bytes, s);
     if (e != cudaSuccess || !p) {
         cudaGetLastError();
         fail(PGB_E_NOMEM, "cudaMallocAsync of " + std::to_string(bytes) + " bytes failed: " +

@@ -79,7 +79,10 @@ void dev_free(void* p, size_t bytes, cudaStream_t s, bool native);
 // Make the calling thread use the CUDA stream-ordered allocator even when
 // hooks are registered (for the library's own threads, which must not call
 // back into the host program).
-void use_native_allocator_in_this_thread();
+// Device memory of this thread's library calls: stream-ordered allocations
+// from `pool` (nullptr: the device's default pool), never the hooks set with
+// pgb_set_allocator.
+void use_native_allocator_in_this_thread(cudaMemPool_t pool = nullptr);
 void live_handles_add(int d);
 
 // Owning device buffer that returns its memory to the library allocator on

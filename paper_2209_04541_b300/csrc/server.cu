@@ -4,8 +4,10 @@
 // The paper runs one computation at a time (Section 4.1); this file is the
 // serving side of the same block-tuple path.  A job is a raw edge list.
 //   submit   copies the edges into the job (the caller's arrays are only
-//            borrowed for the call) and queues it; a job that can never fit
-//            the budget is refused with PGB_E_BUDGET.
+//            borrowed for the call) and queues it: host arrays into host
+//            memory, device arrays into a device buffer that the job keeps
+//            until its batch copies it; a job that can never fit the budget
+//            is refused with PGB_E_BUDGET.
 //   batch    each of the server's batch threads takes the queued jobs that
 //            fit the budget (in arrival order, up to max_batch_jobs and
 //            batch_edges raw edges) and counts them as ONE graph: the
@@ -87,12 +89,28 @@ struct Job {
     uint64_t m = 0;
     uint64_t est = 0;  // admitted device bytes
     std::vector<uint32_t> src, dst;
+    // device input (src then dst, 8 bytes per raw edge), until the batch
+    // copies it; allocated and freed stream-ordered
+    void* dmem = nullptr;
+    // borrowed device input (pgb_server_submit_borrowed): the caller's arrays
+    const uint32_t* bsrc = nullptr;
+    const uint32_t* bdst = nullptr;
     Clock::time_point submitted, finished;
     // results
     uint64_t total = 0;
     std::vector<uint64_t> per_vertex;
     bool cancel = false;
     std::shared_ptr<struct BatchState> batch;  // while RUNNING: the batch it is in
+
+    void drop_input(cudaStream_t s) {
+        src.clear();
+        src.shrink_to_fit();
+        dst.clear();
+        dst.shrink_to_fit();
+        if (dmem) cudaFreeAsync(dmem, s);
+        dmem = nullptr;
+    }
+    ~Job() { drop_input(cudaStreamLegacy); }
 };
 
 // A batch on the device: its thread's cancel token and how many of its jobs
@@ -145,6 +163,11 @@ struct pgb_server {
     std::vector<std::thread> threads;
     std::vector<cudaStream_t> streams;  // one per batch thread, for the server's lifetime
     std::vector<pgb_cancel*> tokens;    // one per batch thread: stops its batch's kernels
+    // the server's own stream-ordered memory pool: batches and queued device
+    // inputs allocate from it, and memory freed there stays mapped for the
+    // next batch until the server is destroyed (the device's default pool
+    // gives freed memory back at every synchronisation)
+    cudaMemPool_t pool = nullptr;
 };
 
 namespace pgb {
@@ -162,10 +185,7 @@ static void finish(pgb_server* S, const std::shared_ptr<Job>& J, int state, int 
     J->err = err;
     J->msg = msg;
     J->finished = Clock::now();
-    J->src.clear();
-    J->src.shrink_to_fit();
-    J->dst.clear();
-    J->dst.shrink_to_fit();
+    J->drop_input(cudaStreamLegacy);
     S->bytes_in_use -= J->est;
     if (state == PGB_JOB_DONE) ++S->n_done;
     else if (state == PGB_JOB_CANCELLED) ++S->n_cancelled;
@@ -196,10 +216,21 @@ static void count_batch(pgb_server* S, const std::vector<std::shared_ptr<Job>>& 
     {
         DevBuf<uint32_t> ds(M, s), dd(M, s);
         for (uint32_t j = 0; j < nj; ++j) {
-            const Job& J = *batch[j];
+            Job& J = *batch[j];
             if (!J.m) continue;
-            PGB_CUDA(cudaMemcpyAsync(ds.ptr + eoff[j], J.src.data(), J.m * 4, cudaMemcpyHostToDevice, s));
-            PGB_CUDA(cudaMemcpyAsync(dd.ptr + eoff[j], J.dst.data(), J.m * 4, cudaMemcpyHostToDevice, s));
+            if (J.bsrc) {
+                PGB_CUDA(cudaMemcpyAsync(ds.ptr + eoff[j], J.bsrc, J.m * 4, cudaMemcpyDeviceToDevice, s));
+                PGB_CUDA(cudaMemcpyAsync(dd.ptr + eoff[j], J.bdst, J.m * 4, cudaMemcpyDeviceToDevice, s));
+            } else if (J.dmem) {
+                const uint32_t* in = static_cast<const uint32_t*>(J.dmem);
+                PGB_CUDA(cudaMemcpyAsync(ds.ptr + eoff[j], in, J.m * 4, cudaMemcpyDeviceToDevice, s));
+                PGB_CUDA(cudaMemcpyAsync(dd.ptr + eoff[j], in + J.m, J.m * 4, cudaMemcpyDeviceToDevice, s));
+                PGB_CUDA(cudaFreeAsync(J.dmem, s));
+                J.dmem = nullptr;
+            } else {
+                PGB_CUDA(cudaMemcpyAsync(ds.ptr + eoff[j], J.src.data(), J.m * 4, cudaMemcpyHostToDevice, s));
+                PGB_CUDA(cudaMemcpyAsync(dd.ptr + eoff[j], J.dst.data(), J.m * 4, cudaMemcpyHostToDevice, s));
+            }
         }
         if (M) {
             k_union_ids<<<(unsigned)std::min<uint64_t>((M + 255) / 256, 148ull * 32), 256, 0, s>>>(
@@ -253,7 +284,7 @@ static void count_batch(pgb_server* S, const std::vector<std::shared_ptr<Job>>& 
 
 static void batch_loop(pgb_server* S, int idx) {
     cudaSetDevice(S->device);
-    use_native_allocator_in_this_thread();
+    use_native_allocator_in_this_thread(S->pool);
     const cudaStream_t s = S->streams[idx];
     const bool serial = S->o.mode == PGB_SERVE_SERIAL;
     const uint32_t cap = serial ? 1 : (S->o.max_batch_jobs ? S->o.max_batch_jobs : 256);
@@ -343,7 +374,21 @@ int pgb_server_create(const pgb_server_opts* opts, pgb_server** out) {
         auto release = [&] {
             for (cudaStream_t x : S->streams) cudaStreamDestroy(x);
             for (pgb_cancel* c : S->tokens) pgb_cancel_free(c);
+            if (S->pool) cudaMemPoolDestroy(S->pool);
         };
+        {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = S->device;
+            PGB_CUDA(cudaMemPoolCreate(&S->pool, &props));
+            uint64_t keep = ~0ull;
+            cudaError_t e = cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) {
+                release();
+                fail(PGB_E_CUDA, std::string("cudaMemPoolSetAttribute: ") + cudaGetErrorString(e));
+            }
+        }
         for (int i = 0; i < nthreads; ++i) {
             cudaStream_t st = nullptr;
             cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -366,39 +411,63 @@ int pgb_server_create(const pgb_server_opts* opts, pgb_server** out) {
     });
 }
 
+// A new job of m raw edges on n vertices, checked against the budget.
+static std::shared_ptr<Job> new_job(pgb_server* S, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n,
+                                    uint64_t* job_id) {
+    if (!S || !job_id) fail(PGB_E_INVAL, "NULL argument");
+    if (m > 0 && (!src || !dst)) fail(PGB_E_INVAL, "src/dst NULL with m > 0");
+    if (m > 0 && n == 0) fail(PGB_E_INVAL, "edges given for an empty vertex set");
+    auto J = std::make_shared<Job>();
+    J->n = n;
+    J->m = m;
+    J->est = job_bytes(m, n);
+    if (J->est > S->o.budget_bytes)
+        fail(PGB_E_BUDGET, "job needs about " + std::to_string(J->est) + " device bytes; budget is " +
+                               std::to_string(S->o.budget_bytes));
+    return J;
+}
+
+static void enqueue(pgb_server* S, const std::shared_ptr<Job>& J, uint64_t* job_id) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) fail(PGB_E_STATE, "server is shutting down");
+    J->id = S->next_id++;
+    J->submitted = Clock::now();
+    S->jobs[J->id] = J;
+    S->queued.push_back(J);
+    S->cv_queue.notify_all();
+    *job_id = J->id;
+}
+
 int pgb_server_submit(pgb_server* S, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, int mem,
                       uint64_t* job_id) {
     return guard([&] {
-        if (!S || !job_id) fail(PGB_E_INVAL, "NULL argument");
-        if (m > 0 && (!src || !dst)) fail(PGB_E_INVAL, "src/dst NULL with m > 0");
         if (mem != PGB_MEM_HOST && mem != PGB_MEM_DEVICE) fail(PGB_E_INVAL, "bad mem kind");
-        if (m > 0 && n == 0) fail(PGB_E_INVAL, "edges given for an empty vertex set");
-        auto J = std::make_shared<Job>();
-        J->n = n;
-        J->m = m;
-        J->est = job_bytes(m, n);
-        if (J->est > S->o.budget_bytes)
-            fail(PGB_E_BUDGET, "job needs about " + std::to_string(J->est) + " device bytes; budget is " +
-                                   std::to_string(S->o.budget_bytes));
+        auto J = new_job(S, src, dst, m, n, job_id);
         if (m) {
             if (mem == PGB_MEM_HOST) {
                 J->src.assign(src, src + m);
                 J->dst.assign(dst, dst + m);
             } else {
-                J->src.resize(m);
-                J->dst.resize(m);
-                PGB_CUDA(cudaMemcpy(J->src.data(), src, m * 4, cudaMemcpyDeviceToHost));
-                PGB_CUDA(cudaMemcpy(J->dst.data(), dst, m * 4, cudaMemcpyDeviceToHost));
+                // on the legacy default stream: after the work the caller
+                // queued there (and on other blocking streams)
+                PGB_CUDA(cudaMallocFromPoolAsync(&J->dmem, m * 8, S->pool, cudaStreamLegacy));
+                uint32_t* in = static_cast<uint32_t*>(J->dmem);
+                PGB_CUDA(cudaMemcpyAsync(in, src, m * 4, cudaMemcpyDeviceToDevice, cudaStreamLegacy));
+                PGB_CUDA(cudaMemcpyAsync(in + m, dst, m * 4, cudaMemcpyDeviceToDevice, cudaStreamLegacy));
+                PGB_CUDA(cudaStreamSynchronize(cudaStreamLegacy));
             }
         }
-        std::lock_guard<std::mutex> lk(S->mu);
-        if (S->stop) fail(PGB_E_STATE, "server is shutting down");
-        J->id = S->next_id++;
-        J->submitted = Clock::now();
-        S->jobs[J->id] = J;
-        S->queued.push_back(J);
-        S->cv_queue.notify_all();
-        *job_id = J->id;
+        enqueue(S, J, job_id);
+    });
+}
+
+int pgb_server_submit_borrowed(pgb_server* S, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n,
+                               uint64_t* job_id) {
+    return guard([&] {
+        auto J = new_job(S, src, dst, m, n, job_id);
+        J->bsrc = m ? src : nullptr;
+        J->bdst = m ? dst : nullptr;
+        enqueue(S, J, job_id);
     });
 }
 
@@ -469,8 +538,7 @@ int pgb_server_cancel(pgb_server* S, uint64_t job_id) {
             J->state = PGB_JOB_CANCELLED;
             J->err = PGB_E_CANCELLED;
             J->finished = Clock::now();
-            J->src.clear();
-            J->dst.clear();
+            J->drop_input(cudaStreamLegacy);
             ++S->n_cancelled;
             S->cv_done.notify_all();
         }
@@ -504,6 +572,7 @@ void pgb_server_destroy(pgb_server* S) {
         for (auto& J : S->queued) {
             J->state = PGB_JOB_CANCELLED;
             J->err = PGB_E_CANCELLED;
+            J->drop_input(cudaStreamLegacy);
         }
         S->queued.clear();
         // batches on the device stop at their next check
@@ -518,6 +587,10 @@ void pgb_server_destroy(pgb_server* S) {
         cudaStreamDestroy(st);
     }
     for (pgb_cancel* c : S->tokens) pgb_cancel_free(c);
+    // every allocation from the pool has been freed (stream-ordered) by now;
+    // its memory goes back once those frees complete
+    cudaStreamSynchronize(cudaStreamLegacy);
+    cudaMemPoolDestroy(S->pool);
     delete S;
     live_handles_add(-1);
 }

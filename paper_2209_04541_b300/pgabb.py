@@ -141,6 +141,8 @@ _SIGS = {
     "pgb_server_create": (ctypes.c_int, [_VP, ctypes.POINTER(_VP)]),
     "pgb_server_submit": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "pgb_server_submit_borrowed": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_uint64, ctypes.c_uint32,
+                                                  ctypes.POINTER(ctypes.c_uint64)]),
     "pgb_server_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
     "pgb_server_pause": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pgb_server_wait": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64), _VP,
@@ -742,6 +744,11 @@ class Server(_Handle):
         super().__init__(ptr, None)
         self.per_vertex = per_vertex
         self.n_of = {}
+        self.borrowed = {}  # job -> the device tensors it reads, kept alive until wait returns
+
+    def free(self):
+        super().free()
+        self.borrowed.clear()
 
 
 def pgb_server_opts_default(**kw) -> ServerOpts:
@@ -765,16 +772,31 @@ def pgb_server_create(opts: ServerOpts | None = None) -> Server:
     return Server(out.value, bool(opts.per_vertex))
 
 
-def pgb_server_submit(srv: Server, src, dst, n: int) -> int:
+def pgb_server_submit(srv: Server, src, dst, n: int, borrow: bool = False) -> int:
+    """Queue a job.  ``borrow`` (CUDA tensors only, fully written): the server
+    reads the tensors in place when the job's batch starts instead of copying
+    them at submit; the binding keeps them alive until the job is waited for."""
     ps, ms, ks = _arr(src, np.uint32)
     pd, md, kd = _arr(dst, np.uint32)
     if ms != md:
         raise ValueError("src and dst must live in the same memory")
     m = 0 if ks is None else int(ks.numel() if hasattr(ks, "numel") else ks.size)
     jid = ctypes.c_uint64()
-    _check(load().pgb_server_submit(srv, ps, pd, m, n, ms, ctypes.byref(jid)), "pgb_server_submit")
+    if borrow:
+        if ms != PGB_MEM_DEVICE and m:
+            raise ValueError("borrow needs CUDA tensors")
+        _check(load().pgb_server_submit_borrowed(srv, ps, pd, m, n, ctypes.byref(jid)),
+               "pgb_server_submit_borrowed")
+        srv.borrowed[int(jid.value)] = (ks, kd)
+    else:
+        _check(load().pgb_server_submit(srv, ps, pd, m, n, ms, ctypes.byref(jid)), "pgb_server_submit")
     srv.n_of[int(jid.value)] = n
     return int(jid.value)
+
+
+def pgb_server_submit_borrowed(srv: Server, src, dst, n: int) -> int:
+    """Queue a job on CUDA tensors the server borrows (see pgb_server_submit)."""
+    return pgb_server_submit(srv, src, dst, n, borrow=True)
 
 
 def pgb_server_pause(srv: Server, paused: bool = True):
@@ -799,6 +821,7 @@ def pgb_server_wait(srv: Server, job: int, timeout_s: float = -1.0, per_vertex: 
     rc = load().pgb_server_wait(srv, job, timeout_s, ctypes.byref(tot), ptr, ctypes.byref(lat))
     if rc != PGB_E_TIMEOUT:
         srv.n_of.pop(job, None)
+        srv.borrowed.pop(job, None)
     _check(rc, "pgb_server_wait")
     return int(tot.value), pv, float(lat.value)
 

@@ -14,7 +14,11 @@ Nothing here touches the CUDA library.
 
     python tests/golden/make_golden.py rmat20 rmat24 grid4096 rmat27
 
-writes ``tests/golden/full_<name>.txt``.
+writes ``tests/golden/full_<name>.txt``.  ``serve22`` writes
+``tests/golden/full_serve22_sample.txt``: for a sample of the serving workload at
+scales up to 22 (``graphgen.serve_spec``; the largest job of each family
+plus seeded random jobs) each job's T and the SHA-256 of its per-vertex
+counts, by the same oracle count.
 """
 import hashlib
 import os
@@ -121,6 +125,72 @@ def load(name):
     return out
 
 
+SERVE_MAX_SCALE = 22
+SERVE_JOBS = 10000
+SERVE_RANDOM = 9
+
+
+def serve_sample():
+    """Job indices of the serving sample: the largest job of each family (by
+    raw edges; RGG by n) among the first SERVE_JOBS, then seeded random ones."""
+    specs = [graphgen.serve_spec(i, SERVE_MAX_SCALE) for i in range(SERVE_JOBS)]
+
+    def size(sp):
+        return sp[2] << sp[1] if sp[0] == "rmat" else (sp[2] if sp[0] == "er" else sp[1])
+
+    big = [max((i for i, sp in enumerate(specs) if sp[0] == fam), key=lambda i: size(specs[i]))
+           for fam in ("rmat", "er", "rgg")]
+    rand = np.random.default_rng(2028).choice(SERVE_JOBS, size=SERVE_RANDOM, replace=False).tolist()
+    return sorted(set(big + rand))
+
+
+def make_serve():
+    path = os.path.join(HERE, "full_serve22_sample.txt")
+    lines = []
+    for i in serve_sample():
+        t0 = time.time()
+        sp = graphgen.serve_spec(i, SERVE_MAX_SCALE)
+        src, dst, n = graphgen.serve_job(i, SERVE_MAX_SCALE)
+        raw = len(src)
+        g = oracle.clean(src, dst, n)
+        del src, dst
+        m = g.m
+        o = oracle.orient(g)
+        del g
+        T, t = oracle.tc_forward_mt(o, per_vertex=True)
+        del o
+        assert int(t.sum(dtype=np.uint64)) == 3 * T
+        lines.append(f"job {i} {' '.join(map(str, sp))} n {n} raw {raw} m {m} T {T} t_sha256 {digest(t)}\n")
+        print(lines[-1].strip(), f"({time.time() - t0:.0f} s)", flush=True)
+    with open(path, "w") as f:
+        f.write(f"# Sample of the serving workload at scales up to {SERVE_MAX_SCALE} (graphgen.serve_spec /\n")
+        f.write("# graphgen.serve_job, job i seeded by i): the largest R-MAT, ER and RGG job among the first\n")
+        f.write(f"# {SERVE_JOBS} plus {SERVE_RANDOM} seeded random jobs.  Values from the oracle only\n")
+        f.write("# (tests/golden/make_golden.py serve22): T = oracle forward count of the cleaned graph;\n")
+        f.write("# t_sha256 = SHA-256 of its n per-vertex counts (uint64 little-endian, original IDs).\n")
+        for line in lines:
+            f.write(line)
+    print(f"-> {path}")
+
+
+def load_serve():
+    """[(job, spec tuple, n, raw, m, T, t_sha256)] from full_serve22_sample.txt."""
+    out = []
+    with open(os.path.join(HERE, "full_serve22_sample.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            w = line.split()
+            k = w.index("n")
+            spec = tuple([w[2]] + [int(x) for x in w[3:k]])
+            kv = dict(zip(w[k::2], w[k + 1::2]))
+            out.append((int(w[1]), spec, int(kv["n"]), int(kv["raw"]), int(kv["m"]), int(kv["T"]), kv["t_sha256"]))
+    return out
+
+
 if __name__ == "__main__":
     for name in sys.argv[1:] or ["rmat20"]:
-        make(name)
+        if name == "serve22":
+            make_serve()
+        else:
+            make(name)

@@ -205,3 +205,117 @@ def test_serve_benchmark_mix_sample_matches_oracle():
     assert stats["batches"] < len(jobs)
     for (T, t), (gT, gt, _) in zip(want, res):
         assert gT == T and np.array_equal(gt, t)
+
+
+def test_serve_device_inputs_match_host_inputs():
+    """Jobs submitted as device arrays (copied and held on the device while
+    queued, or borrowed in place) give the counts of the same jobs submitted
+    from host memory, in both modes."""
+    jobs = job_mix(5)
+    want = expected(jobs)
+    for mode in (P.PGB_SERVE_BATCHED, P.PGB_SERVE_SERIAL):
+        srv = P.pgb_server_create(P.pgb_server_opts_default(mode=mode, max_inflight=2))
+        try:
+            ids = []
+            for k, (s, d, n) in enumerate(jobs):
+                if k % 3:  # two of three jobs from device memory: copied, then borrowed
+                    s = torch.from_numpy(np.ascontiguousarray(s)).cuda()
+                    d = torch.from_numpy(np.ascontiguousarray(d)).cuda()
+                    torch.cuda.synchronize()
+                ids.append(P.pgb_server_submit(srv, s, d, n, borrow=k % 3 == 2))
+                del s, d
+            torch.cuda.synchronize()
+            res = [P.pgb_server_wait(srv, j, 120.0, per_vertex=True) for j in ids]
+        finally:
+            P.pgb_server_destroy(srv)
+        for (T, t), (gT, gt, _) in zip(want, res):
+            assert gT == T and np.array_equal(gt, t)
+
+
+def test_serve_device_inputs_cancel_and_destroy_while_queued():
+    """Queued device jobs can be cancelled, and a server destroyed with device
+    jobs still queued releases them; the next server counts normally."""
+    g = graphgen.rmat(10, 16, 4)
+    T = oracle.tc_node_iterator(oracle.clean(*g), False)[0]
+    ds, dd = torch.from_numpy(g[0]).cuda(), torch.from_numpy(g[1]).cuda()
+    srv = P.pgb_server_create(P.pgb_server_opts_default())
+    try:
+        P.pgb_server_pause(srv, True)
+        ids = [P.pgb_server_submit(srv, ds, dd, g[2]) for _ in range(4)]
+        P.pgb_server_cancel(srv, ids[1])
+        with pytest.raises(P.PgbError) as ei:
+            P.pgb_server_wait(srv, ids[1], 10.0)
+        assert ei.value.code == P.PGB_E_CANCELLED
+        P.pgb_server_pause(srv, False)
+        assert P.pgb_server_wait(srv, ids[0], 60.0)[0] == T
+    finally:
+        P.pgb_server_destroy(srv)  # ids[2], ids[3] may still be queued
+    srv = P.pgb_server_create(P.pgb_server_opts_default())
+    try:
+        assert P.pgb_server_wait(srv, P.pgb_server_submit(srv, ds, dd, g[2]), 60.0)[0] == T
+        # borrowed inputs: a cancelled queued job, then a destroy with jobs queued
+        P.pgb_server_pause(srv, True)
+        ids = [P.pgb_server_submit(srv, ds, dd, g[2], borrow=True) for _ in range(3)]
+        assert len(srv.borrowed) == 3
+        P.pgb_server_cancel(srv, ids[0])
+        with pytest.raises(P.PgbError):
+            P.pgb_server_wait(srv, ids[0], 10.0)
+        assert len(srv.borrowed) == 2
+        P.pgb_server_pause(srv, False)
+        assert P.pgb_server_wait(srv, ids[1], 60.0)[0] == T
+    finally:
+        P.pgb_server_destroy(srv)
+    assert not srv.borrowed
+
+
+def test_serve_full_size_mix_sample_matches_oracle_goldens():
+    """A sample of the serving workload at its stated size (scales up to 22:
+    the largest R-MAT, ER and RGG job of the first 10,000 plus seeded random
+    jobs), generated on the device and submitted from device memory as the
+    full-size bench does, counted in batched mixes: each job's total and
+    per-vertex counts equal the oracle's stored values."""
+    import hashlib
+    import os
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_golden
+    from graphgen import device as gd
+
+    sample = make_golden.load_serve()
+    assert len(sample) >= 12
+    srv = P.pgb_server_create(P.pgb_server_opts_default(mode=P.PGB_SERVE_BATCHED, max_inflight=2))
+    try:
+        ids = []
+        for job, spec, n, raw, m, T, sha in sample:
+            assert graphgen.serve_spec(job, 22) == spec
+            s, d, gn = gd.serve_job(job, 22)
+            assert gn == n and s.numel() == raw
+            torch.cuda.synchronize()
+            ids.append(P.pgb_server_submit(srv, s, d, n, borrow=len(ids) % 2 == 1))
+            del s, d
+        for (job, spec, n, raw, m, T, sha), j in zip(sample, ids):
+            gT, gt, _ = P.pgb_server_wait(srv, j, 600.0, per_vertex=True)
+            assert gT == T, (job, spec)
+            assert hashlib.sha256(np.ascontiguousarray(gt, dtype="<u8").tobytes()).hexdigest() == sha, (job, spec)
+    finally:
+        P.pgb_server_destroy(srv)
+    torch.cuda.empty_cache()
+
+
+def test_bench_device_serve_client_matches_oracle():
+    """bench.py's full-size serve client (device generation, windowed closed
+    loop and timed arrivals) on a small mix: every total equals the oracle's
+    on the host-generated job, in both modes."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    count, scale = 40, 12
+    want = [oracle.tc_node_iterator(oracle.clean(*graphgen.serve_job(i, scale)), False)[0] for i in range(count)]
+    for mode in (P.PGB_SERVE_SERIAL, P.PGB_SERVE_BATCHED):
+        tot, lat, span, st, raw, client = bench.run_serve_device(count, scale, mode, window_edges=1 << 20)
+        assert tot == want and span > 0 and all(x > 0 for x in lat)
+    arrivals = np.cumsum(np.full(count, 0.002))
+    tot, *_ = bench.run_serve_device(count, scale, P.PGB_SERVE_BATCHED, arrivals)
+    assert tot == want

@@ -328,6 +328,47 @@ def test_splitmix_published_sequence():
         6457827717110365317, 3203168211198807973, 9817491932198370423]
 
 
+@pytest.mark.parametrize("bits", [1, 2, 3, 7, 10, 13])
+def test_feistel_relabelling_is_a_bijection(bits):
+    for seed in (1, 2, 99):
+        lab = [graphgen.feistel_label(x, bits, seed) for x in range(1 << bits)]
+        assert sorted(lab) == list(range(1 << bits))
+    if bits >= 7:  # a seeded shuffle, not the identity, and seed-dependent
+        assert lab != list(range(1 << bits))
+        assert lab != [graphgen.feistel_label(x, bits, 1) for x in range(1 << bits)]
+
+
+def test_rmat_relabellings_compose_with_the_unrelabelled_graph():
+    """Relabelled R-MAT = the unrelabelled edges mapped through the stated
+    bijection (Fisher-Yates permutation or Feistel labels), edge by edge."""
+    scale, ef, seed = 11, 8, 6
+    s0, d0, n = graphgen.rmat(scale, ef, seed, relabel="none")
+    perm = graphgen.shuffle_permutation(n, seed)
+    assert sorted(perm.tolist()) == list(range(n))
+    s1, d1, _ = graphgen.rmat(scale, ef, seed, relabel="shuffle")
+    assert np.array_equal(s1, perm[s0]) and np.array_equal(d1, perm[d0])
+    assert np.array_equal(s1, graphgen.rmat(scale, ef, seed)[0])  # the default relabelling
+    lab = np.array([graphgen.feistel_label(x, scale, seed) for x in range(n)], np.uint32)
+    s2, d2, _ = graphgen.rmat(scale, ef, seed, relabel="feistel")
+    assert np.array_equal(s2, lab[s0]) and np.array_equal(d2, lab[d0])
+
+
+def test_serving_mix_spec():
+    """The serving workload's job parameters: families in thirds, stated
+    ranges, deterministic per job index."""
+    specs = [graphgen.serve_spec(i, 22) for i in range(3000)]
+    assert specs == [graphgen.serve_spec(i, 22) for i in range(3000)]
+    assert all(sp[0] == ("rmat", "er", "rgg")[i % 3] for i, sp in enumerate(specs))
+    rm = [sp for sp in specs if sp[0] == "rmat"]
+    assert {sp[1] for sp in rm} == set(range(10, 23)) and {sp[2] for sp in rm} == set(range(8, 33))
+    er = [sp for sp in specs if sp[0] == "er"]
+    assert all(1 << 10 <= sp[1] <= 1 << 22 and 2 * sp[1] <= 2 * sp[2] + 2 <= 64 * sp[1] + 2 for sp in er)
+    assert all(1 << 10 <= sp[1] <= 1 << 22 for sp in specs if sp[0] == "rgg")
+    fam, scale, ef = graphgen.serve_spec(0, 12)
+    src, dst, n = graphgen.serve_job(0, 12)
+    assert fam == "rmat" and n == 1 << scale and len(src) == ef << scale
+
+
 def test_generators_deterministic_and_shaped():
     a = graphgen.rmat(12, 16, 4)
     b = graphgen.rmat(12, 16, 4)
