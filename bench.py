@@ -122,6 +122,19 @@ def measured_peaks():
         return 6400.0, "of fallback"
 
 
+def measured_tensor_peak():
+    """Dense bf16 tensor throughput measured on the B300s, sustained
+    (the dense block runs inside a long step), in TFLOP/s; fp16 runs at the
+    same nominal rate.  Fallback: the recipe's sustained figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained"]), "of measured (bf16 sustained; fp16 same nominal rate)"
+    except Exception:
+        return 1400.0, "of fallback (bf16 sustained)"
+
+
 KERNEL_SOURCE = {"k_tc_hash": "tc_hash.cu", "k_tc_persistent": "tc.cu", "k_tc_tuple": "tc.cu"}
 
 
@@ -836,6 +849,8 @@ def main(argv=None):
     ap.add_argument("--hash-threads", type=int, default=0, choices=[0, 128, 256, 512],
                     help="CTA shape of the hash kernel (0 = autotuned)")
     ap.add_argument("--p", type=int, default=0, help="override the workload's p")
+    ap.add_argument("--dense-core", type=int, default=0,
+                    help="dense top block of the degree order: 0 autotuned, -1 none, K > 0 that many ranks")
     ap.add_argument("--hash-min-lookups", type=int, default=0,
                     help="per-part autotuner threshold, lookups per edge (0 = the library's 32)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -901,8 +916,10 @@ def main(argv=None):
                "hash": P.PGB_VAR_HASH}[args.variant]
     opts = P.pgb_tc_opts_default(mode=mode, per_vertex=args.per_vertex, chunk_edges=args.chunk, variant=variant,
                                  hash_threads=args.hash_threads, hash_min_lookups=args.hash_min_lookups,
+                                 dense_core=args.dense_core,
                                  order=P.PGB_ORDER_WEIGHT if args.order == "weight" else P.PGB_ORDER_LOCALITY)
     info = {}
+    dense_ms = []
 
     def step():
         g = P.pgb_graph_from_edges(ds, dd, n, stream)
@@ -911,7 +928,10 @@ def main(argv=None):
         r = P.pgb_tc_run(b, opts, stream)
         T, _ = P.pgb_tc_result_get(r, per_vertex=tv if args.per_vertex else None)
         kms = P.pgb_tc_result_kernel_ms(r)
+        dc = P.pgb_tc_result_dense_core(r)
+        dense_ms.append(dc["ms"] if dc["ranks"] else 0.0)
         if not info:
+            info["dense"] = dc
             info.update(P.pgb_blocks_info(b))
             info["variant_used"] = P.pgb_tc_result_variant(r)
             pv_ = P.pgb_tc_result_part_variants(r)
@@ -937,6 +957,7 @@ def main(argv=None):
     l0 = P.pgb_kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kms_all = []
+    dense_ms.clear()
     e0.record(stream)
     for _ in range(args.steps):
         T2, kms = step()
@@ -966,20 +987,35 @@ def main(argv=None):
         kname = "k_tc_hash"
     else:
         kname = "k_tc_persistent"
+    dense = info["dense"]
+    dense_mean = statistics.mean(dense_ms) if dense["ranks"] else 0.0
+    # the intersection kernels' own time: the count phase less the dense block's
+    sparse_ms = kernel_ms - dense_mean
     ew_achieved = info["alg_bytes"] / (kernel_ms / 1e3) / 1e9
     if kname == "k_tc_hash":
         # bytes this kernel must stream: every looked-up entry of the tails'
-        # rows (4 per probe), one 8-byte in-edge descriptor per edge, and
-        # each head's list (4 per edge)
-        kb = 4 * info["probes"] + 12 * info["m"]
-        bytes_rule = "4 probes + 12|E+| (looked-up tail-row entries, in-edge index, head lists)"
+        # rows (4 per probe; less the lookups left to the dense block), one
+        # 8-byte in-edge descriptor per edge, and each head's list (4 per edge)
+        kb = 4 * (info["probes"] - dense["lookups_skipped"]) + 12 * info["m"]
+        bytes_rule = "4 (probes - dense-block lookups) + 12|E+| (looked-up tail-row entries, in-edge index, head lists)"
     else:
         kb = info["alg_bytes"]
         bytes_rule = "4|E+| + 4 sum_v indeg(v) outdeg(v) + 8(n+1)"
-    achieved = kb / (kernel_ms / 1e3) / 1e9
+    achieved = kb / (sparse_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_note, "alg_bytes": kb, "alg_bytes_rule": bytes_rule,
-                "kernel_ms": kernel_ms, "traffic": kernel_traffic(kname, args.workload)}
+                "kernel_ms": sparse_ms, "count_phase_ms": kernel_ms,
+                "traffic": kernel_traffic(kname, args.workload) if not dense["ranks"] else None}
+    if dense["ranks"]:
+        tf_peak = measured_tensor_peak()
+        tflops = dense["gemm_flop"] / (dense_mean / 1e3) / 1e12
+        roofline["dense_block"] = {
+            "bound": "tensor", "ranks": dense["ranks"], "triangles": dense["triangles"],
+            "lookups_taken_from_kernels": dense["lookups_skipped"], "ms": dense_mean,
+            "achieved": tflops, "unit": "TFLOP/s", "peak": tf_peak[0], "peak_source": tf_peak[1],
+            "frac": tflops / tf_peak[0] if tf_peak[0] else None,
+            "note": "fp16 0/1 GEMM strips of the top block (fp16 rate = bf16 rate), fill and masked reduction "
+                    "inside the timed ms"}
     if kname == "k_tc_hash":
         roofline["edgewise_bound"] = {
             "note": "4|E+| + 4 sum_v indeg(v) outdeg(v) + 8(n+1): the edge-wise method's bytes, which re-read "

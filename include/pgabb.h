@@ -120,7 +120,15 @@ extern "C" {
  * chosen per work item from its rank range, list length and in-degree.
  * PGB_VAR_MIXED is a result value only (pgb_tc_result_variant), and so is
  * PGB_VAR_HOST (pgb_tc_result_part_variants: a part the HYBRID host kernel
- * counted). */
+ * counted).
+ * Dense top block (pgb_tc_opts.dense_core): the K highest ranks of the degree
+ * order, where the hubs sit, form a dense diagonal block.  Its triangles
+ * (all three vertices among those ranks) are counted from its 0/1 adjacency
+ * A as sum_y A[x][y] (A A)[x][y] / 2 per vertex, the product a dense fp16
+ * GEMM with fp32 accumulation (exact: integers below 2^24); the intersection
+ * kernels skip the in-edges whose tail is in the block.  The autotuner takes
+ * the K (a multiple of 2048, at most 32,768) whose saved lookups outweigh
+ * the GEMM's time by the most, or none. */
 #define PGB_VAR_AUTO    0
 #define PGB_VAR_BSEARCH 1
 #define PGB_VAR_MERGE   2
@@ -341,7 +349,12 @@ typedef struct {
                               at most 10^6: everything on the host) */
     uint32_t hash_min_lookups; /* AUTO: a head part takes the hash kernel at
                               this many lookups per edge or more (0 = 32) */
-    uint32_t reserved[1];
+    int32_t dense_core;    /* PERSISTENT, resident blocks: the top block of
+                              the degree order counted densely on the tensor
+                              cores (below).  0: autotuned with PGB_VAR_AUTO,
+                              none otherwise; > 0: that many top ranks
+                              (rounded up to a multiple of 256, at most n);
+                              < 0: none.  HYBRID runs use none. */
 } pgb_tc_opts;
 
 void pgb_tc_opts_default(pgb_tc_opts* o);
@@ -362,6 +375,21 @@ int pgb_tc_result_get(pgb_tc_result* r, uint64_t* total, uint64_t* per_vertex, i
 
 /* PLAIN mode with per_triple = 1: counts[t] for queue entry t (T entries). */
 int pgb_tc_result_triples(pgb_tc_result* r, uint64_t* counts, int mem);
+
+/* The dense top block of a run (pgb_tc_opts.dense_core). */
+typedef struct {
+    uint32_t ranks;            /* the block's ranks (0: no block) */
+    uint32_t reserved;
+    uint64_t triangles;        /* triangles with all three vertices in the block */
+    uint64_t lookups_skipped;  /* lookups the intersection kernels left to the block
+                                  (exact when ranks is a multiple of 1024, else 0) */
+    double gemm_flop;          /* floating-point operations of its A·A strips */
+    float ms;                  /* device time of the dense count (-1: graph replay) */
+    float reserved2;
+} pgb_dense_core_info;
+
+/* Synchronises the run's stream.  Errors: PGB_E_INVAL. */
+int pgb_tc_result_dense_core(pgb_tc_result* r, pgb_dense_core_info* out);
 
 /* The variant that ran (PGB_VAR_BSEARCH, PGB_VAR_MERGE, PGB_VAR_HASH, or
  * PGB_VAR_MIXED when the autotuner chose differently for different parts). */

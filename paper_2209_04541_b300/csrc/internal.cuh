@@ -235,6 +235,9 @@ struct pgb_blocks {
     uint64_t probes = 0;  // sum over edges (u, v) of the entries of u's row after v
     std::vector<uint64_t> part_probes;  // p: the same sum over edges whose head v lies in part j
     std::vector<uint64_t> head_off;     // p + 1: first in-edge (index order) of each head part
+    // lookups of the in-edges whose tail has rank in [n - 1024 (i + 1), n - 1024 i), i < 32: what a
+    // dense top block of 1024 (i + 1) ranks would take from the intersection kernels (core.cu)
+    std::vector<uint64_t> core_probes;
     uint32_t max_outdeg = 0;
 };
 

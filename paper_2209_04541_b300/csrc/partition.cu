@@ -17,6 +17,7 @@
 #include <mutex>
 #include <numeric>
 
+#include "core.cuh"
 #include "internal.cuh"
 #include "sort.cuh"
 
@@ -310,9 +311,11 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
     // --- block histogram (per-edge block ids are built on demand, for the
     // runs that walk edges block by block)
     const size_t pp = (size_t)p * p;
-    // p x p histogram, the per-part lookups (p), the head parts' in-edge offsets (p + 1)
-    DevBuf<unsigned long long> hist(pp + 2 * (size_t)p + 1, s);
-    PGB_CUDA(cudaMemsetAsync(hist.ptr, 0, (pp + 2 * (size_t)p + 1) * 8, s));
+    // p x p histogram, the per-part lookups (p), the head parts' in-edge
+    // offsets (p + 1), the lookups per top-rank band (kCoreBands)
+    const size_t nhist = pp + 2 * (size_t)p + 1 + kCoreBands;
+    DevBuf<unsigned long long> hist(nhist, s);
+    PGB_CUDA(cudaMemsetAsync(hist.ptr, 0, nhist * 8, s));
     if (m > 0) {
         size_t smem = (size_t)p * 8 + ((size_t)p + 1) * 4 + (pp <= 4096 ? pp * 4 : 0);
         k_block_ids<<<grid_for(m), 256, smem, s>>>(b->rowidx.ptr, b->col.ptr, m, b->cuts_d.ptr, p, nullptr,
@@ -352,6 +355,8 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
         PGB_CHECK_LAUNCH("k_fill_u32");
     }
 
+    core_band_probes(b, hist.ptr + pp + 2 * (size_t)p + 1, s);
+
     // --- one sync: cuts, histogram, stats to the host
     b->block_edges.assign(pp, 0);
     b->part_probes.assign(p, 0);
@@ -362,6 +367,9 @@ void build_partition(const pgb_graph* g, uint32_t p, int rule, cudaStream_t s, p
     PGB_CUDA(cudaMemcpyAsync(b->part_probes.data(), hist.ptr + pp, (size_t)p * 8, cudaMemcpyDeviceToHost, s));
     b->head_off.assign((size_t)p + 1, 0);
     PGB_CUDA(cudaMemcpyAsync(b->head_off.data(), hist.ptr + pp + p, ((size_t)p + 1) * 8, cudaMemcpyDeviceToHost, s));
+    b->core_probes.assign(kCoreBands, 0);
+    PGB_CUDA(cudaMemcpyAsync(b->core_probes.data(), hist.ptr + pp + 2 * (size_t)p + 1, kCoreBands * 8,
+                             cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaMemcpyAsync(&hw, wsum.ptr, 8, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaMemcpyAsync(&hp, wprobe.ptr, 8, cudaMemcpyDeviceToHost, s));
     PGB_CUDA(cudaMemcpyAsync(&hm, wmax.ptr, 4, cudaMemcpyDeviceToHost, s));

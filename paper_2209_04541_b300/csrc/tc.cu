@@ -19,6 +19,7 @@
 #include <memory>
 
 #include "hybrid.cuh"
+#include "core.cuh"
 #include "internal.cuh"
 #include "tc_hash.cuh"
 
@@ -46,6 +47,10 @@ struct Graph {
     const uint32_t* __restrict__ col;
     const uint32_t* __restrict__ rowptr;
     unsigned long long* __restrict__ tv;  // per-vertex counts, rank space (may be null)
+    // first CSR position of the dense top block's rows: an in-edge whose
+    // tail row starts there or later has all three vertices of its
+    // triangles in the block, which the dense count covers (core.cu)
+    uint32_t core_e0 = 0xFFFFFFFFu;
 };
 
 __device__ __forceinline__ uint32_t edge_at(const Graph& G, uint32_t idx) {
@@ -72,8 +77,8 @@ template <bool PV>
 __device__ __forceinline__ void warp_step(const Graph& G, uint32_t idx, bool valid, uint32_t lo, uint32_t hi,
                                           bool clip, unsigned long long& cnt, uint32_t* s_edge, int lane) {
     uint32_t sb = 0, sl = 0, lb = 0, ll = 0, u = 0, v = 0;
-    if (valid) {
-        const uint32_t e = edge_at(G, idx);
+    const uint32_t e = valid ? edge_at(G, idx) : 0u;
+    if (valid && e < G.core_e0) {
         u = __ldg(G.rowidx + e);
         v = __ldg(G.col + e);
         uint32_t xb = e + 1, xe = __ldg(G.rowptr + u + 1);
@@ -148,8 +153,8 @@ template <bool PV>
 __device__ __forceinline__ void warp_step_merge(const Graph& G, uint32_t idx, bool valid, uint32_t lo, uint32_t hi,
                                                 bool clip, unsigned long long& cnt, int lane) {
     uint32_t xb = 0, xe = 0, yb = 0, ye = 0, u = 0, v = 0;
-    if (valid) {
-        const uint32_t e = edge_at(G, idx);
+    const uint32_t e = valid ? edge_at(G, idx) : 0u;
+    if (valid && e < G.core_e0) {
         u = __ldg(G.rowidx + e);
         v = __ldg(G.col + e);
         xb = e + 1;
@@ -379,6 +384,11 @@ struct pgb_tc_result {
     uint64_t streamed = 0;          // host-to-device bytes of a streamed run
     uint32_t chunks = 0;            // stream chunks (or pieces) of a streamed run (0 = resident)
     uint32_t slice_loads = 0;       // column slices copied in (column-streamed runs)
+    uint32_t core_ranks = 0;        // ranks of the dense top block (0: none)
+    pgb::DevBuf<unsigned long long> core_total;  // its triangles
+    uint64_t core_lookups = 0;      // lookups it took off the intersection kernels
+    double core_flop = 0;
+    cudaEvent_t evc0 = nullptr, evc1 = nullptr;  // around its count (runs not replayed from a graph)
     pgb::DevBuf<unsigned long long> total;
     pgb::DevBuf<unsigned long long> tv_orig;
     pgb::DevBuf<unsigned long long> triple_counts;
@@ -392,6 +402,8 @@ struct pgb_tc_result {
     ~pgb_tc_result() {
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        if (evc0) cudaEventDestroy(evc0);
+        if (evc1) cudaEventDestroy(evc1);
     }
 };
 
@@ -515,13 +527,16 @@ struct RunPlan {
     // graph replay: the captured kernels read this plan-owned control block,
     // which each replay refills with the run's stop word
     DevBuf<RunCtl> ctl;
+    // dense top block (core.cu): its plan, and its total in partials[core_slot]
+    CorePlan core;
+    uint64_t core_slot = 0;
     cudaGraphExec_t exec = nullptr;
     uint64_t graph_launches = 0;  // kernel launches one replay makes
     cudaEvent_t done = nullptr;   // the last replay's outputs have been copied out
     bool used = false;
 
-    bool same(const pgb_tc_opts& o, int var, const std::vector<uint8_t>& kinds) const {
-        return mode == o.mode && variant == var && part_kind == kinds && order == o.order &&
+    bool same(const pgb_tc_opts& o, int var, const std::vector<uint8_t>& kinds, uint32_t core_k) const {
+        return mode == o.mode && variant == var && part_kind == kinds && order == o.order && core.K == core_k &&
                per_vertex == (o.per_vertex != 0) &&
                per_triple == (o.mode == PGB_MODE_PLAIN && o.per_triple != 0) && chunk_edges == o.chunk_edges &&
                hash_threads_opt == o.hash_threads;
@@ -536,7 +551,7 @@ struct RunPlan {
 };
 
 static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& o, int variant,
-                                        const std::vector<uint8_t>& part_kind, cudaStream_t s) {
+                                        const std::vector<uint8_t>& part_kind, uint32_t core_k, cudaStream_t s) {
     std::unique_ptr<RunPlan> P(new RunPlan());
     P->part_kind = part_kind;
     bool all_hash = true, any_host = false;
@@ -688,6 +703,17 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
         P->partials.alloc(P->npartials, s);
         if (P->host_slot) PGB_CUDA(cudaMemsetAsync(P->partials.ptr + P->npartials - 1, 0, 8, s));
     }
+    // the dense top block: the intersection kernels skip the in-edges whose
+    // tail row starts at or after its first CSR position; its total takes one
+    // more partial
+    if (core_k) {
+        core_prepare(b, core_k, s, P->core);
+        P->G.core_e0 = P->core.e0;
+        P->H.core_e0 = P->core.e0;
+        P->core_slot = P->npartials;
+        P->npartials += 1;
+        P->partials.alloc(P->npartials, s);
+    }
     // the host arrays copied above are pageable; their copies are staged
     // before the calls return, so the vectors may change afterwards
     return P;
@@ -700,14 +726,17 @@ static void enqueue_reduce(const RunPlan& P, cudaStream_t s);
 
 // The device work of a planned run: the counting launches (between ev0 and
 // ev1 when given), then the reductions.
-static void enqueue_count(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, RunCtl* ctl);
+static void enqueue_count(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, RunCtl* ctl,
+                          cudaEvent_t evc0 = nullptr, cudaEvent_t evc1 = nullptr);
 
-static void enqueue(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, RunCtl* ctl) {
-    enqueue_count(P, s, ev0, ev1, ctl);
+static void enqueue(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, RunCtl* ctl,
+                    cudaEvent_t evc0 = nullptr, cudaEvent_t evc1 = nullptr) {
+    enqueue_count(P, s, ev0, ev1, ctl, evc0, evc1);
     enqueue_reduce(P, s);
 }
 
-static void enqueue_count(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, RunCtl* ctl) {
+static void enqueue_count(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1, RunCtl* ctl,
+                          cudaEvent_t evc0, cudaEvent_t evc1) {
     if (P.per_vertex && P.n) PGB_CUDA(cudaMemsetAsync(P.tv.ptr, 0, (size_t)P.n * 8, s));
     if (ev0) PGB_CUDA(cudaEventRecord(ev0, s));
     if (P.mode == PGB_MODE_PLAIN) {
@@ -751,6 +780,11 @@ static void enqueue_count(const RunPlan& P, cudaStream_t s, cudaEvent_t ev0, cud
             PGB_CUDA(cudaEventRecord(P.join_ev, P.side));
             PGB_CUDA(cudaStreamWaitEvent(s, P.join_ev, 0));
         }
+    }
+    if (P.core.K) {
+        if (evc0) PGB_CUDA(cudaEventRecord(evc0, s));
+        core_enqueue(P.core, P.per_vertex ? P.tv.ptr : nullptr, P.partials.ptr + P.core_slot, s);
+        if (evc1) PGB_CUDA(cudaEventRecord(evc1, s));
     }
     if (ev1) PGB_CUDA(cudaEventRecord(ev1, s));
 }
@@ -853,7 +887,7 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
         // the device parts' launches are queued first; the host threads count
         // the host parts meanwhile; their total fills the plan's last partial
         // and their per-vertex counts are added before the reductions
-        std::unique_ptr<RunPlan> P = prepare(b, o, o.variant, part_kind, s);
+        std::unique_ptr<RunPlan> P = prepare(b, o, o.variant, part_kind, 0, s);
         enqueue_count(*P, s, r->ev0, r->ev1, r->ctl.ptr);
         std::vector<uint8_t> host_mask(b->p);
         for (uint32_t j = 0; j < b->p; ++j) host_mask[j] = part_kind[j] == kPartHost ? 1 : 0;
@@ -885,9 +919,31 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
         r->tv_orig = std::move(P->tv_orig);
         return;
     }
+    // the dense top block: persistent runs with the autotuner, or asked for
+    const uint32_t core_k =
+        o.mode == PGB_MODE_PERSISTENT && (o_in.dense_core > 0 || (o_in.dense_core == 0 && o_in.variant == PGB_VAR_AUTO))
+            ? choose_core(b, o_in.dense_core)
+            : 0;
+    r->core_ranks = core_k;
+    if (core_k) {
+        r->core_flop = core_flop(core_k);
+        if (core_k % kCoreBand == 0)
+            for (uint32_t i = 0; i < core_k / kCoreBand && i < b->core_probes.size(); ++i)
+                r->core_lookups += b->core_probes[i];
+    }
+    auto keep_core_total = [&](const RunPlan& Q) {
+        if (!core_k) return;
+        r->core_total.alloc(1, s);
+        PGB_CUDA(cudaMemcpyAsync(r->core_total.ptr, Q.partials.ptr + Q.core_slot, 8, cudaMemcpyDeviceToDevice, s));
+    };
     if (!o.use_graph) {
-        std::unique_ptr<RunPlan> P = prepare(b, o, o.variant, part_kind, s);
-        enqueue(*P, s, r->ev0, r->ev1, r->ctl.ptr);
+        std::unique_ptr<RunPlan> P = prepare(b, o, o.variant, part_kind, core_k, s);
+        if (core_k) {
+            PGB_CUDA(cudaEventCreate(&r->evc0));
+            PGB_CUDA(cudaEventCreate(&r->evc1));
+        }
+        enqueue(*P, s, r->ev0, r->ev1, r->ctl.ptr, r->evc0, r->evc1);
+        keep_core_total(*P);
         // the outputs move to the result; the rest is released in stream order
         r->total = std::move(P->total);
         r->tv_orig = std::move(P->tv_orig);
@@ -901,10 +957,10 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
     RunPlan* P = nullptr;
     for (auto& sp : b->run_plans) {
         RunPlan* q = static_cast<RunPlan*>(sp.get());
-        if (q->same(o, o.variant, part_kind)) P = q;
+        if (q->same(o, o.variant, part_kind, core_k)) P = q;
     }
     if (!P) {
-        std::unique_ptr<RunPlan> fresh = prepare(b, o, o.variant, part_kind, s);
+        std::unique_ptr<RunPlan> fresh = prepare(b, o, o.variant, part_kind, core_k, s);
         fresh->ctl.alloc(1, s);
         PGB_CUDA(cudaStreamSynchronize(s));  // plan inputs in place before capture
         capture(*fresh);
@@ -920,6 +976,7 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
     PGB_CUDA(cudaEventRecord(r->ev1, s));
     r->total.alloc(1, s);
     PGB_CUDA(cudaMemcpyAsync(r->total.ptr, P->total.ptr, 8, cudaMemcpyDeviceToDevice, s));
+    keep_core_total(*P);
     PGB_CUDA(cudaMemcpyAsync(r->ctl.ptr, P->ctl.ptr, sizeof(RunCtl), cudaMemcpyDeviceToDevice, s));
     if (r->per_vertex) {
         r->tv_orig.alloc(n, s);
@@ -1012,6 +1069,23 @@ int pgb_tc_result_variant(pgb_tc_result* r, int* variant) {
     return guard([&] {
         if (!r || !variant) fail(PGB_E_INVAL, "NULL argument");
         *variant = r->variant;
+    });
+}
+
+int pgb_tc_result_dense_core(pgb_tc_result* r, pgb_dense_core_info* out) {
+    return guard([&] {
+        if (!r || !out) fail(PGB_E_INVAL, "NULL argument");
+        std::memset(out, 0, sizeof(*out));
+        out->ms = -1.0f;
+        out->ranks = r->core_ranks;
+        if (!r->core_ranks) return;
+        unsigned long long t = 0;
+        PGB_CUDA(cudaMemcpyAsync(&t, r->core_total.ptr, 8, cudaMemcpyDeviceToHost, r->stream));
+        PGB_CUDA(cudaStreamSynchronize(r->stream));
+        out->triangles = t;
+        out->lookups_skipped = r->core_lookups;
+        out->gemm_flop = r->core_flop;
+        if (r->evc0 && r->evc1) PGB_CUDA(cudaEventElapsedTime(&out->ms, r->evc0, r->evc1));
     });
 }
 

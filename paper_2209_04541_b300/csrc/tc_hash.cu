@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(T, 1024 / T)
                 // the head read back to pick the member bit
                 const uint32_t v = single ? I.v0 : __ldg(G.colu + (e - G.ubase));
                 vbit = 1u << (v - I.v0);
-                if (vmask & vbit) {
+                if ((vmask & vbit) && e < G.core_e0) {
                     if (I.clip) {
                         xb = hlower_bound_b(G.colu, G.ubase, xb, xe, I.lo);
                         xe = hlower_bound_b(G.colu, G.ubase, xb, xe, I.hi);

@@ -15,6 +15,9 @@ struct HashGraph {
     const uint32_t* __restrict__ itail = nullptr;  // tail of each in-edge (streamed runs), else null
     const uint32_t* __restrict__ colu = nullptr;   // rows of the tails: entry q at colu[q - ubase]
     uint32_t vbase = 0, ubase = 0;                 // ubase is a multiple of 8 (32-byte loads)
+    // in-edges whose tail-row position e (xr low word - 1) is at least this
+    // are skipped: their triangles lie in the dense top block (core.cu)
+    uint32_t core_e0 = 0xFFFFFFFFu;
 };
 
 // Where the item builder finds the heads of a set of in-edges: window w

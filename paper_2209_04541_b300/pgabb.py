@@ -82,7 +82,7 @@ class TcOpts(ctypes.Structure):
                 ("device_budget", ctypes.c_uint64), ("chunk_edges", ctypes.c_uint32),
                 ("hash_threads", ctypes.c_uint32), ("cancel", ctypes.c_void_p), ("host_threads", ctypes.c_uint32),
                 ("host_share_ppm", ctypes.c_uint32), ("hash_min_lookups", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 1)]
+                ("dense_core", ctypes.c_int32)]
 
 
 class BlocksStats(ctypes.Structure):
@@ -119,6 +119,7 @@ _SIGS = {
     "pgb_tc_result_get": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), _VP, ctypes.c_int]),
     "pgb_tc_result_triples": (ctypes.c_int, [_VP, _VP, ctypes.c_int]),
     "pgb_tc_result_kernel_ms": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "pgb_tc_result_dense_core": (ctypes.c_int, [_VP, _VP]),
     "pgb_tc_result_variant": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "pgb_tc_result_part_variants": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint32), _VP]),
     "pgb_tc_result_hybrid": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64),
@@ -600,6 +601,21 @@ def pgb_tc_result_kernel_ms(r: Result) -> float:
     ms = ctypes.c_float()
     _check(load().pgb_tc_result_kernel_ms(r, ctypes.byref(ms)), "pgb_tc_result_kernel_ms")
     return float(ms.value)
+
+
+class DenseCoreInfo(ctypes.Structure):
+    _fields_ = [("ranks", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("triangles", ctypes.c_uint64),
+                ("lookups_skipped", ctypes.c_uint64), ("gemm_flop", ctypes.c_double), ("ms", ctypes.c_float),
+                ("reserved2", ctypes.c_float)]
+
+
+def pgb_tc_result_dense_core(r) -> dict:
+    """The run's dense top block: ranks (0: none), triangles in it, lookups
+    it took off the intersection kernels, GEMM flops, device ms (-1: graph)."""
+    i = DenseCoreInfo()
+    _check(load().pgb_tc_result_dense_core(r, ctypes.byref(i)), "pgb_tc_result_dense_core")
+    return {k: (float(getattr(i, k)) if k in ("gemm_flop", "ms") else int(getattr(i, k)))
+            for k in ("ranks", "triangles", "lookups_skipped", "gemm_flop", "ms")}
 
 
 def pgb_tc_result_variant(r: Result) -> int:
