@@ -117,20 +117,19 @@ __global__ void k_core_finish(const unsigned long long* __restrict__ S, uint32_t
 }
 
 // Lookups of the in-edges whose tail is among the top kCoreBands bands of
-// ranks, per band (block-level histogram, then one atomic per band).
-// The rows start at rowptr[c_top], c_top = n - min(n, kCoreBands kCoreBand).
-__global__ void k_core_bands(const uint32_t* __restrict__ rowidx, const uint32_t* __restrict__ rowptr, uint32_t c_top,
-                             uint64_t m, uint32_t n, unsigned long long* __restrict__ bands) {
+// ranks, per band.  The in-edges with tail u are the edges of u's row, and
+// the one at row position i looks up the L_u - 1 - i entries after it, so
+// u's in-edges take L_u (L_u - 1) / 2 lookups (L_u = |row u|): one thread per
+// top row, a block histogram, one atomic per band.
+__global__ void k_core_bands(const uint32_t* __restrict__ rowptr, uint32_t n, uint32_t top,
+                             unsigned long long* __restrict__ bands) {
     __shared__ unsigned long long h[kCoreBands];
     if (threadIdx.x < kCoreBands) h[threadIdx.x] = 0;
     __syncthreads();
-    const uint64_t e0 = rowptr[c_top];
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t e = e0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-        const uint32_t u = rowidx[e];
-        const uint32_t band = (n - 1 - u) / kCoreBand;
-        const uint32_t after = rowptr[u + 1] - (uint32_t)e - 1;  // entries of u's row after this edge
-        if (band < kCoreBands && after) atomicAdd(&h[band], (unsigned long long)after);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < top; i += gridDim.x * blockDim.x) {
+        const uint32_t u = n - 1 - i;
+        const unsigned long long L = rowptr[u + 1] - rowptr[u];
+        if (L > 1) atomicAdd(&h[i / kCoreBand], L * (L - 1) / 2);
     }
     __syncthreads();
     if (threadIdx.x < kCoreBands && h[threadIdx.x]) atomicAdd(bands + threadIdx.x, h[threadIdx.x]);
@@ -194,8 +193,7 @@ uint32_t choose_core(const pgb_blocks* b, int32_t opt) {
 void core_band_probes(const pgb_blocks* b, unsigned long long* bands, cudaStream_t s) {
     if (b->m == 0 || b->n == 0) return;
     const uint32_t top = std::min<uint32_t>(b->n, kCoreBands * kCoreBand);
-    const unsigned grid = (unsigned)std::min<uint64_t>((b->m + 255) / 256, 148ull * 8);
-    k_core_bands<<<grid, 256, 0, s>>>(b->rowidx.ptr, b->rowptr.ptr, b->n - top, b->m, b->n, bands);
+    k_core_bands<<<(top + 255) / 256, 256, 0, s>>>(b->rowptr.ptr, b->n, top, bands);
     PGB_CHECK_LAUNCH("k_core_bands");
 }
 
