@@ -94,6 +94,8 @@ def generate(w, out=None):
             base += n_
         return np.concatenate(srcs), np.concatenate(dsts), base
     if w["kind"] == "rmat":
+        if w["scale"] >= 16 and _cuda_ok():
+            return rmat_on_device(w, out)
         return graphgen.rmat(w["scale"], w["ef"], w["seed"], out=out)
     if w["kind"] == "grid":
         return graphgen.grid_plus_percent(w["side"], w["pct"], w["seed"])
@@ -104,6 +106,31 @@ def generate(w, out=None):
     if w["kind"] == "rgg":
         return graphgen.rgg(w["n"], None, w["seed"])
     raise ValueError(w)
+
+
+def _cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def rmat_on_device(w, out=None):
+    """graphgen.rmat(scale, ef, seed) made by the device generator (the same
+    edges: the host's Fisher-Yates labels applied on the device) and copied
+    to host arrays (`out`, e.g. pinned, or new numpy arrays); the host
+    generator takes tens of seconds at scale 27."""
+    import torch
+    from graphgen import device as gd
+    s_d, d_d, n = gd.rmat(w["scale"], w["ef"], w["seed"], relabel="shuffle")
+    if out is None:
+        out = (np.empty(s_d.numel(), np.uint32), np.empty(d_d.numel(), np.uint32))
+    torch.from_numpy(out[0]).copy_(s_d)
+    torch.from_numpy(out[1]).copy_(d_d)
+    del s_d, d_d
+    torch.cuda.empty_cache()
+    return out[0], out[1], n
 
 
 def raw_edge_count(w):
@@ -857,12 +884,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=10000)
+    ap.add_argument("--serve-mix", choices=["full", "small"], default="full",
+                    help="full: the serving mix at its stated size (scales up to 22, jobs made on the device and "
+                         "submitted as borrowed device arrays, totals only); small: host-generated jobs up to "
+                         "scale 16, submitted from host memory, per-vertex counts on")
     ap.add_argument("--serve-max-scale", type=int, default=0,
-                    help="largest R-MAT scale and log2 n of the mix (0: 16 for the host-generated mix, 22 with "
-                         "--serve-full)")
-    ap.add_argument("--serve-full", action="store_true",
-                    help="the serving mix at its stated size (scales up to 22, device-generated); instead of the "
-                         "host-generated mix")
+                    help="largest R-MAT scale and log2 n of the mix (0: 22 for the full mix, 16 for the small one)")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-tiers", action="store_true")
     ap.add_argument("--tiers-workloads", default="rmat24,grid4096")
@@ -894,6 +921,8 @@ def main(argv=None):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     from paper_2209_04541_b300 import pgabb as P
 
+    wall = {}  # seconds of wall clock per section of this run
+    t_sec = time.perf_counter()
     w = dict(WORKLOADS[args.workload])
     if args.p:
         w["p"] = args.p
@@ -1005,7 +1034,7 @@ def main(argv=None):
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_note, "alg_bytes": kb, "alg_bytes_rule": bytes_rule,
                 "kernel_ms": sparse_ms, "count_phase_ms": kernel_ms,
-                "traffic": kernel_traffic(kname, args.workload) if not dense["ranks"] else None}
+                "traffic": kernel_traffic(kname, args.workload)}
     if dense["ranks"]:
         tf_peak = measured_tensor_peak()
         tflops = dense["gemm_flop"] / (dense_mean / 1e3) / 1e12
@@ -1023,6 +1052,8 @@ def main(argv=None):
                     "bandwidth fraction",
             "alg_bytes": info["alg_bytes"], "achieved": ew_achieved, "ratio_to_peak": ew_achieved / peak}
 
+    wall["headline"] = round(time.perf_counter() - t_sec, 1)
+    t_sec = time.perf_counter()
     e2e = None
     if not args.no_e2e:
         hout = torch.zeros(n, dtype=torch.uint64, pin_memory=True)
@@ -1040,6 +1071,8 @@ def main(argv=None):
         e2e = {"value": e_units / (e_ms / 1e3), "unit": "edges/s", "ms_per_step": e_ms,
                "h2d_bytes_per_step": 8 * mraw, "d2h_bytes_per_step": 8 + (8 * n if args.per_vertex else 0)}
 
+    wall["e2e"] = round(time.perf_counter() - t_sec, 1)
+    t_sec = time.perf_counter()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -1047,37 +1080,47 @@ def main(argv=None):
         except Exception as exc:  # reported, not hidden
             cpu = {"error": f"{type(exc).__name__}: {exc}"}
 
+    wall["cpu_baseline"] = round(time.perf_counter() - t_sec, 1)
+    t_sec = time.perf_counter()
     serve = None
     del ds, dd, tv
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_serve:
         try:
             if not args.serve_max_scale:
-                args.serve_max_scale = 22 if args.serve_full else 16
-            if args.serve_full:
+                args.serve_max_scale = 22 if args.serve_mix == "full" else 16
+            if args.serve_mix == "full":
                 serve = serve_bench_device(args)
             else:
                 serve = serve_bench(args)
         except Exception as exc:  # reported, not hidden: the TC line stands on its own
             serve = {"error": f"{type(exc).__name__}: {exc}"}
+    wall["serve"] = round(time.perf_counter() - t_sec, 1)
+    t_sec = time.perf_counter()
     tiers = None
     if rank == 0 and not args.no_tiers:
         try:
             tiers = tiers_bench(args)
         except Exception as exc:  # reported, not hidden
             tiers = {"error": f"{type(exc).__name__}: {exc}"}
+    wall["tiers"] = round(time.perf_counter() - t_sec, 1)
+    t_sec = time.perf_counter()
     autotune = None
     if rank == 0 and not args.no_autotune:
         try:
             autotune = autotune_bench(args)
         except Exception as exc:  # reported, not hidden
             autotune = {"error": f"{type(exc).__name__}: {exc}"}
+    wall["autotune"] = round(time.perf_counter() - t_sec, 1)
+    t_sec = time.perf_counter()
     patterns = None
     if rank == 0 and not args.no_patterns:
         try:
             patterns = pattern_bench(args)
         except Exception as exc:  # reported, not hidden
             patterns = {"error": f"{type(exc).__name__}: {exc}"}
+    wall["patterns"] = round(time.perf_counter() - t_sec, 1)
+    t_sec = time.perf_counter()
     streamed = None
     if rank == 0 and not args.no_stream:
         try:
@@ -1085,6 +1128,7 @@ def main(argv=None):
         except Exception as exc:  # reported, not hidden
             streamed = {"error": f"{type(exc).__name__}: {exc}"}
 
+    wall["stream"] = round(time.perf_counter() - t_sec, 1)
     if rank == 0:
         line = {"metric": "TC edges/s", "value": value, "unit": "edges/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -1106,6 +1150,7 @@ def main(argv=None):
                 "clocks": clocks, "serve": serve, "tiers": tiers, "autotune": autotune, "patterns": patterns,
                 "stream": streamed}
         line["serve_summary"] = serve_summary(serve)
+        line["section_wall_s"] = wall
         print(json.dumps(line), flush=True)
     if dist.is_initialized():
         dist.destroy_process_group()
