@@ -54,3 +54,18 @@ def test_largest_serving_jobs_device_equal_host(job):
     workload at scales up to 22."""
     same(graphgen.serve_job(job, 22), gd.serve_job(job, 22))
     torch.cuda.empty_cache()
+
+
+def test_bench_rmat24_made_on_device_equals_host():
+    """The benchmark's R-MAT s24 input, made by the device generator with
+    the host's Fisher-Yates labels (bench.py does so from scale 16 up),
+    equals the host generator's edge list."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    w = bench.WORKLOADS["rmat24"]
+    hs, hd, n = graphgen.rmat(w["scale"], w["ef"], w["seed"])
+    ds, dd, dn = bench.rmat_on_device(w)
+    assert dn == n and np.array_equal(ds, hs) and np.array_equal(dd, hd)
