@@ -188,13 +188,15 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_id: str | None):
+    def __init__(self, gpu_id: str | None, interval_ms: int = 200):
         self.gpu_id = gpu_id
+        self.interval_ms = interval_ms
         self.proc = None
         self.err = None
 
     def start(self):
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms",
+               str(self.interval_ms)]
         if self.gpu_id:
             cmd.insert(1, f"--id={self.gpu_id}")
         try:
@@ -880,6 +882,8 @@ def main(argv=None):
                     help="dense top block of the degree order: 0 autotuned, -1 none, K > 0 that many ranks")
     ap.add_argument("--hash-min-lookups", type=int, default=0,
                     help="per-part autotuner threshold, lookups per edge (0 = the library's 32)")
+    ap.add_argument("--clock-interval-ms", type=int, default=200,
+                    help="nvidia-smi sampling interval during the timed steps (each sample briefly holds the driver)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -981,7 +985,7 @@ def main(argv=None):
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
     except Exception:
         pass
-    sampler = ClockSampler(uuid)
+    sampler = ClockSampler(uuid, args.clock_interval_ms)
     sampler.start()
     l0 = P.pgb_kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
