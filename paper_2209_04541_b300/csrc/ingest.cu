@@ -7,6 +7,8 @@
 // groups equal pairs, a unique pass keeps one of each as a packed key
 // (min << B) | max, and the degree of each vertex is counted from the unique
 // pairs.
+#include <cub/device/device_merge.cuh>
+#include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_select.cuh>
 #include <thrust/iterator/counting_iterator.h>
 #include <thrust/iterator/transform_iterator.h>
@@ -153,6 +155,151 @@ static void finish_ingest(pgb_graph* g, DevBuf<uint32_t>& lo, DevBuf<uint32_t>& 
     g->keys = std::move(uniq);
 }
 
+// ---- host input in chunks
+//
+// A host edge list is copied in chunks on a second stream; each chunk is
+// canonicalised into packed keys (min << B) | max (self-loops and invalid
+// pairs become all ones, which sort last) and sorted while the next chunk
+// is still on the way, so most of the sorting hides behind the host link.
+// The sorted runs are then merged pairwise, and the unique pass and the
+// degree count finish the ingest as for device input.
+constexpr uint64_t kChunkPairs = 1ull << 25;  // pairs per chunk
+constexpr uint64_t kChunkedMin = 1ull << 26;  // host lists of at least this many pairs are chunked
+
+__global__ void k_canon_pack(const uint32_t* __restrict__ src, const uint32_t* __restrict__ dst, uint64_t m,
+                             uint32_t n, uint32_t B, uint64_t* __restrict__ keys, int* __restrict__ err) {
+    const uint64_t sentinel = B >= 32 ? ~0ull : (1ull << (2 * B)) - 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const uint32_t a = src[e], b = dst[e];
+        uint64_t key = sentinel;
+        if (a >= n || b >= n) {
+            atomicOr(err, 1);
+        } else if (a != b) {
+            key = ((uint64_t)(a < b ? a : b) << B) | (a < b ? b : a);
+        }
+        keys[e] = key;
+    }
+}
+
+// Sorted packed keys of the m host pairs, in `out` (m entries); `spare` is
+// an m-entry scratch buffer.
+static void sort_host_chunked(const pgb_graph* g, const uint32_t* src, const uint32_t* dst, uint64_t m,
+                              DevBuf<uint64_t>& out, DevBuf<uint64_t>& spare, const DevBuf<int>& err,
+                              cudaStream_t s) {
+    const uint32_t B = g->id_bits;
+    const int end_bit = (int)(2 * B);
+    const uint64_t C = kChunkPairs;
+    Scratch scratch;
+    DevBuf<uint32_t> stage(4 * C, s);  // two (src, dst) staging pairs
+    cudaStream_t cs = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, used[2] = {nullptr, nullptr};
+    auto cleanup = [&] {
+        for (cudaEvent_t e : copied)
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : used)
+            if (e) cudaEventDestroy(e);
+        if (cs) cudaStreamDestroy(cs);
+    };
+    try {
+        PGB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k) {
+            PGB_CUDA(cudaEventCreateWithFlags(&copied[k], cudaEventDisableTiming));
+            PGB_CUDA(cudaEventCreateWithFlags(&used[k], cudaEventDisableTiming));
+            // the staging memory was allocated on s: the copy stream starts after that
+            PGB_CUDA(cudaEventRecord(used[k], s));
+        }
+        size_t sort_tmp = 0;
+        {
+            cub::DoubleBuffer<uint64_t> db(out.ptr, spare.ptr);
+            PGB_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, sort_tmp, db, (int64_t)C, 0, end_bit, s));
+        }
+        void* tmp = scratch.get(sort_tmp, s);
+        uint64_t i = 0;
+        for (uint64_t off = 0; off < m; off += C, ++i) {
+            const int k = (int)(i & 1);
+            const uint64_t len = m - off < C ? m - off : C;
+            uint32_t* cs_src = stage.ptr + (size_t)k * 2 * C;
+            uint32_t* cs_dst = cs_src + C;
+            PGB_CUDA(cudaStreamWaitEvent(cs, used[k], 0));
+            PGB_CUDA(cudaMemcpyAsync(cs_src, src + off, len * 4, cudaMemcpyHostToDevice, cs));
+            PGB_CUDA(cudaMemcpyAsync(cs_dst, dst + off, len * 4, cudaMemcpyHostToDevice, cs));
+            PGB_CUDA(cudaEventRecord(copied[k], cs));
+            PGB_CUDA(cudaStreamWaitEvent(s, copied[k], 0));
+            k_canon_pack<<<grid_for(len), 256, 0, s>>>(cs_src, cs_dst, len, g->n, B, out.ptr + off, err.ptr);
+            PGB_CHECK_LAUNCH("k_canon_pack");
+            PGB_CUDA(cudaEventRecord(used[k], s));
+            cub::DoubleBuffer<uint64_t> db(out.ptr + off, spare.ptr + off);
+            size_t t = sort_tmp;
+            PGB_CUDA(cub::DeviceRadixSort::SortKeys(tmp, t, db, (int64_t)len, 0, end_bit, s));
+            if (db.Current() != out.ptr + off)
+                PGB_CUDA(cudaMemcpyAsync(out.ptr + off, db.Current(), len * 8, cudaMemcpyDeviceToDevice, s));
+        }
+    } catch (...) {
+        cudaStreamSynchronize(s);
+        if (cs) cudaStreamSynchronize(cs);
+        cleanup();
+        throw;
+    }
+    cleanup();
+    // merge the sorted runs pairwise until one run is left; `out` ends up
+    // holding the result
+    for (uint64_t run = C; run < m; run *= 2) {
+        for (uint64_t a0 = 0; a0 < m; a0 += 2 * run) {
+            const uint64_t a1 = a0 + run < m ? a0 + run : m, b1 = a0 + 2 * run < m ? a0 + 2 * run : m;
+            if (a1 == b1) {  // no partner in this round: carried over
+                PGB_CUDA(cudaMemcpyAsync(spare.ptr + a0, out.ptr + a0, (a1 - a0) * 8, cudaMemcpyDeviceToDevice, s));
+                continue;
+            }
+            size_t t = 0;
+            PGB_CUDA(cub::DeviceMerge::MergeKeys(nullptr, t, out.ptr + a0, (int64_t)(a1 - a0), out.ptr + a1,
+                                                 (int64_t)(b1 - a1), spare.ptr + a0, ::cuda::std::less<>{}, s));
+            void* tm = scratch.get(t, s);
+            PGB_CUDA(cub::DeviceMerge::MergeKeys(tm, t, out.ptr + a0, (int64_t)(a1 - a0), out.ptr + a1,
+                                                 (int64_t)(b1 - a1), spare.ptr + a0, ::cuda::std::less<>{}, s));
+        }
+        out.swap(spare);
+    }
+}
+
+// Unique pass and degree count over sorted packed keys (`sorted`, m
+// entries); `spare` (m entries) receives the unique keys and becomes the
+// graph's.  Fails on the error flags first.
+static void finish_sorted(pgb_graph* g, DevBuf<uint64_t>& sorted, DevBuf<uint64_t>& spare, uint64_t m,
+                          const DevBuf<int>& err, cudaStream_t s) {
+    const uint32_t B = g->id_bits;
+    const int end_bit = (int)(2 * B);
+    Scratch scratch;
+    DevBuf<int64_t> nsel(1, s);
+    size_t tmp = 0;
+    PGB_CUDA(cub::DeviceSelect::Unique(nullptr, tmp, sorted.ptr, spare.ptr, nsel.ptr, (int64_t)m, s));
+    void* t = scratch.get(tmp, s);
+    PGB_CUDA(cub::DeviceSelect::Unique(t, tmp, sorted.ptr, spare.ptr, nsel.ptr, (int64_t)m, s));
+    sorted.release();
+    int64_t nu = 0;
+    int herr = 0;
+    PGB_CUDA(cudaMemcpyAsync(&nu, nsel.ptr, sizeof(nu), cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaMemcpyAsync(&herr, err.ptr, sizeof(herr), cudaMemcpyDeviceToHost, s));
+    PGB_CUDA(cudaStreamSynchronize(s));
+    if (herr & 1) fail(PGB_E_INVAL, "vertex ID >= n in input");
+    uint64_t mu = (uint64_t)nu;
+    if (mu > 0) {
+        uint64_t last = 0;
+        PGB_CUDA(cudaMemcpyAsync(&last, spare.ptr + mu - 1, sizeof(last), cudaMemcpyDeviceToHost, s));
+        PGB_CUDA(cudaStreamSynchronize(s));
+        const uint64_t sentinel = (end_bit >= 64) ? ~0ull : ((1ull << end_bit) - 1);
+        if ((last & sentinel) == sentinel) --mu;
+    }
+    if (mu >= (1ull << 32)) fail(PGB_E_OVERFLOW, "2^32 or more unique edges are not supported");
+    g->m = mu;
+    g->deg.alloc(g->n, s);
+    if (g->n) PGB_CUDA(cudaMemsetAsync(g->deg.ptr, 0, (size_t)g->n * sizeof(uint32_t), s));
+    if (mu) {
+        k_degrees<<<grid_for(mu), 256, 0, s>>>(spare.ptr, mu, B, g->deg.ptr);
+        PGB_CHECK_LAUNCH("k_degrees");
+    }
+    g->keys = std::move(spare);
+}
 static pgb_graph* new_graph(uint32_t n, cudaStream_t s) {
     pgb_graph* g = new pgb_graph();
     g->n = n;
@@ -177,6 +324,17 @@ int pgb_graph_from_edges(const uint32_t* src, const uint32_t* dst, uint64_t m, u
         cudaStream_t s = (cudaStream_t)stream;
         std::unique_ptr<pgb_graph> g(new_graph(n, s));
         const uint32_t top = (uint32_t)((1ull << g->id_bits) - 1);  // the (top, top) pair sorts last
+        if (mem == PGB_MEM_HOST && m >= kChunkedMin) {
+            // host input: sorted per chunk behind the copies, then merged
+            DevBuf<int> err(1, s);
+            PGB_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
+            DevBuf<uint64_t> keys(m, s), spare(m, s);
+            sort_host_chunked(g.get(), src, dst, m, keys, spare, err, s);
+            finish_sorted(g.get(), keys, spare, m, err, s);
+            live_handles_add(1);
+            *out = g.release();
+            return;
+        }
         DevBuf<uint32_t> lo(m, s), hi(m, s);
         DevBuf<int> err(1, s);
         PGB_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
