@@ -796,7 +796,8 @@ def stream_bench(args):
             r = P.pgb_tc_run(b, opts)
             T, tv = P.pgb_tc_result_get(r, per_vertex=True)
             wall = time.perf_counter() - t
-            out.append((T, tv, wall, P.pgb_tc_result_kernel_ms(r), P.pgb_tc_result_stream(r, slice_loads=True)))
+            out.append((T, tv, wall, P.pgb_tc_result_kernel_ms(r), P.pgb_tc_result_stream(r, slice_loads=True),
+                        P.pgb_tc_result_dense_core(r)["ranks"]))
             r.free()
         return out
 
@@ -818,14 +819,14 @@ def stream_bench(args):
         return {"device_budget_bytes": budget, "resident_floor_bytes": floor, "chunks": chunks,
                 "slice_loads": loads, "streamed_bytes": nbytes, "value": m / wall, "unit": "edges/s",
                 "wall_ms": 1e3 * wall, "kernel_ms": kms, "link_gbs": nbytes / (kms / 1e3) / 1e9,
-                "link_frac": nbytes / (kms / 1e3) / 1e9 / link}
+                "link_frac": nbytes / (kms / 1e3) / 1e9 / link, "dense_core_ranks": runs[0][5]}
 
     out = {"metric": "streamed TC edges/s", "workload": w["desc"], "n": n, "unique_edges": m, "triangles": T,
            "resident_graph_bytes": 4 * m + 12 * m + 4 * m + 12 * (n + 1), "steps": reps, "preprocess_s": prep_s,
            "h2d_peak_gbs": link,
            "resident": {"value": m / statistics.median(x[2] for x in res), "unit": "edges/s",
                         "wall_ms": 1e3 * statistics.median(x[2] for x in res),
-                        "kernel_ms": statistics.median(x[3] for x in res)},
+                        "kernel_ms": statistics.median(x[3] for x in res), "dense_core_ranks": res[0][5]},
            "check": "streamed totals and per-vertex counts equal the resident run's; sum t = 3T"}
     # tier 1: the in-edge index streamed, columns resident
     budget = int(args.stream_budget_gb * (1 << 30))

@@ -50,14 +50,19 @@ constexpr double kSecondsPerLookup = 1.0e-12;
 constexpr double kGemmFlops = 1.4e15;
 constexpr double kMinGainSeconds = 3e-4;
 
-__global__ void k_core_fill(const uint32_t* __restrict__ rowidx, const uint32_t* __restrict__ col, uint64_t e0,
-                            uint64_t m, uint32_t c0, uint32_t K, __half* __restrict__ A) {
+// The block's adjacency from its rows: row r in [c0, n) holds only columns
+// in the block (they exceed r), written both ways.  One thread per row: the
+// top ranks' rows are short.
+__global__ void k_core_fill(const uint32_t* __restrict__ rowptr, const uint32_t* __restrict__ col, uint32_t c0,
+                            uint32_t K, __half* __restrict__ A) {
     const __half one = __ushort_as_half((unsigned short)0x3C00u);
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t e = e0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-        const uint32_t a = rowidx[e] - c0, b = col[e] - c0;
-        A[(uint64_t)a * K + b] = one;
-        A[(uint64_t)b * K + a] = one;
+    for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < K; a += gridDim.x * blockDim.x) {
+        const uint32_t q1 = rowptr[c0 + a + 1];
+        for (uint32_t q = rowptr[c0 + a]; q < q1; ++q) {
+            const uint32_t b = col[q] - c0;
+            A[(uint64_t)a * K + b] = one;
+            A[(uint64_t)b * K + a] = one;
+        }
     }
 }
 
@@ -135,7 +140,16 @@ __global__ void k_core_bands(const uint32_t* __restrict__ rowptr, uint32_t n, ui
     if (threadIdx.x < kCoreBands && h[threadIdx.x]) atomicAdd(bands + threadIdx.x, h[threadIdx.x]);
 }
 
+__global__ void k_core_add(const unsigned long long* __restrict__ from, unsigned long long* __restrict__ to) {
+    *to += *from;
+}
+
 }  // namespace
+
+void core_add_total(const unsigned long long* from, unsigned long long* to, cudaStream_t s) {
+    k_core_add<<<1, 1, 0, s>>>(from, to);
+    PGB_CHECK_LAUNCH("k_core_add");
+}
 
 // A cuBLAS handle per host thread (never destroyed: a handle torn down at
 // thread exit could outlive the CUDA context).
@@ -197,11 +211,20 @@ void core_band_probes(const pgb_blocks* b, unsigned long long* bands, cudaStream
     PGB_CHECK_LAUNCH("k_core_bands");
 }
 
+// cuBLAS workspace of a plan: 32 MiB (its recommendation on this GPU) for
+// blocks of 8,192 ranks or more, 4 MiB below.
+static uint64_t core_workspace(uint32_t K) { return K >= 8192 ? (32u << 20) : (4u << 20); }
+
+uint64_t core_bytes(uint32_t K) {
+    const uint64_t T = std::min(kTile, K);
+    return (uint64_t)K * K * sizeof(__half) + T * K * sizeof(float) + (uint64_t)K * 8 + core_workspace(K);
+}
+
 void core_prepare(const pgb_blocks* b, uint32_t K, cudaStream_t s, CorePlan& P) {
     P.K = K;
     P.c0 = b->n - K;
     P.m = b->m;
-    P.rowidx = b->rowidx.ptr;
+    P.rowptr = b->rowptr.ptr;
     P.col = b->col.ptr;
     P.tile = std::min(kTile, K);
     uint32_t e0 = 0;
@@ -211,7 +234,7 @@ void core_prepare(const pgb_blocks* b, uint32_t K, cudaStream_t s, CorePlan& P) 
     P.A.alloc((size_t)K * K, s);
     P.C.alloc((size_t)P.tile * K, s);
     P.S.alloc(K, s);
-    P.workspace.alloc(32u << 20, s);
+    P.workspace.alloc(core_workspace(K), s);
 }
 
 void core_enqueue(const CorePlan& P, unsigned long long* tv, unsigned long long* slot, cudaStream_t s) {
@@ -219,8 +242,7 @@ void core_enqueue(const CorePlan& P, unsigned long long* tv, unsigned long long*
     PGB_CUDA(cudaMemsetAsync(P.A.ptr, 0, (size_t)K * K * sizeof(__half), s));
     PGB_CUDA(cudaMemsetAsync(P.S.ptr, 0, (size_t)K * 8, s));
     if (P.m > P.e0) {
-        const unsigned grid = (unsigned)std::min<uint64_t>((P.m - P.e0 + 255) / 256, 148ull * 16);
-        k_core_fill<<<grid, 256, 0, s>>>(P.rowidx, P.col, P.e0, P.m, P.c0, K, P.A.ptr);
+        k_core_fill<<<(K + 255) / 256, 256, 0, s>>>(P.rowptr, P.col, P.c0, K, P.A.ptr);
         PGB_CHECK_LAUNCH("k_core_fill");
     }
     cublasHandle_t h = blas_handle();

@@ -12,7 +12,7 @@ namespace pgb {
 struct CorePlan {
     uint32_t K = 0, c0 = 0, e0 = 0, tile = 0;  // e0 = rowptr[c0]: the block's first CSR position
     uint64_t m = 0;
-    const uint32_t* rowidx = nullptr;  // the oriented graph (rank space)
+    const uint32_t* rowptr = nullptr;  // the oriented graph's rows (rank space)
     const uint32_t* col = nullptr;
     DevBuf<__half> A;
     DevBuf<float> C;
@@ -39,6 +39,12 @@ void core_prepare(const pgb_blocks* b, uint32_t K, cudaStream_t s, CorePlan& P);
 // Count the block's triangles: adds t[x] of its vertices into tv (rank
 // space, may be null) and writes the block's total to *slot.  Capturable.
 void core_enqueue(const CorePlan& P, unsigned long long* tv, unsigned long long* slot, cudaStream_t s);
+
+// *to += *from on the device (one thread).
+void core_add_total(const unsigned long long* from, unsigned long long* to, cudaStream_t s);
+
+// Device bytes a plan for the top K ranks holds.
+uint64_t core_bytes(uint32_t K);
 
 // The per-band lookups of the top ranks (kCoreBands values), on the device.
 void core_band_probes(const pgb_blocks* b, unsigned long long* bands, cudaStream_t s);

@@ -152,7 +152,7 @@ static std::shared_ptr<StreamPlan> get_plan(const pgb_blocks* b, uint32_t in_chu
 void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint32_t threads, unsigned long long* tv,
                    uint64_t budget,
                    cudaStream_t s, DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
-                   cudaEvent_t ev1, uint64_t* streamed, uint32_t* nchunks_out, RunCtl* ctl) {
+                   cudaEvent_t ev1, uint64_t* streamed, uint32_t* nchunks_out, RunCtl* ctl, uint32_t core_e0) {
     npartials = 0;
     *streamed = 0;
     *nchunks_out = 0;
@@ -175,6 +175,7 @@ void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint32_t thr
     {
         hg[k] = HashGraph{b->rowptr.ptr, b->col.ptr, nullptr, sxr[k].ptr, tv, b->n, stail[k].ptr};
         hg[k].colu = b->col.ptr;
+        hg[k].core_e0 = core_e0;
     }
     npartials = (uint64_t)grid * P->chunks.size();
     partials.alloc(npartials, s);

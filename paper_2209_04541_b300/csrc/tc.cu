@@ -862,17 +862,48 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
             tv.alloc(n, s);
             if (n) PGB_CUDA(cudaMemsetAsync(tv.ptr, 0, (size_t)n * 8, s));
         }
+        // the index tier (rows and columns resident) takes the dense top block
+        // too, its bytes charged to the device budget before the slots
+        CorePlan core;
+        uint64_t budget = o.device_budget;
+        if (!b->cols_offloaded && (o_in.dense_core > 0 || (o_in.dense_core == 0 && o_in.variant == PGB_VAR_AUTO))) {
+            const uint32_t k = choose_core(b, o_in.dense_core);
+            const uint64_t need = k ? core_bytes(k) : 0;
+            // at most half the budget goes to the block; the rest keeps the slots
+            if (k && (budget == 0 || need <= budget / 2)) {
+                core_prepare(b, k, s, core);
+                if (budget) budget -= need;
+                r->core_ranks = k;
+                r->core_flop = core_flop(k);
+                if (k % kCoreBand == 0)
+                    for (uint32_t i = 0; i < k / kCoreBand && i < b->core_probes.size(); ++i)
+                        r->core_lookups += b->core_probes[i];
+            }
+        }
         if (b->cols_offloaded)
             run_column_streaming(b, r->per_vertex, o.hash_threads, tv.ptr, o.device_budget, s, partials, npartials,
                                  r->ev0, r->ev1, &r->streamed, &r->chunks, &r->slice_loads, r->ctl.ptr);
         else
-            run_streaming(b, o.chunk_edges, r->per_vertex, o.hash_threads, tv.ptr, o.device_budget, s, partials,
-                          npartials, r->ev0, r->ev1, &r->streamed, &r->chunks, r->ctl.ptr);
+            run_streaming(b, o.chunk_edges, r->per_vertex, o.hash_threads, tv.ptr, budget, s, partials,
+                          npartials, r->ev0, r->ev1, &r->streamed, &r->chunks, r->ctl.ptr,
+                          core.K ? core.e0 : 0xFFFFFFFFu);
         if (npartials)
             k_reduce_sum<<<1, 1024, 0, s>>>(partials.ptr, npartials, r->total.ptr);
         else
             PGB_CUDA(cudaMemsetAsync(r->total.ptr, 0, 8, s));
         PGB_CHECK_LAUNCH("k_reduce_sum");
+        if (core.K) {
+            // after the streamed launches (run_streaming returned once they
+            // completed); the count phase's end event moves past the block
+            PGB_CUDA(cudaEventCreate(&r->evc0));
+            PGB_CUDA(cudaEventCreate(&r->evc1));
+            r->core_total.alloc(1, s);
+            PGB_CUDA(cudaEventRecord(r->evc0, s));
+            core_enqueue(core, r->per_vertex ? tv.ptr : nullptr, r->core_total.ptr, s);
+            PGB_CUDA(cudaEventRecord(r->evc1, s));
+            core_add_total(r->core_total.ptr, r->total.ptr, s);
+            PGB_CUDA(cudaEventRecord(r->ev1, s));
+        }
         if (r->per_vertex) {
             r->tv_orig.alloc(n, s);
             if (n) {

@@ -92,7 +92,8 @@ void launch_hash(const HashGraph& G, const VItem* items, uint32_t nitems, bool p
 void run_streaming(const pgb_blocks* b, uint32_t in_chunk, bool pv, uint32_t threads, unsigned long long* tv,
                    uint64_t budget,
                    cudaStream_t s, DevBuf<unsigned long long>& partials, uint64_t& npartials, cudaEvent_t ev0,
-                   cudaEvent_t ev1, uint64_t* streamed, uint32_t* nchunks, RunCtl* ctl);
+                   cudaEvent_t ev1, uint64_t* streamed, uint32_t* nchunks, RunCtl* ctl,
+                   uint32_t core_e0 = 0xFFFFFFFFu);  // in-edges at or after it left to the dense top block
 
 // Run over blocks whose columns are offloaded too: pieces of block pairs
 // (tail block, head block) with their column slices in a device cache that

@@ -140,3 +140,36 @@ def test_offloaded_state_rules():
     # and the handle still counts afterwards
     assert _streamed(b, True, 0)[0] == oT
     assert P.pgb_blocks_resident_bytes(b, False) < floor
+
+
+def _induced_top_triangles(src, dst, n, K):
+    """Oracle: triangles of the subgraph the K highest ranks induce."""
+    g = oracle.clean(src, dst, n)
+    o = oracle.orient(g)
+    top = np.zeros(n, bool)
+    top[o.perm[n - K:]] = True
+    s_ = np.repeat(np.arange(n, dtype=np.uint32), np.diff(g.offs).astype(np.int64))
+    d_ = g.adj.astype(np.uint32)
+    keep = top[s_] & top[d_] & (s_ < d_)
+    return oracle.tc_node_iterator(oracle.clean(s_[keep], d_[keep], n), False)[0]
+
+
+@pytest.mark.parametrize("per_vertex", [True, False])
+def test_index_tier_with_dense_top_block(per_vertex):
+    """The index tier with the dense top block: its bytes come out of the
+    budget, the streamed launches skip its in-edges, and the counts still
+    equal the oracle's; the block's own count is the induced subgraph's."""
+    src, dst, n = graphgen.rmat(16, 16, 21)
+    oT, ot = _oracle(src, dst, n)
+    b = _blocks(src, dst, n, 8)
+    m = P.pgb_blocks_info(b)["m"]
+    P.pgb_blocks_offload(b)
+    budget = _budget(b, per_vertex, m // 7) + (256 << 20)
+    r = P.pgb_tc_run(b, P.pgb_tc_opts_default(per_vertex=int(per_vertex), device_budget=budget, dense_core=2048))
+    T, t = P.pgb_tc_result_get(r, per_vertex=per_vertex)
+    d = P.pgb_tc_result_dense_core(r)
+    assert T == oT and d["ranks"] == 2048 and d["ms"] > 0
+    if per_vertex:
+        assert np.array_equal(t, ot)
+    assert d["triangles"] == _induced_top_triangles(src, dst, n, 2048)
+    assert P.pgb_tc_result_stream(r)[1] >= 1
