@@ -354,7 +354,11 @@ typedef struct {
                               cores (below).  0: autotuned with PGB_VAR_AUTO,
                               none otherwise; > 0: that many top ranks
                               (rounded up to a multiple of 256, at most n);
-                              < 0: none.  HYBRID runs use none. */
+                              < 0: none.  HYBRID runs take it too (the
+                              host kernel skips its in-edges); streamed runs
+                              of the index tier when it fits in half the
+                              device budget; PLAIN runs and the column tier
+                              never. */
 } pgb_tc_opts;
 
 void pgb_tc_opts_default(pgb_tc_opts* o);

@@ -148,7 +148,7 @@ std::vector<uint8_t> host_parts_by_cutoff(const pgb_blocks* b, uint32_t share_pp
 
 HostCountResult host_count_parts(const pgb_blocks* b, const std::vector<uint8_t>& host, uint32_t threads,
                                  bool per_vertex, std::vector<std::pair<uint32_t, uint32_t>>& adds,
-                                 const pgb_cancel* cancel, cudaStream_t s) {
+                                 const pgb_cancel* cancel, cudaStream_t s, uint32_t core_e0) {
     HostCountResult R;
     const auto t0 = std::chrono::steady_clock::now();
     // head runs of the host parts, lightest part first
@@ -193,6 +193,7 @@ HostCountResult host_count_parts(const pgb_blocks* b, const std::vector<uint8_t>
                 for (uint32_t q = H.colptr[v]; q < H.colptr[v + 1]; ++q) {
                     const unsigned long long r = H.xr[q];
                     const uint32_t xb = (uint32_t)r, xe = (uint32_t)(r >> 32);
+                    if (xb - 1 >= core_e0) continue;  // the tail is in the dense top block
                     uint64_t c;
                     if (per_vertex) c = intersect(col, xb, xe, vb, ve, [&](uint32_t w) { out.emplace_back(w, 1u); });
                     else c = intersect(col, xb, xe, vb, ve, [](uint32_t) {});

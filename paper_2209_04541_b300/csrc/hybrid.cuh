@@ -24,8 +24,10 @@ struct HostCountResult {
 // as (vertex, count) pairs (a vertex may appear more than once): the host
 // parts are the light ones, so their contributions are sparse.  Copies the
 // oriented graph to a host mirror on first use (synchronising s).
+// In-edges whose tail row starts at CSR position core_e0 or later are left to
+// the dense top block.
 HostCountResult host_count_parts(const pgb_blocks* b, const std::vector<uint8_t>& host, uint32_t threads,
                                  bool per_vertex, std::vector<std::pair<uint32_t, uint32_t>>& adds,
-                                 const pgb_cancel* cancel, cudaStream_t s);
+                                 const pgb_cancel* cancel, cudaStream_t s, uint32_t core_e0 = 0xFFFFFFFFu);
 
 }  // namespace pgb

@@ -515,7 +515,8 @@ struct RunPlan {
     int grid = 0, threads = 128;
     int hgrid = 0;                // general plans: CTAs of the hash launch (partials [0, hgrid))
     bool general = false;         // parts split between kernels (and the host): filtered launches
-    bool host_slot = false;       // HYBRID: the last partial holds the host's total
+    bool host_slot = false;       // HYBRID: partials[host_idx] holds the host's total
+    uint64_t host_idx = 0;
     std::vector<uint8_t> part_kind;
     DevBuf<uint8_t> dpart_hash;
     const uint32_t* perm = nullptr;
@@ -699,9 +700,9 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
             PGB_CUDA(cudaEventCreateWithFlags(&P->fork_ev, cudaEventDisableTiming));
             PGB_CUDA(cudaEventCreateWithFlags(&P->join_ev, cudaEventDisableTiming));
         }
-        if (P->host_slot) P->npartials += 1;  // written once the host parts are counted
+        if (P->host_slot) P->host_idx = P->npartials++;  // written once the host parts are counted
         P->partials.alloc(P->npartials, s);
-        if (P->host_slot) PGB_CUDA(cudaMemsetAsync(P->partials.ptr + P->npartials - 1, 0, 8, s));
+        if (P->host_slot) PGB_CUDA(cudaMemsetAsync(P->partials.ptr + P->host_idx, 0, 8, s));
     }
     // the dense top block: the intersection kernels skip the in-edges whose
     // tail row starts at or after its first CSR position; its total takes one
@@ -713,6 +714,7 @@ static std::unique_ptr<RunPlan> prepare(const pgb_blocks* b, const pgb_tc_opts& 
         P->core_slot = P->npartials;
         P->npartials += 1;
         P->partials.alloc(P->npartials, s);
+        if (P->host_slot) PGB_CUDA(cudaMemsetAsync(P->partials.ptr + P->host_idx, 0, 8, s));
     }
     // the host arrays copied above are pageable; their copies are staged
     // before the calls return, so the vectors may change afterwards
@@ -914,16 +916,41 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
         }
         return;
     }
+    // the dense top block: persistent runs with the autotuner, or asked for
+    const uint32_t core_k =
+        (o.mode == PGB_MODE_PERSISTENT || o.mode == PGB_MODE_HYBRID) &&
+                (o_in.dense_core > 0 || (o_in.dense_core == 0 && o_in.variant == PGB_VAR_AUTO))
+            ? choose_core(b, o_in.dense_core)
+            : 0;
+    r->core_ranks = core_k;
+    if (core_k) {
+        r->core_flop = core_flop(core_k);
+        if (core_k % kCoreBand == 0)
+            for (uint32_t i = 0; i < core_k / kCoreBand && i < b->core_probes.size(); ++i)
+                r->core_lookups += b->core_probes[i];
+    }
+    auto keep_core_total = [&](const RunPlan& Q) {
+        if (!core_k) return;
+        r->core_total.alloc(1, s);
+        PGB_CUDA(cudaMemcpyAsync(r->core_total.ptr, Q.partials.ptr + Q.core_slot, 8, cudaMemcpyDeviceToDevice, s));
+    };
     if (o.mode == PGB_MODE_HYBRID) {
         // the device parts' launches are queued first; the host threads count
         // the host parts meanwhile; their total fills the plan's last partial
         // and their per-vertex counts are added before the reductions
-        std::unique_ptr<RunPlan> P = prepare(b, o, o.variant, part_kind, 0, s);
-        enqueue_count(*P, s, r->ev0, r->ev1, r->ctl.ptr);
+        std::unique_ptr<RunPlan> P = prepare(b, o, o.variant, part_kind, core_k, s);
+        if (core_k) {
+            PGB_CUDA(cudaEventCreate(&r->evc0));
+            PGB_CUDA(cudaEventCreate(&r->evc1));
+        }
+        enqueue_count(*P, s, r->ev0, r->ev1, r->ctl.ptr, r->evc0, r->evc1);
+        keep_core_total(*P);
         std::vector<uint8_t> host_mask(b->p);
         for (uint32_t j = 0; j < b->p; ++j) host_mask[j] = part_kind[j] == kPartHost ? 1 : 0;
         std::vector<std::pair<uint32_t, uint32_t>> adds;
-        const HostCountResult hr = host_count_parts(b, host_mask, o.host_threads, r->per_vertex, adds, o.cancel, s);
+        // the host kernel skips the dense block's in-edges as the device kernels do
+        const HostCountResult hr = host_count_parts(b, host_mask, o.host_threads, r->per_vertex, adds, o.cancel, s,
+                                                    core_k ? P->core.e0 : 0xFFFFFFFFu);
         r->host_ms = hr.ms;
         r->host_in_edges = hr.in_edges;
         r->host_parts = hr.parts;
@@ -931,7 +958,7 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
         r->host_cancelled = hr.cancelled;
         if (P->host_slot) {
             const unsigned long long h_total = hr.total;
-            PGB_CUDA(cudaMemcpyAsync(P->partials.ptr + P->npartials - 1, &h_total, 8, cudaMemcpyHostToDevice, s));
+            PGB_CUDA(cudaMemcpyAsync(P->partials.ptr + P->host_idx, &h_total, 8, cudaMemcpyHostToDevice, s));
         }
         DevBuf<uint32_t> dadds;
         if (r->per_vertex && !adds.empty()) {
@@ -950,23 +977,6 @@ static void run(const pgb_blocks* b, const pgb_tc_opts& o_in, cudaStream_t s, pg
         r->tv_orig = std::move(P->tv_orig);
         return;
     }
-    // the dense top block: persistent runs with the autotuner, or asked for
-    const uint32_t core_k =
-        o.mode == PGB_MODE_PERSISTENT && (o_in.dense_core > 0 || (o_in.dense_core == 0 && o_in.variant == PGB_VAR_AUTO))
-            ? choose_core(b, o_in.dense_core)
-            : 0;
-    r->core_ranks = core_k;
-    if (core_k) {
-        r->core_flop = core_flop(core_k);
-        if (core_k % kCoreBand == 0)
-            for (uint32_t i = 0; i < core_k / kCoreBand && i < b->core_probes.size(); ++i)
-                r->core_lookups += b->core_probes[i];
-    }
-    auto keep_core_total = [&](const RunPlan& Q) {
-        if (!core_k) return;
-        r->core_total.alloc(1, s);
-        PGB_CUDA(cudaMemcpyAsync(r->core_total.ptr, Q.partials.ptr + Q.core_slot, 8, cudaMemcpyDeviceToDevice, s));
-    };
     if (!o.use_graph) {
         std::unique_ptr<RunPlan> P = prepare(b, o, o.variant, part_kind, core_k, s);
         if (core_k) {

@@ -111,3 +111,20 @@ def test_hybrid_cancel_and_states(graph):
     with pytest.raises(P.PgbError) as ei:
         P.pgb_tc_run(b, P.pgb_tc_opts_default(mode=P.PGB_MODE_HYBRID, host_share_ppm=2000000))
     assert ei.value.code == P.PGB_E_INVAL
+
+
+@pytest.mark.parametrize("share", [1000, 1000000])
+@pytest.mark.parametrize("per_vertex", [True, False])
+def test_hybrid_with_dense_top_block(graph, share, per_vertex):
+    """The dense top block in HYBRID runs: with every part on the host
+    (share 10^6) the host kernel must skip the block's in-edges, or the
+    block's triangles would be counted twice."""
+    b, T, t = graph
+    assert P.pgb_blocks_info(b)["n"] > 2048
+    r = P.pgb_tc_run(b, P.pgb_tc_opts_default(mode=P.PGB_MODE_HYBRID, host_share_ppm=share, dense_core=2048,
+                                              per_vertex=int(per_vertex)))
+    gT, gt = P.pgb_tc_result_get(r, per_vertex=per_vertex)
+    d = P.pgb_tc_result_dense_core(r)
+    assert d["ranks"] == 2048 and d["triangles"] > 0 and gT == T
+    if per_vertex:
+        assert np.array_equal(gt, t)
