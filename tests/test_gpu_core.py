@@ -101,3 +101,14 @@ def test_autotuner_leaves_small_and_flat_graphs_alone():
         T, t, (ranks, _) = run(src, dst, n, 4)
         assert ranks == 0
         assert T == oracle.tc_node_iterator(oracle.clean(src, dst, n), False)[0]
+
+
+@pytest.mark.parametrize("n,m,seed", [(1001, 30000, 3), (777, 60000, 5)])
+def test_dense_block_of_unaligned_size(n, m, seed):
+    """K = n not a multiple of 8 (leading dimensions cuBLAS cannot tile with
+    aligned tensor-core loads): still exact."""
+    src, dst, _ = graphgen.er_distinct(n, m, seed)
+    g = oracle.clean(src, dst, n)
+    T_ref, t_ref = oracle.tc_node_iterator(g)
+    T, t, (ranks, tc) = run(src, dst, n, 4, dense_core=n)
+    assert ranks == n and tc == T_ref and T == T_ref and np.array_equal(t, t_ref)
