@@ -404,169 +404,177 @@ def serve_bench(args):
             "batched_launches_closed_loop": st_b["batches"]}
 
 
-def run_serve_device(count, max_scale, mode, arrivals=None, window_edges=1 << 31, lookahead=64,
-                     lookahead_edges=1 << 30):
-    """The serving workload with jobs made on the device just before they
-    are submitted (device arrays the server borrows until the job ends): a
-    producer thread generates job k on its own stream, the caller submits it
-    at its arrival offset (arrivals in seconds; None: as soon as the window
-    allows), a waiter thread collects results.  At most `window_edges` raw
-    edges are submitted and not yet finished, which bounds the device copies
-    of queued jobs; the producer runs ahead by at most `lookahead` jobs and
-    `lookahead_edges` raw edges, on a high-priority stream.  Totals only.
-    Returns (totals, latencies s, makespan s, stats, raw edges, client dict:
-    submissions later than 1 ms past their arrival, and seconds spent waiting
-    for the generator, for the window, and in submit calls)."""
+def run_serve_staged(count, max_scale, mode, arrivals=None, buf=None, stream=None, inflight=1):
+    """The serving workload from a staging buffer: the jobs are generated on
+    the device in segments, each copied into `buf` (a uint32 tensor: pinned
+    host memory, or device memory) while the server is idle and outside the
+    timed region, until the next job would not fit; then the segment's jobs
+    are submitted as borrowed slices of `buf` (all at once, or at their
+    arrival offsets in seconds, restarted at each segment), so that each
+    job's latency includes the server's copy of its edges from `buf`.  Only
+    the serving is timed: the makespan is the sum over segments of (last
+    completion - segment start).  Totals only.  Returns (totals, latencies
+    s, makespan s, stats, raw edges, client dict: submissions later than
+    1 ms past their arrival, segments, staging seconds, seconds in submit
+    calls).  `inflight`: the server's batch threads (BATCHED mode), so that
+    one batch's copy and graph build overlap another's counting."""
     import queue
     import threading
 
     import torch
     from paper_2209_04541_b300 import pgabb as P
-    srv = P.pgb_server_create(P.pgb_server_opts_default(mode=mode, per_vertex=0))
-    gen_q = queue.Queue(maxsize=lookahead)
-    done_q = queue.Queue()
-    stop = threading.Event()
-    cond = threading.Condition()
-    state = {"out": 0, "err": None, "ahead": 0}
-    totals, lats, subs = [0] * count, [0.0] * count, [0.0] * count
-    stream = torch.cuda.Stream(priority=-1)
-
-    def producer():
-        try:
-            for i in range(count):
-                if stop.is_set():
-                    return
-                with cond:
-                    cond.wait_for(lambda: stop.is_set() or state["ahead"] <= lookahead_edges)
-                s, d, n = serve_job_device(i, max_scale, stream)
-                stream.synchronize()
-                with cond:
-                    state["ahead"] += int(s.numel())
-                gen_q.put((s, d, n))
-        except BaseException as exc:  # handed to the caller
-            gen_q.put(exc)
-
-    def waiter():
-        try:
-            for _ in range(count):
-                item = done_q.get()
-                if item is None:
-                    return
-                k, jid, m = item
-                totals[k], _, lats[k] = P.pgb_server_wait(srv, jid, 900.0)
-                with cond:
-                    state["out"] -= m
-                    cond.notify_all()
-        except BaseException as exc:
-            state["err"] = exc
-            with cond:
-                cond.notify_all()
-
-    th_p = threading.Thread(target=producer, daemon=True)
-    th_w = threading.Thread(target=waiter, daemon=True)
-    th_p.start()
-    th_w.start()
-    raw = late = 0
-    t_gen = t_win = t_sub = 0.0
-    submitted = []
+    cap = int(buf.numel())
+    stream = stream or torch.cuda.Stream()
+    srv = P.pgb_server_create(P.pgb_server_opts_default(mode=mode, per_vertex=0, max_inflight=inflight))
+    totals, lats = [0] * count, [0.0] * count
+    span = 0.0
+    raw = late = segments = 0
+    t_stage = t_sub = 0.0
+    carry = None
+    pending = []
+    th = q = None
     try:
-        t0 = time.perf_counter()
-        for k in range(count):
-            ta = time.perf_counter()
-            item = gen_q.get()
-            if isinstance(item, BaseException):
-                raise item
-            s, d, n = item
-            m = int(s.numel())
-            raw += m
-            tb = time.perf_counter()
-            t_gen += tb - ta
-            if arrivals is not None:
-                delay = t0 + arrivals[k] - tb
-                if delay > 0:
-                    time.sleep(delay)
-            tc = time.perf_counter()
-            with cond:
-                cond.wait_for(lambda: state["err"] is not None or state["out"] == 0
-                              or state["out"] + m <= window_edges)
-                if state["err"] is not None:
-                    raise state["err"]
-                state["out"] += m
-            subs[k] = time.perf_counter()
-            t_win += subs[k] - tc
-            if arrivals is not None and subs[k] - (t0 + arrivals[k]) > 1e-3:
-                late += 1
-            jid = P.pgb_server_submit(srv, s, d, n, borrow=True)
-            t_sub += time.perf_counter() - subs[k]
-            submitted.append(jid)
-            done_q.put((k, jid, m))
-            del s, d, item
-            with cond:
-                state["ahead"] -= m
-                cond.notify_all()
-        th_w.join()
-        if state["err"] is not None:
-            raise state["err"]
-        span = max(subs[k] + lats[k] for k in range(count)) - t0
+        k = 0
+        while k < count:
+            ts = time.perf_counter()
+            seg, pos = [], 0
+            while k + len(seg) < count:
+                s, d, n = carry if carry is not None else serve_job_device(k + len(seg), max_scale, stream)
+                carry = None
+                m = int(s.numel())
+                if pos + 2 * m > cap:
+                    if not seg:
+                        raise ValueError(f"job {k} ({m} raw edges) does not fit the staging buffer of {cap} words")
+                    carry = (s, d, n)
+                    break
+                with torch.cuda.stream(stream):
+                    buf[pos:pos + m].copy_(s, non_blocking=True)
+                    buf[pos + m:pos + 2 * m].copy_(d, non_blocking=True)
+                seg.append((pos, m, n))
+                pos += 2 * m
+                del s, d
+            stream.synchronize()
+            t_stage += time.perf_counter() - ts
+            q = queue.Queue()
+            err = []
+
+            def waiter(todo=len(seg)):
+                try:
+                    for _ in range(todo):
+                        j, jid = q.get()
+                        if jid is None:
+                            return
+                        totals[j], _, lats[j] = P.pgb_server_wait(srv, jid, 900.0)
+                except BaseException as exc:  # handed to the caller
+                    err.append(exc)
+
+            th = threading.Thread(target=waiter, daemon=True)
+            th.start()
+            base = arrivals[k - 1] if arrivals is not None and k else 0.0
+            subs = []
+            t0 = time.perf_counter()
+            for o, (pos, m, n) in enumerate(seg):
+                if err:
+                    break
+                if arrivals is not None:
+                    due = t0 + arrivals[k + o] - base
+                    delay = due - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                tsub = time.perf_counter()
+                if arrivals is not None and tsub - due > 1e-3:
+                    late += 1
+                jid = P.pgb_server_submit(srv, buf[pos:pos + m], buf[pos + m:pos + 2 * m], n, borrow=True)
+                t_sub += time.perf_counter() - tsub
+                subs.append(tsub)
+                pending.append(jid)
+                q.put((k + o, jid))
+            th.join()
+            th = None
+            if err:
+                raise err[0]
+            pending.clear()
+            span += max(subs[o] + lats[k + o] for o in range(len(seg))) - t0
+            raw += sum(m for _, m, _ in seg)
+            k += len(seg)
+            segments += 1
         stats = P.pgb_server_stats(srv)
     finally:
-        stop.set()
-        with cond:
-            cond.notify_all()
-        if th_w.is_alive():
-            # an error: cancel what is left so that the waiter returns
-            # before the server goes away
-            for jid in submitted:
+        if th is not None:  # an error while submitting: let the waiter return before the server goes
+            for jid in pending:
                 try:
                     P.pgb_server_cancel(srv, jid)
                 except Exception:
                     pass
-            done_q.put(None)
-            th_w.join()
-        while th_p.is_alive():
-            try:
-                gen_q.get(timeout=0.1)
-            except queue.Empty:
-                pass
+            q.put((None, None))
+            th.join()
         P.pgb_server_destroy(srv)
-    client = {"late_submissions": late, "generator_wait_s": round(t_gen, 3), "window_wait_s": round(t_win, 3),
+    client = {"late_submissions": late, "segments": segments, "staging_s": round(t_stage, 3),
               "submit_s": round(t_sub, 3)}
     return totals, lats, span, stats, raw, client
 
 
 def serve_bench_device(args):
     """The serving workload at its stated size (R-MAT scales up to 22, ER and
-    RGG n up to 2^22): jobs made on the device as they are submitted, since
-    the whole mix (tens of G raw edges) fits neither host nor device memory.
-    Capacity (closed loop) and a Poisson load at 0.8x the one-at-a-time
-    capacity, for both modes; totals only."""
+    RGG n up to 2^22).  The whole mix (tens of G raw edges) fits neither host
+    nor device memory, so it is served in segments: each segment's jobs are
+    made on the device and staged (untimed, server idle) in pinned host
+    memory (by default; each job's host-to-device copy is then inside its
+    latency) or in device memory, then served (timed).  Capacity (closed
+    loop) and Poisson loads at the given fractions of the one-at-a-time
+    capacity (0.8 by default), for both modes; totals only."""
+    import torch
     from paper_2209_04541_b300 import pgabb as P
     J, S = args.serve_jobs, args.serve_max_scale
-    run_serve_device(24, S, P.PGB_SERVE_BATCHED)  # warm-up
-    tot_s, _, span_s, _, raw, cl_s = run_serve_device(J, S, P.PGB_SERVE_SERIAL)
-    tot_b, _, span_b, st_b, _, cl_b = run_serve_device(J, S, P.PGB_SERVE_BATCHED)
+    loads = [float(x) for x in args.serve_loads.split(",")]
+    words = args.serve_stage_words
+    if args.serve_input == "host":
+        buf = torch.empty(words, dtype=torch.uint32, pin_memory=True)
+    else:
+        buf = torch.empty(words, dtype=torch.uint32, device="cuda")
+    k = args.serve_inflight
+    run = lambda mode, arrivals=None: run_serve_staged(J, S, mode, arrivals, buf, inflight=k)  # noqa: E731
+    run_serve_staged(24, S, P.PGB_SERVE_BATCHED, None, buf, inflight=k)  # warm-up
+    tot_s, _, span_s, _, raw, cl_s = run(P.PGB_SERVE_SERIAL)
+    tot_b, _, span_b, st_b, _, cl_b = run(P.PGB_SERVE_BATCHED)
     assert tot_s == tot_b, "serial and batched counts differ"
     cap_s, cap_b = J / span_s, J / span_b
-    rate = 0.8 * cap_s
-    rng = np.random.default_rng(12345)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=J))
-    res = {}
-    for name, mode in (("serial", P.PGB_SERVE_SERIAL), ("batched", P.PGB_SERVE_BATCHED)):
-        tot, lat, span, st, _, client = run_serve_device(J, S, mode, arrivals)
-        assert tot == tot_s
-        lat_ms = np.array(lat) * 1e3
-        res[name] = {"jobs_s": J / span, "p50_ms": float(np.percentile(lat_ms, 50)),
-                     "p99_ms": float(np.percentile(lat_ms, 99)), "launches": st["batches"], "client": client}
-    return {"metric": "serve jobs/s and p50/p99 latency", "jobs": J, "raw_edges": raw,
-            "triangles": int(sum(tot_s)),
-            "mix": f"thirds of R-MAT (scale 10-{S}, ef 8-32, Feistel relabelling), ER (n 2^10-2^{S} log-uniform, "
-                   "avg degree 4-64 log-uniform), RGG (avg degree 6); seed = job index; generated on the device, "
-                   "submitted as borrowed device arrays; totals only",
-            "capacity_jobs_s": {"serial": cap_s, "batched": cap_b},
-            "capacity_edges_s": {"serial": raw / span_s, "batched": raw / span_b},
-            "capacity_client": {"serial": cl_s, "batched": cl_b},
-            "poisson_rate_jobs_s": rate, "poisson": res,
-            "batched_launches_closed_loop": st_b["batches"]}
+    sweep = {}
+    for factor in loads:
+        rate = factor * cap_s
+        rng = np.random.default_rng(12345)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=J))
+        res = {}
+        for name, mode in (("serial", P.PGB_SERVE_SERIAL), ("batched", P.PGB_SERVE_BATCHED)):
+            tot, lat, span, st, _, client = run(mode, arrivals)
+            assert tot == tot_s
+            lat_ms = np.array(lat) * 1e3
+            res[name] = {"jobs_s": J / span, "p50_ms": float(np.percentile(lat_ms, 50)),
+                         "p99_ms": float(np.percentile(lat_ms, 99)), "launches": st["batches"],
+                         "client": client}
+        sweep[f"{factor:.2f}"] = {"rate_jobs_s": rate, **res}
+    del buf
+    torch.cuda.empty_cache()
+    head = sweep.get("0.80") or sweep[f"{loads[0]:.2f}"]
+    where = "pinned host memory" if args.serve_input == "host" else "device memory"
+    out = {"metric": "serve jobs/s and p50/p99 latency", "jobs": J, "raw_edges": raw,
+           "triangles": int(sum(tot_s)),
+           "mix": f"thirds of R-MAT (scale 10-{S}, ef 8-32, Feistel relabelling), ER (n 2^10-2^{S} log-uniform, "
+                  "avg degree 4-64 log-uniform), RGG (avg degree 6); seed = job index; made on the device in "
+                  f"segments of up to {words} words, staged in {where} while the server is idle (untimed), "
+                  "then submitted from there as borrowed arrays (the server's copy inside each job's "
+                  "latency); makespan = sum of the segments' serving times; totals only",
+           "inputs": args.serve_input,
+           "batched_threads": k,
+           "capacity_jobs_s": {"serial": cap_s, "batched": cap_b},
+           "capacity_edges_s": {"serial": raw / span_s, "batched": raw / span_b},
+           "capacity_client": {"serial": cl_s, "batched": cl_b},
+           "poisson_rate_jobs_s": head["rate_jobs_s"],
+           "poisson": {k: head[k] for k in ("serial", "batched")},
+           "batched_launches_closed_loop": st_b["batches"]}
+    if len(sweep) > 1:
+        out["poisson_sweep_by_fraction_of_serial_capacity"] = sweep
+    return out
 
 
 def serve_summary(serve):
@@ -890,9 +898,19 @@ def main(argv=None):
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=10000)
     ap.add_argument("--serve-mix", choices=["full", "small"], default="full",
-                    help="full: the serving mix at its stated size (scales up to 22, jobs made on the device and "
-                         "submitted as borrowed device arrays, totals only); small: host-generated jobs up to "
-                         "scale 16, submitted from host memory, per-vertex counts on")
+                    help="full: the serving mix at its stated size (scales up to 22, jobs made on the device in "
+                         "segments, staged (see --serve-input), totals only); small: host-generated "
+                         "jobs up to scale 16, submitted from host memory, per-vertex counts on")
+    ap.add_argument("--serve-input", choices=["host", "device"], default="host",
+                    help="full mix: where the jobs are staged before they are submitted: pinned host memory "
+                         "(each job's host-to-device copy inside its latency) or device memory")
+    ap.add_argument("--serve-stage-words", type=int, default=1 << 33,
+                    help="full mix: staging buffer in uint32 words (2 per raw edge; a segment is the jobs that "
+                         "fit)")
+    ap.add_argument("--serve-inflight", type=int, default=6,
+                    help="full mix: the server's batch threads in BATCHED mode")
+    ap.add_argument("--serve-loads", default="0.8",
+                    help="full mix: comma-separated Poisson loads, as fractions of the one-at-a-time capacity")
     ap.add_argument("--serve-max-scale", type=int, default=0,
                     help="largest R-MAT scale and log2 n of the mix (0: 22 for the full mix, 16 for the small one)")
     ap.add_argument("--no-stream", action="store_true")

@@ -467,7 +467,9 @@ typedef struct pgb_server pgb_server;
 
 typedef struct {
     uint64_t budget_bytes;    /* HBM admission budget (0 = 64 GiB) */
-    uint32_t max_inflight;    /* BATCHED: batch threads (0 = 1, at most 16); SERIAL uses 1 */
+    uint32_t max_inflight;    /* BATCHED: batch threads (0 = 1, at most 16; the default is 4: one
+                                 batch's input copy and graph build overlap others' counting);
+                                 SERIAL uses 1 */
     uint32_t p;               /* parts per dimension of a batch's graph (0 = 8, capped at n) */
     int32_t mode;             /* PGB_SERVE_* */
     int32_t per_vertex;       /* also return per-vertex counts */
@@ -503,16 +505,18 @@ int pgb_server_create(const pgb_server_opts* opts, pgb_server** out);
 int pgb_server_submit(pgb_server* s, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, int mem,
                       uint64_t* job_id);
 
-/* Queue one job on device arrays that the server borrows instead of
- * copying: src/dst (m raw pairs, IDs < n, device memory of the server's
- * device) must be fully written before the call (their producer stream
- * synchronised) and stay valid and unchanged until pgb_server_wait for the
- * job has returned, or the server is destroyed.  The job's batch reads them
- * on its own stream when it starts; submit itself queues no device work, so
- * it does not wait behind kernels already running.  Errors as
- * pgb_server_submit. */
+/* Queue one job on arrays that the server borrows instead of copying:
+ * src/dst (m raw pairs, IDs < n) in device memory of the server's device
+ * (mem = PGB_MEM_DEVICE) or in host memory (PGB_MEM_HOST; pinned memory
+ * makes the batch's copy asynchronous and at the link's speed).  They must
+ * be fully written before the call (a producer stream synchronised) and stay
+ * valid and unchanged until pgb_server_wait for the job has returned, or
+ * the server is destroyed.  The job's batch copies them to the device on its
+ * own stream when it starts (the copy is part of the job's latency); submit
+ * itself queues no device work, so it does not wait behind kernels already
+ * running.  Errors as pgb_server_submit. */
 int pgb_server_submit_borrowed(pgb_server* s, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n,
-                               uint64_t* job_id);
+                               int mem, uint64_t* job_id);
 
 /* Hold (paused != 0) or resume admission: while held, queued jobs stay
  * queued; jobs already admitted continue. */

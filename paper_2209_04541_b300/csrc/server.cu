@@ -92,7 +92,8 @@ struct Job {
     // device input (src then dst, 8 bytes per raw edge), until the batch
     // copies it; allocated and freed stream-ordered
     void* dmem = nullptr;
-    // borrowed device input (pgb_server_submit_borrowed): the caller's arrays
+    // borrowed input (pgb_server_submit_borrowed): the caller's arrays, in
+    // device or host memory
     const uint32_t* bsrc = nullptr;
     const uint32_t* bdst = nullptr;
     Clock::time_point submitted, finished;
@@ -219,8 +220,9 @@ static void count_batch(pgb_server* S, const std::vector<std::shared_ptr<Job>>& 
             Job& J = *batch[j];
             if (!J.m) continue;
             if (J.bsrc) {
-                PGB_CUDA(cudaMemcpyAsync(ds.ptr + eoff[j], J.bsrc, J.m * 4, cudaMemcpyDeviceToDevice, s));
-                PGB_CUDA(cudaMemcpyAsync(dd.ptr + eoff[j], J.bdst, J.m * 4, cudaMemcpyDeviceToDevice, s));
+                // borrowed arrays in device or (ideally pinned) host memory
+                PGB_CUDA(cudaMemcpyAsync(ds.ptr + eoff[j], J.bsrc, J.m * 4, cudaMemcpyDefault, s));
+                PGB_CUDA(cudaMemcpyAsync(dd.ptr + eoff[j], J.bdst, J.m * 4, cudaMemcpyDefault, s));
             } else if (J.dmem) {
                 const uint32_t* in = static_cast<const uint32_t*>(J.dmem);
                 PGB_CUDA(cudaMemcpyAsync(ds.ptr + eoff[j], in, J.m * 4, cudaMemcpyDeviceToDevice, s));
@@ -350,7 +352,7 @@ void pgb_server_opts_default(pgb_server_opts* o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
     o->budget_bytes = 64ull << 30;
-    o->max_inflight = 1;
+    o->max_inflight = 4;
     o->p = 8;
     o->mode = PGB_SERVE_BATCHED;
     o->per_vertex = 1;
@@ -462,8 +464,9 @@ int pgb_server_submit(pgb_server* S, const uint32_t* src, const uint32_t* dst, u
 }
 
 int pgb_server_submit_borrowed(pgb_server* S, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n,
-                               uint64_t* job_id) {
+                               int mem, uint64_t* job_id) {
     return guard([&] {
+        if (mem != PGB_MEM_HOST && mem != PGB_MEM_DEVICE) fail(PGB_E_INVAL, "bad mem kind");
         auto J = new_job(S, src, dst, m, n, job_id);
         J->bsrc = m ? src : nullptr;
         J->bdst = m ? dst : nullptr;

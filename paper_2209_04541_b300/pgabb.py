@@ -142,7 +142,7 @@ _SIGS = {
     "pgb_server_create": (ctypes.c_int, [_VP, ctypes.POINTER(_VP)]),
     "pgb_server_submit": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_uint64)]),
-    "pgb_server_submit_borrowed": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_uint64, ctypes.c_uint32,
+    "pgb_server_submit_borrowed": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
                                                   ctypes.POINTER(ctypes.c_uint64)]),
     "pgb_server_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
     "pgb_server_pause": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -789,9 +789,10 @@ def pgb_server_create(opts: ServerOpts | None = None) -> Server:
 
 
 def pgb_server_submit(srv: Server, src, dst, n: int, borrow: bool = False) -> int:
-    """Queue a job.  ``borrow`` (CUDA tensors only, fully written): the server
-    reads the tensors in place when the job's batch starts instead of copying
-    them at submit; the binding keeps them alive until the job is waited for."""
+    """Queue a job.  ``borrow`` (CUDA tensors, or host tensors/arrays, best
+    pinned; fully written): the server copies them when the job's batch
+    starts instead of at submit; the binding keeps them alive until the job
+    is waited for."""
     ps, ms, ks = _arr(src, np.uint32)
     pd, md, kd = _arr(dst, np.uint32)
     if ms != md:
@@ -799,9 +800,7 @@ def pgb_server_submit(srv: Server, src, dst, n: int, borrow: bool = False) -> in
     m = 0 if ks is None else int(ks.numel() if hasattr(ks, "numel") else ks.size)
     jid = ctypes.c_uint64()
     if borrow:
-        if ms != PGB_MEM_DEVICE and m:
-            raise ValueError("borrow needs CUDA tensors")
-        _check(load().pgb_server_submit_borrowed(srv, ps, pd, m, n, ctypes.byref(jid)),
+        _check(load().pgb_server_submit_borrowed(srv, ps, pd, m, n, ms, ctypes.byref(jid)),
                "pgb_server_submit_borrowed")
         srv.borrowed[int(jid.value)] = (ks, kd)
     else:
@@ -811,7 +810,7 @@ def pgb_server_submit(srv: Server, src, dst, n: int, borrow: bool = False) -> in
 
 
 def pgb_server_submit_borrowed(srv: Server, src, dst, n: int) -> int:
-    """Queue a job on CUDA tensors the server borrows (see pgb_server_submit)."""
+    """Queue a job on arrays the server borrows (see pgb_server_submit)."""
     return pgb_server_submit(srv, src, dst, n, borrow=True)
 
 

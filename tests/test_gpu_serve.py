@@ -209,8 +209,9 @@ def test_serve_benchmark_mix_sample_matches_oracle():
 
 def test_serve_device_inputs_match_host_inputs():
     """Jobs submitted as device arrays (copied and held on the device while
-    queued, or borrowed in place) give the counts of the same jobs submitted
-    from host memory, in both modes."""
+    queued, or borrowed in place) or as borrowed host arrays (pinned and
+    pageable) give the counts of the same jobs submitted from host memory, in
+    both modes."""
     jobs = job_mix(5)
     want = expected(jobs)
     for mode in (P.PGB_SERVE_BATCHED, P.PGB_SERVE_SERIAL):
@@ -218,11 +219,17 @@ def test_serve_device_inputs_match_host_inputs():
         try:
             ids = []
             for k, (s, d, n) in enumerate(jobs):
-                if k % 3:  # two of three jobs from device memory: copied, then borrowed
+                kind = k % 5  # host copied, device copied, device borrowed, pinned and pageable host borrowed
+                if kind in (1, 2):
                     s = torch.from_numpy(np.ascontiguousarray(s)).cuda()
                     d = torch.from_numpy(np.ascontiguousarray(d)).cuda()
                     torch.cuda.synchronize()
-                ids.append(P.pgb_server_submit(srv, s, d, n, borrow=k % 3 == 2))
+                elif kind == 3:
+                    s = torch.from_numpy(np.ascontiguousarray(s)).pin_memory()
+                    d = torch.from_numpy(np.ascontiguousarray(d)).pin_memory()
+                elif kind == 4:
+                    s, d = np.array(s, np.uint32), np.array(d, np.uint32)
+                ids.append(P.pgb_server_submit(srv, s, d, n, borrow=kind >= 2))
                 del s, d
             torch.cuda.synchronize()
             res = [P.pgb_server_wait(srv, j, 120.0, per_vertex=True) for j in ids]
@@ -302,10 +309,13 @@ def test_serve_full_size_mix_sample_matches_oracle_goldens():
     torch.cuda.empty_cache()
 
 
-def test_bench_device_serve_client_matches_oracle():
-    """bench.py's full-size serve client (device generation, windowed closed
-    loop and timed arrivals) on a small mix: every total equals the oracle's
-    on the host-generated job, in both modes."""
+def test_bench_staged_serve_client_matches_oracle():
+    """bench.py's full-size serve client (jobs made on the device in
+    segments, staged in pinned host memory or in device memory, submitted
+    from there in a closed loop or at timed arrivals) on a small mix with a
+    staging buffer of 2^18 words (one of the largest jobs, 2^12 x 32 raw
+    edges, takes 2^18), so that it runs in many segments: every total equals the
+    oracle's on the host-generated job, in both modes."""
     import os
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
@@ -313,9 +323,17 @@ def test_bench_device_serve_client_matches_oracle():
 
     count, scale = 40, 12
     want = [oracle.tc_node_iterator(oracle.clean(*graphgen.serve_job(i, scale)), False)[0] for i in range(count)]
-    for mode in (P.PGB_SERVE_SERIAL, P.PGB_SERVE_BATCHED):
-        tot, lat, span, st, raw, client = bench.run_serve_device(count, scale, mode, window_edges=1 << 20)
-        assert tot == want and span > 0 and all(x > 0 for x in lat)
     arrivals = np.cumsum(np.full(count, 0.002))
-    tot, *_ = bench.run_serve_device(count, scale, P.PGB_SERVE_BATCHED, arrivals)
-    assert tot == want
+    for where in ("host", "device"):
+        words = 1 << 18
+        buf = (torch.empty(words, dtype=torch.uint32, pin_memory=True) if where == "host"
+               else torch.empty(words, dtype=torch.uint32, device="cuda"))
+        for mode in (P.PGB_SERVE_SERIAL, P.PGB_SERVE_BATCHED):
+            tot, lat, span, st, raw, client = bench.run_serve_staged(count, scale, mode, None, buf)
+            assert tot == want and span > 0 and all(x > 0 for x in lat)
+            assert client["segments"] >= 8
+        tot, *_ = bench.run_serve_staged(count, scale, P.PGB_SERVE_BATCHED, arrivals, buf)
+        assert tot == want
+    with pytest.raises(ValueError):  # a job larger than the buffer
+        bench.run_serve_staged(count, scale, P.PGB_SERVE_BATCHED, None, torch.empty(1000, dtype=torch.uint32,
+                                                                                     pin_memory=True))
