@@ -423,8 +423,11 @@ def run_serve_staged(count, max_scale, mode, arrivals=None, buf=None, stream=Non
 
     import torch
     from paper_2209_04541_b300 import pgabb as P
+    import collections
+
     cap = int(buf.numel())
     stream = stream or torch.cuda.Stream()
+    copy_stream = torch.cuda.Stream()
     srv = P.pgb_server_create(P.pgb_server_opts_default(mode=mode, per_vertex=0, max_inflight=inflight))
     totals, lats = [0] * count, [0.0] * count
     span = 0.0
@@ -438,6 +441,7 @@ def run_serve_staged(count, max_scale, mode, arrivals=None, buf=None, stream=Non
         while k < count:
             ts = time.perf_counter()
             seg, pos = [], 0
+            flight, flight_edges = collections.deque(), 0  # copies not yet known to be done
             while k + len(seg) < count:
                 s, d, n = carry if carry is not None else serve_job_device(k + len(seg), max_scale, stream)
                 carry = None
@@ -447,12 +451,26 @@ def run_serve_staged(count, max_scale, mode, arrivals=None, buf=None, stream=Non
                         raise ValueError(f"job {k} ({m} raw edges) does not fit the staging buffer of {cap} words")
                     carry = (s, d, n)
                     break
-                with torch.cuda.stream(stream):
+                # the copy overlaps the next job's generation; at most 2^28
+                # raw edges of generated arrays wait for their copies
+                copy_stream.wait_stream(stream)
+                with torch.cuda.stream(copy_stream):
                     buf[pos:pos + m].copy_(s, non_blocking=True)
                     buf[pos + m:pos + 2 * m].copy_(d, non_blocking=True)
+                s.record_stream(copy_stream)
+                d.record_stream(copy_stream)
+                ev = torch.cuda.Event()
+                ev.record(copy_stream)
+                flight.append((ev, m))
+                flight_edges += m
+                while flight_edges > 1 << 28:
+                    e, mm = flight.popleft()
+                    e.synchronize()
+                    flight_edges -= mm
                 seg.append((pos, m, n))
                 pos += 2 * m
                 del s, d
+            copy_stream.synchronize()
             stream.synchronize()
             t_stage += time.perf_counter() - ts
             q = queue.Queue()

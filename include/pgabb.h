@@ -467,8 +467,9 @@ typedef struct pgb_server pgb_server;
 
 typedef struct {
     uint64_t budget_bytes;    /* HBM admission budget (0 = 64 GiB) */
-    uint32_t max_inflight;    /* BATCHED: batch threads (0 = 1, at most 16; the default is 4: one
-                                 batch's input copy and graph build overlap others' counting);
+    uint32_t max_inflight;    /* BATCHED: batch threads (0 = 1, at most 16; the default is 1, best
+                                 for small jobs; with large jobs from host memory, more threads
+                                 overlap one batch's input copy and build with others' counting);
                                  SERIAL uses 1 */
     uint32_t p;               /* parts per dimension of a batch's graph (0 = 8, capped at n) */
     int32_t mode;             /* PGB_SERVE_* */

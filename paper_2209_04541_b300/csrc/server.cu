@@ -352,7 +352,7 @@ void pgb_server_opts_default(pgb_server_opts* o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
     o->budget_bytes = 64ull << 30;
-    o->max_inflight = 4;
+    o->max_inflight = 1;
     o->p = 8;
     o->mode = PGB_SERVE_BATCHED;
     o->per_vertex = 1;

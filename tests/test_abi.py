@@ -79,7 +79,7 @@ def test_server_opts_and_admission_estimate():
     lib = pgabb.load(register_torch_allocator=False)
     o = pgabb.pgb_server_opts_default()
     assert o.mode == pgabb.PGB_SERVE_BATCHED and o.budget_bytes == 64 << 30
-    assert o.max_inflight == 4 and o.per_vertex == 1 and o.max_batch_jobs == 256 and o.p == 8
+    assert o.max_inflight == 1 and o.per_vertex == 1 and o.max_batch_jobs == 256 and o.p == 8
     assert ctypes.sizeof(pgabb.ServerOpts) == 64 and ctypes.sizeof(pgabb.ServerInfo) == 64
     est = pgabb.pgb_server_job_bytes
     assert 0 < est(0, 0) < est(10, 10) < est(1000, 10) < est(1000, 100000)
