@@ -28,6 +28,7 @@
 #include <cub/device/device_scan.cuh>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.cuh"
 #include "tc_hash.cuh"
@@ -41,6 +42,7 @@ constexpr uint32_t kInChunkDefault = 4096;  // in-edges per item unless the call
 // most one hit per in-edge of the item and is 16 bits wide.
 constexpr uint32_t kInChunkMax = 65535;
 constexpr uint32_t kEmpty = 0xffffffffu;
+constexpr int kModeDense = 0, kModeBitmap = 1, kModeTable = 2;  // an item's lookup structure
 constexpr unsigned kFullMask = 0xffffffffu;
 // Table keys per work item of a CTA shape (tables stay at most half full),
 // and the widest third-vertex range it holds as a bitmap.
@@ -460,146 +462,154 @@ __global__ void __launch_bounds__(T, 1024 / T)
         // R-MAT scale 24 with 256 threads, 3.5% at scale 27 with 512); the
         // 128-thread shape keeps 32 consecutive in-edges per batch (strided
         // was 3.4% slower at scale 23).
-        constexpr bool kStrided = T >= 256;
-        const uint32_t nb = (I.in_end - I.in_begin + 31) >> 5;
-        for (;;) {
-            uint32_t b = 0;
-            if (lane == 0) b = atomicAdd(&s_next, 1u);
-            b = __shfl_sync(kFullMask, b, 0);
-            if (b >= nb) break;
-            const uint32_t idx = kStrided ? I.in_begin + b + lane * nb : I.in_begin + b * 32 + lane;
-            uint32_t sb = 0, sl = 0, vbit = 0, e = 0;
-            if (idx < I.in_end) {
-                const unsigned long long r = __ldg(G.xr + idx);
-                uint32_t xb = (uint32_t)r, xe = (uint32_t)(r >> 32);
-                e = xb - 1;
-                // a singleton item's in-edges all end at v0; a group's need
-                // the head read back to pick the member bit
-                const uint32_t v = single ? I.v0 : __ldg(G.colu + (e - G.ubase));
-                vbit = 1u << (v - I.v0);
-                if ((vmask & vbit) && e < G.core_e0) {
-                    if (I.clip) {
-                        xb = hlower_bound_b(G.colu, G.ubase, xb, xe, I.lo);
-                        xe = hlower_bound_b(G.colu, G.ubase, xb, xe, I.hi);
+        // The probe loop, compiled once per lookup mode (the mode is fixed for
+        // the item), so that no lookup tests it.
+        auto probe = [&](auto mode) {
+            constexpr int M = decltype(mode)::value;
+            constexpr bool kStrided = T >= 256;
+            const uint32_t nb = (I.in_end - I.in_begin + 31) >> 5;
+            for (;;) {
+                uint32_t b = 0;
+                if (lane == 0) b = atomicAdd(&s_next, 1u);
+                b = __shfl_sync(kFullMask, b, 0);
+                if (b >= nb) break;
+                const uint32_t idx = kStrided ? I.in_begin + b + lane * nb : I.in_begin + b * 32 + lane;
+                uint32_t sb = 0, sl = 0, vbit = 0, e = 0;
+                if (idx < I.in_end) {
+                    const unsigned long long r = __ldg(G.xr + idx);
+                    uint32_t xb = (uint32_t)r, xe = (uint32_t)(r >> 32);
+                    e = xb - 1;
+                    // a singleton item's in-edges all end at v0; a group's need
+                    // the head read back to pick the member bit
+                    const uint32_t v = single ? I.v0 : __ldg(G.colu + (e - G.ubase));
+                    vbit = 1u << (v - I.v0);
+                    if ((vmask & vbit) && e < G.core_e0) {
+                        if (I.clip) {
+                            xb = hlower_bound_b(G.colu, G.ubase, xb, xe, I.lo);
+                            xe = hlower_bound_b(G.colu, G.ubase, xb, xe, I.hi);
+                        }
+                        sb = xb;
+                        sl = xe - xb;
                     }
-                    sb = xb;
-                    sl = xe - xb;
                 }
-            }
-            // The lists of the batch, cut into aligned 8-entry pairs of quads,
-            // form one sequence that the lanes share: each lane takes
-            // kPairSlots pairs per step with one 32-byte load each, so many
-            // loads per lane are in flight across in-edge boundaries, and the
-            // owner lookup is paid once per 8 entries.
-            const uint32_t qa = sb >> 3;
-            const uint32_t nq = sl ? ((sb + sl + 7) >> 3) - qa : 0;
-            uint32_t incl = nq;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(kFullMask, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const uint32_t total = __shfl_sync(kFullMask, incl, 31);
-            const uint32_t excl = incl - nq;
-            const uint32_t send = sb + sl;
-            uint32_t tally = 0, tally_own = 0;  // per-vertex runs: this lane's hits for owner tally_own
-            constexpr int U = kPairSlots;
-            for (uint32_t r0 = 0; r0 < total; r0 += 32 * U) {
-                uint4 qv[U], qw[U];
-                uint32_t qb[U], lo_[U], hi_[U], bits[U], own[U];
-#pragma unroll
-                for (int j = 0; j < U; ++j) {
-                    const uint32_t f = r0 + 32 * j + lane;
-                    int o = 0;
-#pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        uint32_t ex = __shfl_sync(kFullMask, excl, o + step);
-                        if (ex <= f) o += step;
-                    }
-                    const uint32_t o_ex = __shfl_sync(kFullMask, excl, o);
-                    lo_[j] = __shfl_sync(kFullMask, sb, o);
-                    hi_[j] = __shfl_sync(kFullMask, send, o);
-                    bits[j] = __shfl_sync(kFullMask, vbit, o);
-                    own[j] = o;
-                    qb[j] = 8 * ((lo_[j] >> 3) + (f - o_ex));
-                    if (f < total) {
-                        // one 256-bit read-only load per pair (32-byte aligned:
-                        // qb and ubase are multiples of 8, colu is checked at launch)
-                        const uint32_t* a = G.colu + (qb[j] - G.ubase);
-                        asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                            : "=r"(qv[j].x), "=r"(qv[j].y), "=r"(qv[j].z), "=r"(qv[j].w), "=r"(qw[j].x),
-                              "=r"(qw[j].y), "=r"(qw[j].z), "=r"(qw[j].w)
-                            : "l"(a));
-                    } else {
-                        qv[j] = qw[j] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
-                    }
-                    if (f >= total) hi_[j] = 0;
+                // The lists of the batch, cut into aligned 8-entry pairs of quads,
+                // form one sequence that the lanes share: each lane takes
+                // kPairSlots pairs per step with one 32-byte load each, so many
+                // loads per lane are in flight across in-edge boundaries, and the
+                // owner lookup is paid once per 8 entries.
+                const uint32_t qa = sb >> 3;
+                const uint32_t nq = sl ? ((sb + sl + 7) >> 3) - qa : 0;
+                uint32_t incl = nq;
+    #pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(kFullMask, incl, o);
+                    if (lane >= o) incl += y;
                 }
-#pragma unroll
-                for (int j = 0; j < U; ++j) {
-                    const uint32_t xv[8] = {qv[j].x, qv[j].y, qv[j].z, qv[j].w, qw[j].x, qw[j].y, qw[j].z, qw[j].w};
-                    uint32_t h4 = 0;
-                    // entries of the pair inside the owner's range [lo, hi)
-                    // as an 8-bit mask (qb > lo - 8 for every slot; a slot
-                    // past the batch has hi = 0 and an empty mask)
-                    const uint32_t va = lo_[j] > qb[j] ? lo_[j] - qb[j] : 0u;
-                    const uint32_t vb = hi_[j] < qb[j] + 8 ? min(qb[j] + 8 - hi_[j], 8u) : 0u;
-                    const uint32_t vm = (0xFFu << va) & (0xFFu >> vb);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        if (!((vm >> i) & 1u)) continue;
-                        const uint32_t x = xv[i];
-                        bool hit;
-                        uint32_t h = 0;
-                        if (dense) {
-                            const uint32_t r1 = dense16[x - rlo];
-                            hit = r1 != 0u;
-                            h = r1 - 1u;
-                        } else if (bitmap) {
-                            const uint32_t d = x - rlo;
-                            const uint32_t word = regA[d >> 5];
-                            hit = (word >> (d & 31)) & 1u;
-                            // counter index = rank of x in v's sorted list
-                            if (PV && hit) h = pre[d >> 5] + __popc(word & ((1u << (d & 31)) - 1u));
+                const uint32_t total = __shfl_sync(kFullMask, incl, 31);
+                const uint32_t excl = incl - nq;
+                const uint32_t send = sb + sl;
+                uint32_t tally = 0, tally_own = 0;  // per-vertex runs: this lane's hits for owner tally_own
+                constexpr int U = kPairSlots;
+                for (uint32_t r0 = 0; r0 < total; r0 += 32 * U) {
+                    uint4 qv[U], qw[U];
+                    uint32_t qb[U], lo_[U], hi_[U], bits[U], own[U];
+    #pragma unroll
+                    for (int j = 0; j < U; ++j) {
+                        const uint32_t f = r0 + 32 * j + lane;
+                        int o = 0;
+    #pragma unroll
+                        for (int step = 16; step >= 1; step >>= 1) {
+                            uint32_t ex = __shfl_sync(kFullMask, excl, o + step);
+                            if (ex <= f) o += step;
+                        }
+                        const uint32_t o_ex = __shfl_sync(kFullMask, excl, o);
+                        lo_[j] = __shfl_sync(kFullMask, sb, o);
+                        hi_[j] = __shfl_sync(kFullMask, send, o);
+                        bits[j] = __shfl_sync(kFullMask, vbit, o);
+                        own[j] = o;
+                        qb[j] = 8 * ((lo_[j] >> 3) + (f - o_ex));
+                        if (f < total) {
+                            // one 256-bit read-only load per pair (32-byte aligned:
+                            // qb and ubase are multiples of 8, colu is checked at launch)
+                            const uint32_t* a = G.colu + (qb[j] - G.ubase);
+                            asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                                : "=r"(qv[j].x), "=r"(qv[j].y), "=r"(qv[j].z), "=r"(qv[j].w), "=r"(qw[j].x),
+                                  "=r"(qw[j].y), "=r"(qw[j].z), "=r"(qw[j].w)
+                                : "l"(a));
                         } else {
-                            h = table_find(keys, x, L);
-                            hit = h != kEmpty && (single || (masks[h] & bits[j]));
+                            qv[j] = qw[j] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
                         }
-                        if (hit) {
-                            ++h4;
-                            if (PV) atomicAdd(&cnts[h >> 1], 1u << ((h & 1) << 4));
+                        if (f >= total) hi_[j] = 0;
+                    }
+    #pragma unroll
+                    for (int j = 0; j < U; ++j) {
+                        const uint32_t xv[8] = {qv[j].x, qv[j].y, qv[j].z, qv[j].w, qw[j].x, qw[j].y, qw[j].z, qw[j].w};
+                        uint32_t h4 = 0;
+                        // entries of the pair inside the owner's range [lo, hi)
+                        // as an 8-bit mask (qb > lo - 8 for every slot; a slot
+                        // past the batch has hi = 0 and an empty mask)
+                        const uint32_t va = lo_[j] > qb[j] ? lo_[j] - qb[j] : 0u;
+                        const uint32_t vb = hi_[j] < qb[j] + 8 ? min(qb[j] + 8 - hi_[j], 8u) : 0u;
+                        const uint32_t vm = (0xFFu << va) & (0xFFu >> vb);
+    #pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            if (!((vm >> i) & 1u)) continue;
+                            const uint32_t x = xv[i];
+                            bool hit;
+                            uint32_t h = 0;
+                            if constexpr (M == kModeDense) {
+                                const uint32_t r1 = dense16[x - rlo];
+                                hit = r1 != 0u;
+                                h = r1 - 1u;
+                            } else if constexpr (M == kModeBitmap) {
+                                const uint32_t d = x - rlo;
+                                const uint32_t word = regA[d >> 5];
+                                hit = (word >> (d & 31)) & 1u;
+                                // counter index = rank of x in v's sorted list
+                                if (PV && hit) h = pre[d >> 5] + __popc(word & ((1u << (d & 31)) - 1u));
+                            } else {
+                                h = table_find(keys, x, L);
+                                hit = h != kEmpty && (single || (masks[h] & bits[j]));
+                            }
+                            if (hit) {
+                                ++h4;
+                                if (PV) atomicAdd(&cnts[h >> 1], 1u << ((h & 1) << 4));
+                            }
+                        }
+                        cnt += h4;
+                        if (PV) {
+                            // per-in-edge tally: a lane's slots belong to
+                            // non-decreasing owners, so it sums its hits in a
+                            // register and adds them to the owner's shared slot
+                            // only when its owner changes
+                            if (own[j] != tally_own) {
+                                if (tally) atomicAdd(&s_edge[warp][tally_own], tally);
+                                tally_own = own[j];
+                                tally = 0;
+                            }
+                            tally += h4;
                         }
                     }
-                    cnt += h4;
-                    if (PV) {
-                        // per-in-edge tally: a lane's slots belong to
-                        // non-decreasing owners, so it sums its hits in a
-                        // register and adds them to the owner's shared slot
-                        // only when its owner changes
-                        if (own[j] != tally_own) {
-                            if (tally) atomicAdd(&s_edge[warp][tally_own], tally);
-                            tally_own = own[j];
-                            tally = 0;
-                        }
-                        tally += h4;
+                }
+                if (PV) {
+                    if (tally) atomicAdd(&s_edge[warp][tally_own], tally);
+                    __syncwarp();
+                    const uint32_t c = s_edge[warp][lane];
+                    if (c) {
+                        s_edge[warp][lane] = 0;
+                        // the tail u: from the streamed per-in-edge tails when the
+                        // row index is not resident, else from the row index
+                        const uint32_t u = G.itail ? __ldg(G.itail + idx) : __ldg(G.rowidx + e);
+                        atomicAdd(G.tv + u, (unsigned long long)c);
+                        atomicAdd(&s_vcnt[31 - __clz(vbit)], c);
                     }
+                    __syncwarp();
                 }
             }
-            if (PV) {
-                if (tally) atomicAdd(&s_edge[warp][tally_own], tally);
-                __syncwarp();
-                const uint32_t c = s_edge[warp][lane];
-                if (c) {
-                    s_edge[warp][lane] = 0;
-                    // the tail u: from the streamed per-in-edge tails when the
-                    // row index is not resident, else from the row index
-                    const uint32_t u = G.itail ? __ldg(G.itail + idx) : __ldg(G.rowidx + e);
-                    atomicAdd(G.tv + u, (unsigned long long)c);
-                    atomicAdd(&s_vcnt[31 - __clz(vbit)], c);
-                }
-                __syncwarp();
-            }
-        }
+        };
+        if (dense) probe(std::integral_constant<int, kModeDense>{});
+        else if (bitmap) probe(std::integral_constant<int, kModeBitmap>{});
+        else probe(std::integral_constant<int, kModeTable>{});
         // the item's count goes to the CTA's shared accumulator
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFullMask, cnt, o);
