@@ -337,8 +337,8 @@ typedef struct {
                               offloaded ones; larger than 65,535 counts as
                               65,535) */
     uint32_t hash_threads; /* hash variant: threads per CTA, 128 (8 CTAs per
-                              SM, bitmaps over up to 131,072 ranks), 256 (4
-                              per SM, 262,144 ranks) or 512 (2 per SM,
+                              SM, bitmaps over fewer than 131,072 ranks), 256
+                              (4 per SM, 262,144 ranks) or 512 (2 per SM,
                               524,288 ranks); 0 = autotuned by vertex count:
                               128 below 2^24 vertices, 256 below 2^26, else
                               512 (128 always for column-offloaded blocks) */

@@ -45,7 +45,8 @@ constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr int kModeDense = 0, kModeBitmap = 1, kModeTable = 2;  // an item's lookup structure
 constexpr unsigned kFullMask = 0xffffffffu;
 // Table keys per work item of a CTA shape (tables stay at most half full),
-// and the widest third-vertex range it holds as a bitmap.
+// and its bitmap bits (a third-vertex range narrower than that is held as a
+// bitmap).
 constexpr uint32_t key_capacity(int threads) { return 32u * threads / 4; }
 constexpr uint32_t bitmap_range(int threads) { return 32u * 32u * threads; }
 
@@ -172,7 +173,7 @@ __device__ __forceinline__ WindowInfo window_info(const ItemSpace& sp, uint32_t 
     W.run_len = W.run_mask = W.run_keys = 0;
     W.mine = 0;
     if (W.group || W.keys == 0) return W;
-    const bool light = W.act && W.dp <= sp.keycap && W.dm <= in_chunk && sp.n - W.v - 1 > sp.bitmap_bits;
+    const bool light = W.act && W.dp <= sp.keycap && W.dm <= in_chunk && sp.n - W.v - 1 >= sp.bitmap_bits;
     const bool heavy = W.act && !light;
     if (heavy) W.mine = ((W.dm + in_chunk - 1) / in_chunk) * ((W.dp + sp.keycap - 1) / sp.keycap);
     // the same greedy scan in every lane (uniform), each keeping its own run
@@ -299,8 +300,8 @@ __global__ void k_items_emit(const ItemSpace sp, uint32_t in_chunk, const uint32
 }
 
 // Three CTA shapes: T = 128 threads (8 CTAs per SM, a 16 KB region A:
-// bitmaps over up to 131,072 ranks), T = 256 (4 CTAs per SM, 32 KB: 262,144
-// ranks) and T = 512 (2 CTAs per SM, 64 KB: 524,288 ranks).  Region A holds
+// bitmaps over fewer than 131,072 ranks), T = 256 (4 CTAs per SM, 32 KB:
+// 262,144 ranks) and T = 512 (2 CTAs per SM, 64 KB: 524,288 ranks).  Region A holds
 // the bitmap or the table keys and masks (half of it each: 16T slots, so 8T
 // keys per item); thread t owns words [32t, 32t + 32) of it in the bitmap
 // prefix scan.
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(T, 1024 / T)
               RunCtl* __restrict__ ctl) {
     extern __shared__ uint32_t hsm[];
     // Region A: the bitmap of a bitmap-mode item, the 16-bit rank entries of
-    // a dense-mode item (ranges of at most 2 x region A words), or the keys
+    // a dense-mode item (ranges narrower than 2 x region A words), or the keys
     // and member masks of a hash-mode item; all zero between items.  Region B
     // (per-vertex counts only) holds 16-bit counters, two per word (a counter
     // counts at most one hit per in-edge of the item): in hash mode one per
@@ -321,9 +322,9 @@ __global__ void __launch_bounds__(T, 1024 / T)
     uint32_t* regA = hsm;
     constexpr int kHThreads = T, kHWarps = T / 32;
     constexpr uint32_t kRegionA = 32u * T;           // words
-    constexpr uint32_t kBitmapBits = 32u * kRegionA;  // widest third-vertex range held as a bitmap
+    constexpr uint32_t kBitmapBits = 32u * kRegionA;  // third-vertex ranges narrower than this: a bitmap
     constexpr uint32_t kMaxSlots = kRegionA / 2;     // table slots (keys, then member masks)
-    constexpr uint32_t kDenseRanks = 2u * kRegionA;   // widest range held as 16-bit rank entries
+    constexpr uint32_t kDenseRanks = 2u * kRegionA;   // narrower ranges: 16-bit rank entries
     uint32_t* regB = hsm + kRegionA;
     __shared__ uint32_t s_wsum[kHWarps];
     __shared__ VItem s_it, s_itn;      // current item and the next one (prefetched)
@@ -374,12 +375,17 @@ __global__ void __launch_bounds__(T, 1024 / T)
         // exceed v, so its range starts at v + 1
         const uint32_t rlo = I.clip ? I.lo : (single ? I.v0 + 1 : 0);
         const uint32_t rhi = I.clip ? I.hi : G.n;
-        const bool bitmap = single && rhi - rlo <= kBitmapBits;
-        // a range of at most kDenseRanks ranks (the top of the degree order:
+        // A bitmap or dense range is strictly narrower than region A holds,
+        // so the slot just past it (at span) stays zero: a lookup of an
+        // entry outside its in-edge's row reads that slot instead of taking
+        // a branch.
+        const bool bitmap = single && rhi - rlo < kBitmapBits;
+        // a range narrower than kDenseRanks ranks (the top of the degree order:
         // most lookups at R-MAT scale) is held densely instead: one 16-bit
         // entry per rank, the key's rank in the list plus one (0: absent),
         // so a lookup is one shared load giving the hit and its counter
-        const bool dense = bitmap && rhi - rlo <= kDenseRanks;
+        const bool dense = bitmap && rhi - rlo < kDenseRanks;
+        const uint32_t span = rhi - rlo;
         // a singleton's (clipped) list; its row bounds came with the item
         uint32_t rb = 0, re = 0;
         if (single) {
@@ -553,16 +559,20 @@ __global__ void __launch_bounds__(T, 1024 / T)
                         const uint32_t vm = (0xFFu << va) & (0xFFu >> vb);
     #pragma unroll
                         for (int i = 0; i < 8; ++i) {
-                            if (!((vm >> i) & 1u)) continue;
+                            const bool in = (vm >> i) & 1u;
+                            if constexpr (M == kModeTable) {
+                                if (!in) continue;
+                            }
                             const uint32_t x = xv[i];
                             bool hit;
                             uint32_t h = 0;
                             if constexpr (M == kModeDense) {
-                                const uint32_t r1 = dense16[x - rlo];
+                                // an entry outside the in-edge's row reads the zero slot at span
+                                const uint32_t r1 = dense16[in ? x - rlo : span];
                                 hit = r1 != 0u;
                                 h = r1 - 1u;
                             } else if constexpr (M == kModeBitmap) {
-                                const uint32_t d = x - rlo;
+                                const uint32_t d = in ? x - rlo : span;
                                 const uint32_t word = regA[d >> 5];
                                 hit = (word >> (d & 31)) & 1u;
                                 // counter index = rank of x in v's sorted list

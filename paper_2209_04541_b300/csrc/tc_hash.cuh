@@ -29,7 +29,7 @@ struct ItemSpace {
     const uint32_t* col;
     uint32_t cbase, vbase, w0, nwin, n;
     uint32_t keycap;       // table keys per item: 1024 (fits both CTA shapes) or 2048 (256 threads only)
-    uint32_t bitmap_bits;  // widest range a singleton holds as a bitmap (such vertices are never grouped)
+    uint32_t bitmap_bits;  // a singleton range narrower than this is a bitmap (such vertices are never grouped)
     // optional filter: only heads v whose part j (cuts[j] <= v < cuts[j+1])
     // has part_hash[j] != 0 get work items (null: every head)
     const uint8_t* part_hash = nullptr;
