@@ -21,7 +21,8 @@ partitioning are inside the timed step).
            The second formula is also given for the middle-vertex kernel,
            as ``edgewise_bound``: it charges a re-read of v's list per
            in-edge, which that kernel serves from shared memory, so it is a
-           bound for the edge-wise method, not a bandwidth fraction.
+           bound for the edge-wise method, not a bandwidth fraction; so is
+           ``merge_bytes``, both lists read per oriented edge.
 ``cpu_baseline``: the oracle on the same workload: its clean, degree order
            and orientation single-threaded in full, and its forward count
            on a stride sample of the rows with every host core (OpenMP
@@ -1007,6 +1008,9 @@ def main(argv=None):
             pv_ = P.pgb_tc_result_part_variants(r)
             info["parts_by_kernel"] = {"hash": int((pv_ == P.PGB_VAR_HASH).sum()),
                                        "edgewise": int(((pv_ == P.PGB_VAR_BSEARCH) | (pv_ == P.PGB_VAR_MERGE)).sum())}
+            # sum_u outdeg(u)^2 from the oriented offsets (first warm-up step only)
+            outdeg = np.diff(P.pgb_blocks_export(b, P.PGB_EXPORT_ROWPTR)).astype(np.uint64)
+            info["sum_outdeg_sq"] = int((outdeg * outdeg).sum())
         r.free()
         b.free()
         return T, kms
@@ -1092,6 +1096,13 @@ def main(argv=None):
                     "v's list per in-edge; this kernel holds that list in shared memory, so this is not a "
                     "bandwidth fraction",
             "alg_bytes": info["alg_bytes"], "achieved": ew_achieved, "ratio_to_peak": ew_achieved / peak}
+        # the per-edge merge's bytes: both partial lists read for every
+        # oriented edge (u, v), 4 sum_u outdeg(u)^2 + 4 sum_v indeg(v) outdeg(v)
+        mb = 4 * (info["sum_outdeg_sq"] + info["wedges"])
+        roofline["merge_bytes"] = {
+            "note": "4 sum over oriented edges (u,v) of (outdeg(u) + outdeg(v)): both lists read per edge, as a "
+                    "merge would; not a bandwidth fraction for this kernel",
+            "bytes": mb, "achieved": mb / (kernel_ms / 1e3) / 1e9, "ratio_to_peak": mb / (kernel_ms / 1e3) / 1e9 / peak}
 
     wall["headline"] = round(time.perf_counter() - t_sec, 1)
     t_sec = time.perf_counter()
