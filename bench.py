@@ -901,7 +901,9 @@ def main(argv=None):
     ap.add_argument("--mode", choices=["persistent", "plain"], default="persistent")
     ap.add_argument("--order", choices=["weight", "locality"], default="weight")
     ap.add_argument("--variant", choices=["auto", "bsearch", "merge", "hash"], default="auto")
-    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="pgb_tc_opts.chunk_edges: edges per chunk of the binary-search kernel AND in-edges per item "
+                         "of the hash kernel (0 = each kernel's own default)")
     ap.add_argument("--per-vertex", type=int, default=1)
     ap.add_argument("--hash-threads", type=int, default=0, choices=[0, 128, 256, 512],
                     help="CTA shape of the hash kernel (0 = autotuned)")

@@ -332,10 +332,12 @@ typedef struct {
                               slots cannot hold the largest work item, gives
                               PGB_E_BUDGET.  Ignored for resident blocks. */
     uint32_t chunk_edges;  /* PERSISTENT: binary-search variant: edges per
-                              dequeued chunk; hash variant: in-edges per work
-                              item (0 = 16,384 for resident blocks, 4,096 for
-                              offloaded ones; larger than 65,535 counts as
-                              65,535) */
+                              dequeued chunk (0 = 64); hash variant: in-edges
+                              per work item (0 = 16,384 for resident blocks,
+                              4,096 for offloaded ones; larger than 65,535
+                              counts as 65,535).  A per-part run uses both
+                              kernels, and a value set here applies to both:
+                              leave it 0 unless one variant is forced */
     uint32_t hash_threads; /* hash variant: threads per CTA, 128 (8 CTAs per
                               SM, bitmaps over fewer than 131,072 ranks), 256
                               (4 per SM, 262,144 ranks) or 512 (2 per SM,
