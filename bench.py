@@ -951,6 +951,14 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.serve_jobs < 1 or args.serve_inflight < 1 or args.serve_stage_words < 2:
+        ap.error("--serve-jobs and --serve-inflight must be >= 1, --serve-stage-words >= 2")
+    try:
+        loads = [float(x) for x in args.serve_loads.split(",")]
+    except ValueError:
+        loads = []
+    if not loads or not all(0.0 < x < 10.0 for x in loads):
+        ap.error("--serve-loads takes comma-separated positive fractions, e.g. 0.5,0.8,0.95")
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -78,8 +78,9 @@ def test_reference_arm_runs_on_rank0_only(monkeypatch):
     assert line["e2e"]["h2d_bytes_per_step"] == 0
 
 
-@pytest.mark.parametrize("bad", [["--warmup", "1"]])
-def test_bench_rejects_short_warmup(bad):
+@pytest.mark.parametrize("bad", [["--warmup", "1"], ["--serve-jobs", "0"], ["--serve-inflight", "0"],
+                                 ["--serve-loads", "0.8,x"], ["--serve-loads", "0"], ["--serve-stage-words", "1"]])
+def test_bench_rejects_bad_arguments(bad):
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference"] + bad,
                          capture_output=True, text=True, timeout=120)
     assert out.returncode != 0
